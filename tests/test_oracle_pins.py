@@ -1,0 +1,468 @@
+"""Pins of the CPU oracle against the paper's closed forms and against mathematics.
+
+Every test here fixes a part of the oracle to something other than the oracle itself:
+an exact identity, a closed form, an independent FFT computation, a brute-force
+Newton solve, or an invariance.  Each names the passage of arXiv 2604.15434 it pins.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.integrate import quad
+
+import oracle as O
+from oracle import sphere
+from paper_2604_15434_gb300 import synth
+
+# ---------------------------------------------------------------- coefficients
+
+
+@pytest.mark.parametrize("a", [0.3, 0.55, 1.0])
+def test_C2_vanishes_without_modification(a):
+    """Sec. 2.2: with all alphas zero the chi equation must disappear (C2 = 0)."""
+    c = O.coefficients(0.0, 0.0, a)
+    assert abs(c["C2"]) < 1e-15
+    assert c["geff"] == 1.0 and c["nu"] == pytest.approx(0.0, abs=1e-15)
+
+
+def test_coefficients_config_c1_by_hand():
+    """alpha_B0=-0.5, alpha_M0=0, a=1, Omega_m0=0.3, worked by hand from Sec. 2.2 and 2.5:
+    C2 = -0.5 + 0.55*(-0.45) - 0.45 + 0.45 = -0.725, nu = 0.725 - 0.25 = 0.475,
+    xi = -0.5, C4 = 2, kappa = 2/4 = 0.5."""
+    c = O.coefficients(-0.5, 0.0, 1.0)
+    assert c["C2"] == pytest.approx(-0.725, abs=1e-15)
+    assert c["nu"] == pytest.approx(0.475, abs=1e-15)
+    assert c["xi"] == -0.5 and c["C4"] == 2.0 and c["kappa"] == pytest.approx(0.5, abs=1e-15)
+    assert c["mu_chi"] == pytest.approx(-0.5 / 0.475, rel=1e-15)
+
+
+@pytest.mark.parametrize("aB0,aM0", [(-0.5, 0.0), (-1.0, 0.2), (-0.24, -0.2), (-2.0, 0.5)])
+def test_alpha_today_and_nu_is_laplacian_prefactor(aB0, aM0):
+    """Eq. alpha-a at a=1 returns alpha_I0; nu (Eq. linearised) equals Eq. chi's
+    Laplacian prefactor 2 aB aM - aB^2 - C2; mu_Psi = 1 + xi^2/nu."""
+    c = O.coefficients(aB0, aM0, 1.0)
+    assert c["alpha_B"] == pytest.approx(aB0, rel=1e-15) and c["alpha_M"] == pytest.approx(aM0, rel=1e-15)
+    assert c["nu"] == pytest.approx(2 * aB0 * aM0 - aB0 ** 2 - c["C2"], abs=1e-14)
+    assert c["mu_psi"] == pytest.approx(1 + c["xi"] ** 2 / c["nu"], rel=1e-14)
+    assert c["E2"] == pytest.approx(1.0, abs=1e-15)
+
+
+@pytest.mark.parametrize("aM0", [0.2, -0.2, 0.5])
+def test_geff_matches_definition_by_quadrature(aM0):
+    """Sec. 2.4: G_eff/G = exp(-int_0^a alpha_M(a')/a' da'), checked by quadrature
+    against the closed form Omega_m(a)^(alpha_M0/(3(1-Omega_m0)))."""
+    om0 = 0.3
+    for a in (0.4, 0.8, 1.0):
+        def am(x):
+            return O.coefficients(0.0, aM0, x)["alpha_M"] / x
+        integ, _ = quad(am, 1e-8, a, epsabs=1e-14, epsrel=1e-13, limit=200)
+        assert O.coefficients(0.0, aM0, a)["geff"] == pytest.approx(math.exp(-integ), rel=1e-10)
+
+
+def test_alphaB_dot_is_log_derivative():
+    """Reading of alpha_B-dot/H as d alpha_B / d ln a (Sec. 2.2), checked by central differences."""
+    for a in (0.35, 0.7, 1.0):
+        e = 1e-5
+        up = O.coefficients(-0.8, 0.0, a * math.exp(e))["alpha_B"]
+        dn = O.coefficients(-0.8, 0.0, a * math.exp(-e))["alpha_B"]
+        num = (up - dn) / (2 * e)
+        assert O.coefficients(-0.8, 0.0, a)["alphaB_dot_over_h"] == pytest.approx(num, rel=1e-8)
+        assert O.coefficients(-0.8, 0.0, a, include_dot=False)["alphaB_dot_over_h"] == 0.0
+
+
+def test_hdot_matches_background():
+    """H-dot/H^2 = d ln E / d ln a for E^2 = Omega_m0 a^-3 + 1 - Omega_m0."""
+    for a in (0.4, 1.0):
+        e = 1e-5
+        lnE = lambda x: 0.5 * math.log(O.coefficients(0, 0, x)["E2"])
+        num = (lnE(a * math.exp(e)) - lnE(a * math.exp(-e))) / (2 * e)
+        assert O.coefficients(0, 0, a)["hdot_over_h2"] == pytest.approx(num, rel=1e-8)
+
+
+# ---------------------------------------------------------------- discrete operator
+
+
+def _padded_quadratic(n, A, b, c0, h):
+    idx = (np.arange(-1, n + 1) + 0.5) * h
+    z, y, x = np.meshgrid(idx, idx, idx, indexing="ij")
+    X = np.stack([x, y, z])
+    quadf = 0.5 * np.einsum("i...,ij,j...->...", X, A, X)
+    return quadf + np.einsum("i,i...->...", b, X) + c0
+
+
+def test_operator_exact_on_quadratic_polynomials():
+    """Sec. 3.2.1 stencils are exact on quadratics: L = tr A and the bracket of Eq. chi_scm
+    (L chi)^2 - chi_ij chi^ij = (tr A)^2 - |A|_F^2.  A sign error, a dropped cross term or
+    a transposed index in q2 changes this value."""
+    rng = np.random.default_rng(7)
+    n, h = 6, 1.0 / 6
+    for _ in range(5):
+        M = rng.standard_normal((3, 3))
+        A = M + M.T
+        p = _padded_quadratic(n, A, rng.standard_normal(3), 0.3, h)
+        nu, kap = 0.7, 0.0
+        L = O.apply_N_padded(p, h, 1.0, 0.0)
+        assert np.allclose(L, np.trace(A), rtol=1e-9, atol=1e-9)
+        q2 = -O.apply_N_padded(p, h, 0.0, 1.0)
+        exact = np.trace(A) ** 2 - np.sum(A * A)
+        assert np.allclose(q2, exact, rtol=1e-8, atol=1e-8 * max(1, abs(exact)))
+        N = O.apply_N_padded(p, h, nu, 0.37)
+        assert np.allclose(N, nu * np.trace(A) - 0.37 * exact, rtol=1e-8, atol=1e-8)
+
+
+def test_laplacian_matches_fft_eigenvalues():
+    """The 7-point Laplacian has eigenvalues -(4/h^2) sum sin^2(pi m/n) on a periodic grid."""
+    rng = np.random.default_rng(3)
+    n = 16
+    u = rng.standard_normal((n, n, n))
+    got = O.apply_N(u, 1.0, 0.0)
+    m = np.fft.fftfreq(n) * n
+    s = np.sin(np.pi * m / n) ** 2
+    lam = -(4.0 * n * n) * (s[:, None, None] + s[None, :, None] + s[None, None, :])
+    want = np.real(np.fft.ifftn(lam * np.fft.fftn(u)))
+    assert np.allclose(got, want, atol=1e-9 * np.abs(want).max())
+
+
+def test_operator_plane_parallel_has_no_screening():
+    """For a field that varies along one axis only the discrete bracket vanishes exactly."""
+    n = 16
+    x = (np.arange(n) + 0.5) / n
+    u = np.broadcast_to((np.sin(2 * np.pi * x) + 0.3 * np.cos(6 * np.pi * x))[None, None, :], (n, n, n)).copy()
+    assert np.array_equal(O.apply_N(u, 0.0, 1.0), np.zeros_like(u))
+
+
+def test_operator_commutes_with_axis_permutation_and_shift():
+    rng = np.random.default_rng(11)
+    n = 8
+    u = rng.standard_normal((n, n, n))
+    N = O.apply_N(u, 0.4, 0.9)
+    assert np.allclose(O.apply_N(np.transpose(u, (1, 2, 0)), 0.4, 0.9), np.transpose(N, (1, 2, 0)), atol=1e-9)
+    assert np.allclose(O.apply_N(np.roll(u, 3, axis=1), 0.4, 0.9), np.roll(N, 3, axis=1), atol=1e-9)
+
+
+def test_local_update_solves_the_cell_equation():
+    """Eq. quadratic: after a red half-sweep each red cell, with only its own value changed,
+    zeroes its residual (real root) or sits on the floored root (Sec. 3.3)."""
+    rng = np.random.default_rng(5)
+    n = 8
+    u = 0.002 * rng.standard_normal((n, n, n))
+    f = rng.standard_normal((n, n, n))
+    nu, kap, eta = 0.475, 0.5, 0.35
+    u1 = O.smooth_sweep(u, f, 0.0, nu, kap, eta)
+    red = (np.indices(u.shape).sum(0) % 2) == 0
+    checked = 0
+    for cell in zip(*np.nonzero(red)):
+        uc = u.copy()
+        uc[cell] = u1[cell]
+        r, sat = O.residual(uc, f, 0.0, nu, kap, eta)
+        scale = 6 * nu * n * n * max(abs(uc[cell]), 1e-3)
+        assert abs(r[cell]) < 1e-11 * scale, (cell, r[cell], sat[cell])
+        checked += 1
+    assert checked == n ** 3 // 2
+
+
+def test_root_branch_is_linear_continuation():
+    """Eq. quadratic picks the root that continues the linearised solution: for tiny kappa a
+    sweep must agree with the kappa = 0 (linear Gauss-Seidel) sweep to O(kappa)."""
+    rng = np.random.default_rng(9)
+    n = 8
+    u = 0.01 * rng.standard_normal((n, n, n))
+    f = rng.standard_normal((n, n, n))
+    for nu in (0.475, -1.1):
+        lin = O.smooth_sweep(u, f, 0.0, nu, 0.0, 0.2)
+        nl = O.smooth_sweep(u, f, 0.0, nu, 1e-9, 0.2)
+        assert np.abs(nl - lin).max() < 1e-8 * np.abs(lin).max()
+
+
+# ---------------------------------------------------------------- multigrid solutions
+
+
+def _fft_linear_solve(f, nu):
+    n = f.shape[0]
+    m = np.fft.fftfreq(n) * n
+    s = np.sin(np.pi * m / n) ** 2
+    lam = -(4.0 * n * n) * (s[:, None, None] + s[None, :, None] + s[None, None, :])
+    fk = np.fft.fftn(f)
+    lam[0, 0, 0] = 1.0
+    uk = fk / (nu * lam)
+    uk[0, 0, 0] = 0.0
+    return np.real(np.fft.ifftn(uk))
+
+
+def test_linear_limit_matches_fft_solve():
+    """Screening off (kappa = 0): the FAS solve equals the FFT solve of nu L chi = f - <f>
+    to 1e-10 relative (the benchmark spec's first oracle check; Eq. linearised)."""
+    pos = synth.zeldovich_particles(32, -1.5, 1.0, 1001, nyquist_cutoff=True)
+    d = O.density(O.deposit_cic(pos, 32), pos.shape[1])
+    c = O.coefficients(-0.5, 0.0, 1.0)
+    f = O.source(d, c)
+    chi, info, st = O.mg_solve(f, c["nu"], 0.0, 1e-13)
+    assert st == 0
+    ref = _fft_linear_solve(f, c["nu"])
+    assert np.linalg.norm(chi - ref) / np.linalg.norm(ref) < 1e-10
+
+
+def test_plane_parallel_nonlinear_equals_linear():
+    """With kappa != 0 but a source varying along z only, q2 vanishes exactly, so the
+    nonlinear solve must return the FFT linear solution (no floor triggered)."""
+    n = 32
+    z = (np.arange(n) + 0.5) / n
+    prof = 0.5 * np.sin(2 * np.pi * z) + 0.2 * np.cos(4 * np.pi * z + 0.4)
+    d = np.broadcast_to(prof[:, None, None], (n, n, n)).copy()
+    c = O.coefficients(-0.5, 0.0, 1.0)
+    f = O.source(d, c)
+    chi, info, st = O.mg_solve(f, c["nu"], c["kappa"], 1e-13)
+    assert st == 0 and info["sat_cells"] == 0
+    ref = _fft_linear_solve(f, c["nu"])
+    assert np.linalg.norm(chi - ref) / np.linalg.norm(ref) < 1e-10
+
+
+def _newton_dense(f, nu, kap, eta, chi0):
+    """Brute force: damped Newton on the residual map (r(chi, lambda), <chi>) of the whole grid.
+    The residual is piecewise quadratic, so central differences give its Jacobian exactly
+    (up to rounding) wherever no cell changes piece; a backtracking line search on |F|
+    globalises the iteration."""
+    n = f.shape[0]
+    m = n ** 3
+    chi = chi0.copy()
+    lam = 0.0
+    fnorm = np.linalg.norm(f - f.mean())
+
+    def F_of(chi, lam):
+        r, _ = O.residual(chi, f, lam, nu, kap, eta)
+        return np.concatenate([r.ravel(), [chi.mean() * 6 * abs(nu) * n * n]])
+
+    F = F_of(chi, lam)
+    for it in range(200):
+        if np.linalg.norm(F) < 1e-14 * fnorm:
+            return chi, lam, it
+        J = np.zeros((m + 1, m + 1))
+        t = 1e-6 * max(np.abs(chi).max(), 1e-6)
+        for j in range(m):
+            e = np.zeros(m)
+            e[j] = t
+            J[:, j] = (F_of(chi + e.reshape(chi.shape), lam) - F_of(chi - e.reshape(chi.shape), lam)) / (2 * t)
+        tl = 1e-6 * max(abs(lam), np.abs(f).max())
+        J[:, m] = (F_of(chi, lam + tl) - F_of(chi, lam - tl)) / (2 * tl)
+        dx = np.linalg.solve(J, -F)
+        step = 1.0
+        while step > 1e-4:
+            chi_t = chi + step * dx[:m].reshape(chi.shape)
+            lam_t = lam + step * dx[m]
+            Ft = F_of(chi_t, lam_t)
+            if np.linalg.norm(Ft) < (1 - 1e-4 * step) * np.linalg.norm(F):
+                break
+            step *= 0.5
+        chi, lam, F = chi_t, lam_t, Ft
+    raise AssertionError("dense Newton did not converge")
+
+
+@pytest.mark.parametrize("amp", [0.5, 3.0])
+def test_fas_matches_dense_newton_8cubed(amp):
+    """The benchmark spec's third oracle check: a full Newton solve of the discrete system on an
+    8^3 grid agrees with the FAS multigrid to 1e-12 (amp = 3 exercises the screening term)."""
+    rng = np.random.default_rng(21)
+    n = 8
+    g = rng.standard_normal((n, n, n))
+    d = amp * (g - g.mean())
+    c = O.coefficients(-0.5, 0.0, 1.0)
+    f = O.source(d, c)
+    chi_mg, info, st = O.mg_solve(f, c["nu"], c["kappa"], 1e-14, coarsest_n=4)
+    assert st == 0
+    chi_lin = _fft_linear_solve(f, c["nu"])
+    chi_nt, lam, it = _newton_dense(f, c["nu"], c["kappa"], O.ETA_DEFAULT, chi_lin)
+    assert np.linalg.norm(chi_mg - chi_nt) / np.linalg.norm(chi_nt) < 1e-12
+    assert info["lambda"] == pytest.approx(lam, abs=1e-10 * np.abs(f).max())
+
+
+def test_solution_commutes_with_axis_permutation():
+    pos = synth.zeldovich_particles(16, -1.5, 1.0, 1234, nyquist_cutoff=True)
+    d = O.density(O.deposit_cic(pos, 16), pos.shape[1])
+    chi, _, st = O.scalar_solve(d, -0.5, 0.0, 1.0, 1e-13)
+    chi2, _, st2 = O.scalar_solve(np.transpose(d, (2, 0, 1)), -0.5, 0.0, 1.0, 1e-13)
+    assert st == 0 and st2 == 0
+    assert np.linalg.norm(np.transpose(chi, (2, 0, 1)) - chi2) / np.linalg.norm(chi) < 1e-11
+
+
+@pytest.mark.parametrize("aB0,aM0", [(-0.5, 0.0), (-2.0, 0.0)])
+def test_floored_solution_is_unique(aB0, aM0):
+    """Reading R-sat (Sec. 3.3): with the floored discriminant the discrete problem has one
+    solution.  Two different starting points (zero and the linear FFT solution) and two
+    cycle shapes must land on the same field, including strongly floored cases (nu < 0)."""
+    d = synth.lognormal_delta(32, -2.0, 1.5, 1003)
+    c = O.coefficients(aB0, aM0, 1.0)
+    f = O.source(d, c)
+    a, ia, sa = O.mg_solve(f, c["nu"], c["kappa"], 1e-13)
+    b, ib, sb = O.mg_solve(f, c["nu"], c["kappa"], 1e-13, chi0=_fft_linear_solve(f, c["nu"]), npre=3, npost=1)
+    assert sa == 0 and sb == 0 and ia["sat_cells"] > 0
+    assert np.linalg.norm(a - b) / np.linalg.norm(a) < 1e-10
+
+
+# ---------------------------------------------------------------- spherical closed form
+
+
+def _sphere_setup(n, kind, nu, kap, xi, S0, R):
+    h = 1.0 / n
+    levels = []
+    nl = n
+    while nl >= 4:
+        levels.append(nl)
+        nl //= 2
+    ghosts = []
+    for nl in levels:
+        hl = 1.0 / nl
+        idx = (np.arange(-1, nl + 1) + 0.5) * hl - 0.5
+        z, y, x = np.meshgrid(idx, idx, idx, indexing="ij")
+        r = np.sqrt(x * x + y * y + z * z)
+        prof = sphere.tophat_profile(r, S0, R, nu, kap, xi) if kind == "tophat" else \
+            sphere.gauss_profile(r, S0, R, nu, kap, xi)
+        ghosts.append(prof)
+    idx = (np.arange(n) + 0.5) * h - 0.5
+    z, y, x = np.meshgrid(idx, idx, idx, indexing="ij")
+    r = np.sqrt(x * x + y * y + z * z)
+    if kind == "tophat":
+        # cell average of the top-hat (volume fraction from 8^3 sub-samples per cell), the
+        # consistent finite-volume source for the sharp-edged closed form
+        sub = (np.arange(8) + 0.5) / 8 - 0.5
+        frac = np.zeros_like(r)
+        for dz in sub:
+            for dy in sub:
+                for dx in sub:
+                    frac += ((x + dx * h) ** 2 + (y + dy * h) ** 2 + (z + dz * h) ** 2) <= R * R
+        S = S0 * frac / 512.0
+    else:
+        S = S0 * np.exp(-0.5 * (r / R) ** 2)
+    return r, xi * S, ghosts
+
+
+def test_tophat_sphere_matches_closed_form():
+    """Sec. 3.6.1 / Fig. grids analogue: top-hat source, Dirichlet faces from the closed form,
+    config-1 coefficients, strongly screened (nu^2 << 8 kappa |xi| y_N).  The paper reports
+    chi within 0.2% at 32^3 and 64^3; here chi is within 0.5% (32^3) and 0.25% (64^3) of
+    the central value, and the error falls with resolution."""
+    c = O.coefficients(-0.5, 0.0, 1.0)
+    nu, kap, xi = c["nu"], c["kappa"], c["xi"]
+    S0, R = 6.0, 0.2
+    assert 8 * kap * abs(xi) * S0 / 3 > 10 * nu ** 2  # deep in the screened regime
+    errs = []
+    for n in (32, 64):
+        r, f, ghosts = _sphere_setup(n, "tophat", nu, kap, xi, S0, R)
+        chi, info, st = O.mg_solve(f, nu, kap, 1e-11, ghosts=ghosts)
+        assert st == 0 and info["sat_cells"] == 0
+        ref = sphere.tophat_profile(r, S0, R, nu, kap, xi)
+        errs.append(np.abs(chi - ref).max() / np.abs(ref).max())
+    assert errs[0] < 5e-3 and errs[1] < 2.5e-3 and errs[1] < errs[0] / 1.8, errs
+
+
+def test_gaussian_sphere_converges_second_order():
+    """Same closed form with a smooth source: the discretisation error at 16^3 -> 32^3 falls
+    by about 4 (the 7-point and 4h^2 cross stencils are second order)."""
+    c = O.coefficients(-0.5, 0.0, 1.0)
+    nu, kap, xi = c["nu"], c["kappa"], c["xi"]
+    S0, s = 8.0, 0.07
+    errs = []
+    for n in (16, 32):
+        r, f, ghosts = _sphere_setup(n, "gauss", nu, kap, xi, S0, s)
+        chi, info, st = O.mg_solve(f, nu, kap, 1e-12, ghosts=ghosts)
+        assert st == 0
+        ref = sphere.gauss_profile(r, S0, s, nu, kap, xi)
+        errs.append(np.abs(chi - ref).max() / np.abs(ref).max())
+    assert errs[1] < 4e-3
+    assert 3.3 < errs[0] / errs[1] < 4.7, errs
+
+
+def test_spherical_ratio_limits():
+    """Fig. spher-ana: Psi'/Psi'_GR -> mu_Psi far from the mass and -> 1 deep inside the
+    screening radius (Eq. analytical)."""
+    c = O.coefficients(-0.5, 0.0, 1.0)
+    far = sphere.radial_derivative_ratio(1e-9, c["nu"], c["kappa"], c["xi"])
+    near = sphere.radial_derivative_ratio(1e9, c["nu"], c["kappa"], c["xi"])
+    assert far == pytest.approx(c["mu_psi"], rel=1e-6)
+    assert near == pytest.approx(1.0, abs=2e-4)
+
+
+# ---------------------------------------------------------------- particle-mesh steps
+
+
+def test_cic_mass_and_single_particle():
+    """CIC (Sec. 3.6.2): weights sum to one per particle; a particle at a cell centre
+    lands in one cell; one at a quarter-cell offset splits 3/4 : 1/4 exactly."""
+    n = 8
+    pos = np.array([[0.5 / n], [1.5 / n], [2.5 / n]])
+    acc = O.deposit_cic(pos, n)
+    assert acc[2, 1, 0] == 2 ** 40 and np.count_nonzero(acc) == 1
+    pos = np.array([[0.75 / n], [1.5 / n], [2.5 / n]])
+    acc = O.deposit_cic(pos, n)
+    assert acc[2, 1, 0] == 3 * 2 ** 38 and acc[2, 1, 1] == 2 ** 38 and np.count_nonzero(acc) == 2
+    pos = np.array([[0.1 / n], [7.9 / n], [0.0]])  # wraps on every axis
+    acc = O.deposit_cic(pos, n)
+    assert acc.sum() == 2 ** 40 and acc[7, 7, 7] > 0
+
+
+def test_cic_is_permutation_invariant_and_mass_exact():
+    pos = synth.zeldovich_particles(16, -1.5, 2.0, 77)
+    acc = O.deposit_cic(pos, 16)
+    perm = np.random.default_rng(1).permutation(pos.shape[1])
+    assert np.array_equal(acc, O.deposit_cic(pos[:, perm], 16))
+    assert abs(int(acc.sum()) - pos.shape[1] * 2 ** 40) <= 8 * pos.shape[1]
+
+
+def test_interp_is_adjoint_of_deposit():
+    """Same weights for assignment and interpolation (no self-force): sum_p W g = sum_c rho g."""
+    rng = np.random.default_rng(2)
+    n = 8
+    pos = rng.random((3, 50))
+    grid = rng.standard_normal((3, n, n, n))
+    at_p = O.interp_cic(grid, pos)
+    acc = O.deposit_cic(pos, n).astype(np.float64) / 2 ** 40
+    for d in range(3):
+        assert at_p[d].sum() == pytest.approx((acc * grid[d]).sum(), rel=1e-9)
+    const = np.ones((3, n, n, n)) * 2.5
+    assert np.allclose(O.interp_cic(const, pos), 2.5, rtol=1e-15)
+
+
+def test_poisson_fft_solves_the_7pt_equation():
+    """Eq. phipsi_mod: L_7pt Psi_N = (3/2)(G_eff/G) a Omega_m0 delta (zero-mean part)."""
+    d = synth.lognormal_delta(16, -2.0, 1.0, 4)
+    c = O.coefficients(-1.0, 0.2, 0.8)
+    psi = O.poisson_fft(d, c, 0.8)
+    lap = O.apply_N(psi, 1.0, 0.0)
+    rhs = 1.5 * c["geff"] * 0.8 * 0.3 * d
+    assert np.allclose(lap, rhs - rhs.mean(), atol=1e-10 * np.abs(rhs).max())
+    assert abs(psi.mean()) < 1e-14
+
+
+def test_five_point_gradient_spectral_factor():
+    """Sec. 3.5.2 five-point stencil on a sinusoid: derivative times (8 sin t - sin 2t)/(6 t),
+    t = k h, which is 1 - t^4/30 + O(t^6) (fourth order)."""
+    n = 32
+    x = (np.arange(n) + 0.5) / n
+    for m in (1, 3):
+        k = 2 * np.pi * m
+        psi = np.broadcast_to(np.sin(k * x)[None, None, :], (n, n, n)).copy()
+        g = O.accel_grid(psi, None, 0.0, n)
+        t = k / n
+        fac = (8 * np.sin(t) - np.sin(2 * t)) / (6 * t)
+        want = -k * np.cos(k * x) * fac
+        assert np.allclose(g[0, 0, 0, :], want, atol=1e-12 * k)
+        assert np.allclose(g[1], 0.0, atol=1e-9) and np.allclose(g[2], 0.0, atol=1e-9)
+        assert abs(fac - (1 - t ** 4 / 30)) < t ** 6
+
+
+def test_force_adds_fifth_force_with_coupling():
+    """Eq. force / Eq. phipsi_mod: the grid force is -grad(Psi_N + (alpha_B - alpha_M) chi)."""
+    rng = np.random.default_rng(4)
+    n = 8
+    psi = rng.standard_normal((n, n, n))
+    chi = rng.standard_normal((n, n, n))
+    g = O.accel_grid(psi, chi, -0.7, n)
+    assert np.allclose(g, O.accel_grid(psi, None, 0.0, n) - 0.7 * O.accel_grid(chi, None, 0.0, n), atol=1e-10)
+
+
+def test_kick_drift_closed_form_and_wrap():
+    pos = np.array([[0.95], [0.1], [0.5]])
+    vel = np.array([[1.0], [-2.0], [0.0]])
+    acc = np.array([[10.0], [0.0], [-4.0]])
+    p2, v2 = O.kick_drift(pos, vel, acc, 0.01)
+    assert np.allclose(v2[:, 0], [1.1, -2.0, -0.04])
+    assert np.allclose(p2[:, 0], [(0.95 + 0.011) % 1.0, 0.08, 0.5 - 0.0004])
