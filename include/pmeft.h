@@ -1,0 +1,191 @@
+/*
+ * pmeft.h -- C ABI of the GB300 (sm_103a) library for the screened EFTofDE
+ * particle-mesh path of arXiv 2604.15434 (PySCo-EFT / ECOSMOG-EFT).
+ *
+ * Conventions for every entry point
+ *   - Grids are n^3 arrays of double in device memory, index (k*n + j)*n + i with
+ *     x (i) fastest; cell i is centred at (i + 1/2)/n in box units (box = 1,
+ *     supercomoving code units of Sec. 3.1).  n must be a power of two >= 8.
+ *   - Particle arrays are [3][np] doubles in device memory (rows x, y, z), positions
+ *     in [0, 1).
+ *   - The caller allocates and owns every input and output buffer.  The context
+ *     owns its scratch (multigrid levels, FFT plans, accumulators); it allocates it
+ *     on first use for a given n and keeps it until pm_destroy.
+ *   - All work is enqueued on the context's stream.  Only scalar_mg_solve*, pm_step
+ *     and the calls that return host scalars synchronise that stream.
+ *   - Errors are reported only through the return code; pm_last_error(ctx) gives a
+ *     one-line message.  Nothing is thrown across the ABI.  A context is used by one
+ *     host thread at a time.
+ */
+#ifndef PMEFT_H
+#define PMEFT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pm_ctx pm_ctx;
+
+typedef enum {
+    PM_OK = 0,
+    PM_ERR_INVALID_ARG = 1, /* bad pointer, size, parameter or alignment */
+    PM_ERR_CUDA = 2,        /* a CUDA runtime or cuFFT call failed */
+    PM_ERR_OOM = 3,         /* device allocation failed */
+    PM_ERR_NONFINITE = 4,   /* a NaN or Inf appeared in the input or the iteration */
+    PM_ERR_NOCONV = 5,      /* max_cycles reached before the tolerance */
+    PM_ERR_TIMEOUT = 6,     /* a device-side wait gave up (bounded spin) */
+    PM_ERR_OVERFLOW = 7     /* fixed-point deposit capacity exceeded */
+} pm_status;
+
+/* Solver parameters.  pm_default_params fills the defaults noted here. */
+typedef struct {
+    double omega_m0;       /* Omega_m0 of the LCDM background (0.3; Sec. 3.6.1) */
+    double eta;            /* discriminant floor sqrt(D_floor) = eta * 6|nu|/h^2 (0.35; Sec. 3.3) */
+    int npre, npost;       /* smoothing sweeps before / after the coarse correction (2, 2) */
+    int max_cycles;        /* cap on V-cycles (FP64) or outer iterations (mixed) (100) */
+    int coarsest_n;        /* coarsest grid of the V-cycle (4) */
+    int coarse_sweeps;     /* sweeps of the coarsest-level solve (60) */
+    int precision;         /* 0: FP64 FAS cycle; 1: FP32 inner cycle inside an FP64 defect-correction loop */
+    int include_dot_alphaB;/* 1: keep alpha_B-dot/H = d alpha_B/d ln a in C2 (Sec. 2.2) */
+} pm_params;
+
+/* Report of one solve.  rel_res = |r|_2 / |f - <f>|_2 of the FP64 residual. */
+typedef struct {
+    int cycles;                /* V-cycles (FP64) or outer iterations (mixed) performed */
+    int status;                /* the pm_status the solve returned */
+    double rel_res;            /* final relative residual */
+    double lambda;             /* gauge multiplier: N(chi) = f + lambda on a periodic box */
+    long long floored_cells;   /* cells on the floored discriminant at the end (Sec. 3.3) */
+    int unstable_nu;           /* 1 when nu <= 0 (non-viable model, Sec. 2.5) */
+    double rel_res_hist[64];   /* rel_res before each cycle, [0..min(cycles, 63)] */
+    double ms_total;           /* wall time of the solve on the stream, milliseconds */
+} pm_solve_info;
+
+/* EFT coefficients at scale factor a (Sec. 2.2, Eq. alpha-a, G_eff/G, Eq. linearised,
+ * Eq. chi_scm).  kappa = C4/(4 E^2 a^4); src = xi (3/2)(G_eff/G) a Omega_m0 is the
+ * factor of the chi source f = src * delta. */
+typedef struct {
+    double omega_m_a, alpha_B, alpha_M, geff, E2, C2, C4, nu, xi, kappa, mu_chi, mu_psi, src, poisson_fac;
+} pm_coeffs;
+
+void pm_default_params(pm_params* p);
+
+/* Host-only; no context needed.  Returns PM_ERR_INVALID_ARG for a <= 0, omega_m0 outside (0,1). */
+pm_status pm_coefficients(double alpha_B0, double alpha_M0, double a, double omega_m0, int include_dot_alphaB,
+                          pm_coeffs* out);
+
+/* Create a context on CUDA device `device` that enqueues on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  p may be NULL for defaults. */
+pm_status pm_create(pm_ctx** ctx, int device, void* cuda_stream, const pm_params* p);
+void pm_destroy(pm_ctx* ctx);
+const char* pm_last_error(const pm_ctx* ctx);
+pm_status pm_set_params(pm_ctx* ctx, const pm_params* p);
+
+/*
+ * CIC density assignment (Sec. 3.6.2; cell-centred CIC).  Each particle adds
+ * round((w_x w_y) w_z * 2^40) to 8 cells of an int64 accumulator with integer
+ * atomics, so the grid is bit-exact and independent of particle order; then
+ * delta = acc * 2^-40 * n^3/np - 1.  pos: device [3][np] in [0,1); delta: device n^3.
+ * PM_ERR_INVALID_ARG for np < 1, a bad n or NULL pointers.
+ */
+pm_status pm_deposit_cic(pm_ctx* ctx, const double* pos, long long np, int n, double* delta);
+/* The same deposit, returning the raw int64 fixed-point grid (device n^3 long long). */
+pm_status pm_deposit_cic_fixed(pm_ctx* ctx, const double* pos, long long np, int n, long long* acc);
+
+/*
+ * Standard Poisson equation in code units with the G_eff factor (Eq. phipsi_mod,
+ * Sec. 3.5.1):  L_7pt psi_N = (3/2)(G_eff/G) a Omega_m0 delta on the periodic box,
+ * solved by FFT with the discrete 7-point eigenvalues; psi_N has zero mean.
+ * delta, psi_N: device n^3 (may not alias).
+ */
+pm_status poisson_solve(pm_ctx* ctx, const double* delta, int n, double a, double alpha_M0, double* psi_N);
+
+/*
+ * Scalar-field solve (Eq. chi_scm; Method I discretisation Sec. 3.2.1; void floor
+ * Sec. 3.3; FAS multigrid Sec. 3.4):
+ *     nu L(chi) - kappa q2(chi) = xi (3/2)(G_eff/G) a Omega_m0 delta + lambda,  <chi> = 0,
+ * with red-black Newton-Gauss-Seidel smoothing, to relative residual <= tol.
+ * phi_inout: device n^3, initial guess on entry (zeros for a cold start), chi on
+ * exit.  info (host, nullable) receives the report.  Returns PM_ERR_NOCONV when
+ * max_cycles is reached (phi_inout then holds the last iterate), PM_ERR_NONFINITE
+ * if the iteration produced NaN/Inf.  params.precision selects the FP64 cycle or the
+ * FP32-inner / FP64-outer defect correction.  xi = 0 returns chi = 0 at once.
+ */
+pm_status scalar_mg_solve(pm_ctx* ctx, const double* delta, int n, double alpha_B0, double alpha_M0, double a,
+                          double tol, double* phi_inout, pm_solve_info* info);
+
+/*
+ * Force interpolation (Eq. force, Eq. phipsi_mod, Sec. 3.5.2): acc = -grad Psi at the
+ * particles, Psi = psi_N + (alpha_B - alpha_M) chi, the five-point fourth-order
+ * gradient on the mesh and the CIC weights of the deposit.  phi may be NULL (psi_N
+ * alone).  acc: device [3][np].
+ */
+pm_status force_interp(pm_ctx* ctx, const double* psi_N, const double* phi, int n, double alpha_B0,
+                       double alpha_M0, double a, const double* pos, long long np, double* acc);
+
+/*
+ * One particle-mesh step (Sec. 3.5.1 order): deposit, Poisson, chi solve (warm
+ * started from phi_state, which receives chi), force interpolation, then one kick
+ * and one drift: v += g dt; x = frac(x + v dt).  pos, vel: device [3][np], updated
+ * in place.  phi_state: device n^3.  info as for scalar_mg_solve.
+ */
+pm_status pm_step(pm_ctx* ctx, double* pos, double* vel, long long np, int n, double alpha_B0, double alpha_M0,
+                  double a, double dt, double tol, double* phi_state, pm_solve_info* info);
+
+/* ---- tracing: per-kernel-class device time and launch counts ----
+ * With tracing on, the library records a CUDA event pair around each of its kernel
+ * launches on the context stream (a small overhead) and sums the elapsed times per
+ * class.  Launch counts are kept whether tracing is on or not. */
+typedef enum {
+    PM_K_SWEEP64 = 0,   /* FP64 red-black half-sweeps, all levels */
+    PM_K_SWEEP32 = 1,   /* FP32 half-sweeps of the inner cycle, all levels */
+    PM_K_RESID64 = 2,   /* FP64 residual kernels (fine level of either path) */
+    PM_K_RESID32 = 3,   /* FP32 residual kernels */
+    PM_K_TRANSFER = 4,  /* restriction, FAS right-hand side, prolongation */
+    PM_K_COARSEST = 5,  /* coarsest-level solve */
+    PM_K_REDUCE = 6,    /* reductions, re-centring, corrections, copies */
+    PM_K_PM = 7,        /* deposit, density, Poisson (own kernels + cuFFT), force, kick-drift */
+    PM_K_COUNT = 8
+} pm_kernel_class;
+
+typedef struct {
+    long long launches[PM_K_COUNT];  /* own kernel launches per class (cuFFT counted as 1 each) */
+    double ms[PM_K_COUNT];           /* summed event time per class (0 unless tracing was on) */
+    long long cells[PM_K_COUNT];     /* cells processed by the finest-level launches per class */
+    long long fine_launches[PM_K_COUNT]; /* launches that ran on the finest level of their call */
+    double fine_ms[PM_K_COUNT];      /* event time of those finest-level launches */
+} pm_profile;
+
+/* Turn per-launch event tracing on (1) or off (0); resets the counters. */
+pm_status pm_trace_enable(pm_ctx* ctx, int on);
+/* Synchronise the stream and return the counters accumulated since the last reset. */
+pm_status pm_trace_get(pm_ctx* ctx, pm_profile* out);
+pm_status pm_trace_reset(pm_ctx* ctx);
+
+/* FMA throughput probe: GFLOP/s of independent FP64 and FP32 FMA chains on this device
+ * (the denominator of the ALU roofline of the FP64 stencil kernels).  Allocates and frees
+ * a small device buffer; synchronises the stream. */
+pm_status pm_probe_fma(pm_ctx* ctx, double* fp64_gflops, double* fp32_gflops);
+
+/* ---- single multigrid operations on a periodic n^3 grid (for testing the kernels
+ * one at a time against a reference; same semantics as inside scalar_mg_solve) ---- */
+
+/* One red-black sweep (red = (i+j+k) even first; a half-sweep reads same-colour
+ * neighbours from the values at its start).  u updated in place; f the right-hand
+ * side; lambda added to it; kmask (device n^3 bytes, nullable) switches the screening
+ * term off per cell.  h = 1/n. */
+pm_status pm_mg_sweep(pm_ctx* ctx, double* u, const double* f, double lambda, int n, double nu, double kappa,
+                      double eta, const unsigned char* kmask);
+/* Residual: r = f + lambda - N(u) in cells with a real root, nu (L_sat - L(u)) in floored
+ * cells; floored (device n^3 bytes, nullable) receives the floored-cell flags. */
+pm_status pm_mg_residual(pm_ctx* ctx, const double* u, const double* f, double lambda, int n, double nu,
+                         double kappa, double eta, const unsigned char* kmask, double* r, unsigned char* floored);
+/* Restriction (average of 8 children) fine n^3 -> coarse (n/2)^3. */
+pm_status pm_mg_restrict(pm_ctx* ctx, const double* fine, int n, double* coarse);
+/* fine (n^3) += trilinear cell-centred prolongation of coarse ((n/2)^3), periodic. */
+pm_status pm_mg_prolong_add(pm_ctx* ctx, const double* coarse, int n, double* fine);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PMEFT_H */

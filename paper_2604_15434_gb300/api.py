@@ -1,0 +1,304 @@
+"""Python binding of the ``libpmeft.so`` C ABI (``include/pmeft.h``): argument marshalling only.
+
+Every function takes torch CUDA tensors, checks dtype / device / layout, and passes raw
+pointers to the entry point of the same name; all computation happens in the CUDA
+library.  There is no CPU fallback: if ``libpmeft.so`` is missing or fails to load, every
+call raises.  Build the library with ``python -m paper_2604_15434_gb300.build``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpmeft.so")
+
+PM_OK, PM_ERR_INVALID_ARG, PM_ERR_CUDA, PM_ERR_OOM, PM_ERR_NONFINITE, PM_ERR_NOCONV, PM_ERR_TIMEOUT, \
+    PM_ERR_OVERFLOW = range(8)
+_STATUS = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_CUDA", 3: "PM_ERR_OOM", 4: "PM_ERR_NONFINITE",
+           5: "PM_ERR_NOCONV", 6: "PM_ERR_TIMEOUT", 7: "PM_ERR_OVERFLOW"}
+
+
+class PMError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("omega_m0", ctypes.c_double), ("eta", ctypes.c_double), ("npre", ctypes.c_int),
+                ("npost", ctypes.c_int), ("max_cycles", ctypes.c_int), ("coarsest_n", ctypes.c_int),
+                ("coarse_sweeps", ctypes.c_int), ("precision", ctypes.c_int), ("include_dot_alphaB", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int), ("status", ctypes.c_int), ("rel_res", ctypes.c_double),
+                ("lam", ctypes.c_double), ("floored_cells", ctypes.c_longlong), ("unstable_nu", ctypes.c_int),
+                ("rel_res_hist", ctypes.c_double * 64), ("ms_total", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        k = min(self.cycles + 1, 64)
+        return {"cycles": self.cycles, "status": self.status, "rel_res": self.rel_res, "lambda": self.lam,
+                "floored_cells": self.floored_cells, "unstable_nu": self.unstable_nu,
+                "hist": list(self.rel_res_hist[:k]), "ms_total": self.ms_total}
+
+
+class Coeffs(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "omega_m_a", "alpha_B", "alpha_M", "geff", "E2", "C2", "C4", "nu", "xi", "kappa", "mu_chi", "mu_psi",
+        "src", "poisson_fac")]
+
+
+_lock = threading.Lock()
+_lib = None
+
+# name -> (restype, argtypes)
+_D, _I, _LL, _P = ctypes.c_double, ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p
+SIGNATURES = {
+    "pm_default_params": (None, [_P]),
+    "pm_coefficients": (_I, [_D, _D, _D, _D, _I, _P]),
+    "pm_create": (_I, [_P, _I, _P, _P]),
+    "pm_destroy": (None, [_P]),
+    "pm_last_error": (ctypes.c_char_p, [_P]),
+    "pm_set_params": (_I, [_P, _P]),
+    "pm_deposit_cic": (_I, [_P, _P, _LL, _I, _P]),
+    "pm_deposit_cic_fixed": (_I, [_P, _P, _LL, _I, _P]),
+    "poisson_solve": (_I, [_P, _P, _I, _D, _D, _P]),
+    "scalar_mg_solve": (_I, [_P, _P, _I, _D, _D, _D, _D, _P, _P]),
+    "force_interp": (_I, [_P, _P, _P, _I, _D, _D, _D, _P, _LL, _P]),
+    "pm_step": (_I, [_P, _P, _P, _LL, _I, _D, _D, _D, _D, _D, _P, _P]),
+    "pm_mg_sweep": (_I, [_P, _P, _P, _D, _I, _D, _D, _D, _P]),
+    "pm_mg_residual": (_I, [_P, _P, _P, _D, _I, _D, _D, _D, _P, _P, _P]),
+    "pm_mg_restrict": (_I, [_P, _P, _I, _P]),
+    "pm_mg_prolong_add": (_I, [_P, _P, _I, _P]),
+    "pm_trace_enable": (_I, [_P, _I]),
+    "pm_trace_get": (_I, [_P, _P]),
+    "pm_trace_reset": (_I, [_P]),
+    "pm_probe_fma": (_I, [_P, _P, _P]),
+}
+
+KERNEL_CLASSES = ("sweep64", "sweep32", "resid64", "resid32", "transfer", "coarsest", "reduce", "pm")
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong * 8), ("ms", ctypes.c_double * 8), ("cells", ctypes.c_longlong * 8),
+                ("fine_launches", ctypes.c_longlong * 8), ("fine_ms", ctypes.c_double * 8)]
+
+    def as_dict(self) -> dict:
+        return {k: {"launches": self.launches[i], "ms": self.ms[i], "cells": self.cells[i],
+                    "fine_launches": self.fine_launches[i], "fine_ms": self.fine_ms[i]}
+                for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def load():
+    """Load libpmeft.so and declare the C signatures; raises if the library is absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2604_15434_gb300.build`")
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def default_params(**overrides) -> Params:
+    p = Params()
+    load().pm_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def coefficients(alpha_B0, alpha_M0, a, omega_m0=0.3, include_dot_alphaB=True) -> dict:
+    c = Coeffs()
+    st = load().pm_coefficients(alpha_B0, alpha_M0, a, omega_m0, int(bool(include_dot_alphaB)), ctypes.byref(c))
+    if st != PM_OK:
+        raise PMError(st, "pm_coefficients: invalid argument")
+    return {n: getattr(c, n) for n, _ in Coeffs._fields_}
+
+
+class Context:
+    """Owns a ``pm_ctx``: device scratch (multigrid levels, FFT plans) and the stream it enqueues on."""
+
+    def __init__(self, device=None, stream=None, **params):
+        lib = load()
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.device = dev
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.params = default_params(**params)
+        h = ctypes.c_void_p()
+        st = lib.pm_create(ctypes.byref(h), dev.index, ctypes.c_void_p(self.stream.cuda_stream),
+                           ctypes.byref(self.params))
+        if st != PM_OK:
+            raise PMError(st, "pm_create failed")
+        self._h = h
+
+    def set_params(self, **params):
+        for k, v in params.items():
+            setattr(self.params, k, v)
+        self._check(load().pm_set_params(self._h, ctypes.byref(self.params)))
+
+    def _check(self, st):
+        if st != PM_OK:
+            msg = load().pm_last_error(self._h)
+            raise PMError(st, msg.decode() if msg else "")
+
+    def trace(self, on: bool = True):
+        """Per-launch CUDA-event tracing of the library's kernels (see pm_trace_enable)."""
+        self._check(load().pm_trace_enable(self._h, int(bool(on))))
+
+    def trace_get(self) -> dict:
+        p = Profile()
+        self._check(load().pm_trace_get(self._h, ctypes.byref(p)))
+        return p.as_dict()
+
+    def trace_reset(self):
+        self._check(load().pm_trace_reset(self._h))
+
+    def probe_fma(self):
+        """(FP64, FP32) FMA throughput of this device in GFLOP/s."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        self._check(load().pm_probe_fma(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_default_ctx = {}
+
+
+def default_context() -> Context:
+    dev = torch.cuda.current_device()
+    s = torch.cuda.current_stream(dev)
+    key = (dev, s.cuda_stream)
+    if key not in _default_ctx:
+        _default_ctx[key] = Context(dev, s)
+    return _default_ctx[key]
+
+
+def _ptr(t: torch.Tensor | None, dtype=torch.float64, shape=None, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def pm_deposit_cic(pos, n, delta=None, ctx=None):
+    """delta (n,n,n) float64 from particle positions pos (3, np) float64 in [0,1)."""
+    ctx = ctx or default_context()
+    npart = pos.shape[1]
+    if delta is None:
+        delta = torch.empty((n, n, n), dtype=torch.float64, device=pos.device)
+    ctx._check(load().pm_deposit_cic(ctx._h, _ptr(pos, name="pos"), npart, n, _ptr(delta, shape=(n, n, n))))
+    return delta
+
+
+def pm_deposit_cic_fixed(pos, n, acc=None, ctx=None):
+    ctx = ctx or default_context()
+    if acc is None:
+        acc = torch.empty((n, n, n), dtype=torch.int64, device=pos.device)
+    ctx._check(load().pm_deposit_cic_fixed(ctx._h, _ptr(pos, name="pos"), pos.shape[1], n,
+                                           _ptr(acc, torch.int64, (n, n, n), "acc")))
+    return acc
+
+
+def poisson_solve(delta, a, alpha_M0, psi=None, ctx=None):
+    ctx = ctx or default_context()
+    n = delta.shape[0]
+    if psi is None:
+        psi = torch.empty_like(delta)
+    ctx._check(load().poisson_solve(ctx._h, _ptr(delta, shape=(n, n, n)), n, a, alpha_M0, _ptr(psi, shape=(n, n, n))))
+    return psi
+
+
+def scalar_mg_solve(delta, alpha_B0, alpha_M0, a, tol, phi=None, ctx=None, raise_on_noconv=True):
+    """chi for the density contrast delta; phi (in/out) is the initial guess.  Returns (phi, info)."""
+    ctx = ctx or default_context()
+    n = delta.shape[0]
+    if phi is None:
+        phi = torch.zeros_like(delta)
+    info = SolveInfo()
+    st = load().scalar_mg_solve(ctx._h, _ptr(delta, shape=(n, n, n), name="delta"), n, alpha_B0, alpha_M0, a, tol,
+                                _ptr(phi, shape=(n, n, n), name="phi"), ctypes.byref(info))
+    if st != PM_OK and (raise_on_noconv or st != PM_ERR_NOCONV):
+        ctx._check(st)
+    return phi, info.as_dict()
+
+
+def force_interp(psi_N, phi, alpha_B0, alpha_M0, a, pos, acc=None, ctx=None):
+    ctx = ctx or default_context()
+    n = psi_N.shape[0]
+    if acc is None:
+        acc = torch.empty_like(pos)
+    ctx._check(load().force_interp(ctx._h, _ptr(psi_N, shape=(n, n, n)), _ptr(phi, shape=(n, n, n)), n, alpha_B0,
+                                   alpha_M0, a, _ptr(pos, name="pos"), pos.shape[1], _ptr(acc, shape=pos.shape)))
+    return acc
+
+
+def pm_step(pos, vel, n, alpha_B0, alpha_M0, a, dt, tol, phi_state, ctx=None):
+    """One PM step in place on pos/vel (3, np); phi_state (n,n,n) warm start in, chi out.  Returns info."""
+    ctx = ctx or default_context()
+    info = SolveInfo()
+    ctx._check(load().pm_step(ctx._h, _ptr(pos, name="pos"), _ptr(vel, shape=pos.shape, name="vel"), pos.shape[1], n,
+                              alpha_B0, alpha_M0, a, dt, tol, _ptr(phi_state, shape=(n, n, n)), ctypes.byref(info)))
+    return info.as_dict()
+
+
+def pm_mg_sweep(u, f, lam, nu, kappa, eta, kmask=None, ctx=None):
+    """One red-black sweep of u in place (periodic n^3)."""
+    ctx = ctx or default_context()
+    n = u.shape[0]
+    ctx._check(load().pm_mg_sweep(ctx._h, _ptr(u, shape=(n, n, n)), _ptr(f, shape=(n, n, n)), lam, n, nu, kappa, eta,
+                                  _ptr(kmask, torch.uint8, (n, n, n), "kmask")))
+    return u
+
+
+def pm_mg_residual(u, f, lam, nu, kappa, eta, kmask=None, ctx=None):
+    ctx = ctx or default_context()
+    n = u.shape[0]
+    r = torch.empty_like(u)
+    fl = torch.empty((n, n, n), dtype=torch.uint8, device=u.device)
+    ctx._check(load().pm_mg_residual(ctx._h, _ptr(u, shape=(n, n, n)), _ptr(f, shape=(n, n, n)), lam, n, nu, kappa,
+                                     eta, _ptr(kmask, torch.uint8, (n, n, n), "kmask"), _ptr(r), _ptr(fl, torch.uint8)))
+    return r, fl
+
+
+def pm_mg_restrict(fine, ctx=None):
+    ctx = ctx or default_context()
+    n = fine.shape[0]
+    out = torch.empty((n // 2,) * 3, dtype=torch.float64, device=fine.device)
+    ctx._check(load().pm_mg_restrict(ctx._h, _ptr(fine, shape=(n, n, n)), n, _ptr(out)))
+    return out
+
+
+def pm_mg_prolong_add(coarse, fine, ctx=None):
+    ctx = ctx or default_context()
+    n = fine.shape[0]
+    ctx._check(load().pm_mg_prolong_add(ctx._h, _ptr(coarse, shape=(n // 2,) * 3), n, _ptr(fine, shape=(n, n, n))))
+    return fine

@@ -1,0 +1,251 @@
+// internal.cuh -- shared declarations of the pmeft CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "pmeft.h"
+
+#define PM_CUDA(call)                                                                    \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            ctx->set_error(std::string(#call) + ": " + cudaGetErrorString(e_));          \
+            return e_ == cudaErrorMemoryAllocation ? PM_ERR_OOM : PM_ERR_CUDA;           \
+        }                                                                                \
+    } while (0)
+
+#define PM_TRY(expr)                          \
+    do {                                      \
+        pm_status s_ = (expr);                \
+        if (s_ != PM_OK) return s_;           \
+    } while (0)
+
+namespace pmeft {
+
+constexpr int kThreads = 256;
+constexpr int kMaxPartials = 4096;  // blocks of a reduction launch (fixed => deterministic)
+
+// One multigrid level of one precision.  u[0]/u[1] ping-pong under the red-black sweep.
+template <typename T>
+struct Level {
+    int n = 0;
+    size_t cells = 0;
+    T* u[2] = {nullptr, nullptr};
+    int cur = 0;            // index of the buffer holding the current iterate
+    T* f = nullptr;         // right-hand side (coarse levels; level 0 reads the source directly)
+    T* r = nullptr;         // residual, then the restricted residual of the finer level
+    T* ur = nullptr;        // restriction of the finer iterate (for the FAS correction)
+    T* bg = nullptr;        // background field of the correction form (mixed precision), or null
+    T* gap = nullptr;       // L_sat - L(background) from the FP64 iterate (finest inner level), or null
+    uint8_t* kmask = nullptr;  // 1: screening term off (coarse levels)
+    uint8_t* sat = nullptr;    // 1: floored piece used by the last residual
+    bool fine = false;         // finest level of its hierarchy (for tracing)
+};
+
+struct Workspace {
+    int n = 0;
+    int nlev = 0;
+    std::vector<Level<double>> d;  // FP64 hierarchy
+    std::vector<Level<float>> s;   // FP32 hierarchy (mixed precision inner cycle)
+    float* rplain = nullptr;       // FP32 inner right-hand side f + lambda - N(chi) at level 0
+    double* psi = nullptr;         // scratch n^3 (Poisson output / total potential)
+    double* delta = nullptr;       // scratch n^3 (pm_step)
+    long long* acc = nullptr;      // int64 fixed-point deposit grid
+    cufftHandle plan_r2c = 0, plan_c2r = 0;
+    double2* spec = nullptr;       // n*n*(n/2+1) complex
+    bool fft_ready = false;
+};
+
+}  // namespace pmeft
+
+struct pm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    pm_params prm{};
+    std::string err;
+    std::map<int, pmeft::Workspace*> ws;
+    double* red_partials = nullptr;  // kMaxPartials * 8 doubles
+    double* red_out = nullptr;       // device results (64 doubles: [0..8] residual, [16..] mean, [32..] norms)
+    double* host_out = nullptr;      // pinned host mirror (64 doubles)
+    int* flag = nullptr;             // device error flag
+    int num_sms = 152;
+    // tracing (pm_trace_*): event pairs per launch, summed per class on read-out
+    bool tracing = false;
+    pm_profile prof{};
+    struct Rec {
+        int cls;
+        bool fine;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    int open_cls = -1;
+    bool open_fine = false;
+    cudaEvent_t open_a = nullptr;
+    void set_error(const std::string& m) { err = m; }
+    cudaEvent_t ev()
+    {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        return e;
+    }
+    // bracket one launch: begin(cls) ... launch ... end()
+    void begin(int cls, bool fine = false, long long cells = 0)
+    {
+        prof.launches[cls] += 1;
+        if (fine) {
+            prof.fine_launches[cls] += 1;
+            prof.cells[cls] += cells;
+        }
+        if (!tracing) return;
+        open_cls = cls;
+        open_fine = fine;
+        open_a = ev();
+        cudaEventRecord(open_a, stream);
+    }
+    void end()
+    {
+        if (!tracing || open_cls < 0) return;
+        cudaEvent_t b = ev();
+        cudaEventRecord(b, stream);
+        recs.push_back({open_cls, open_fine, open_a, b});
+        open_cls = -1;
+    }
+};
+
+namespace pmeft {
+
+pm_status get_workspace(pm_ctx* ctx, int n, Workspace** out);
+pm_status ensure_mg(pm_ctx* ctx, Workspace* w, bool want_fp32);
+pm_status ensure_fft(pm_ctx* ctx, Workspace* w);
+bool valid_n(int n);
+int grid_for(pm_ctx* ctx, size_t work, int threads = kThreads);
+void coefficients(double aB0, double aM0, double a, double om0, int include_dot, pm_coeffs* c);
+
+// Multigrid entry used by scalar_mg_solve and pm_step.
+pm_status mg_solve(pm_ctx* ctx, const double* delta, int n, const pm_coeffs& c, double tol, double* phi,
+                   pm_solve_info* info);
+// Poisson (psi_N) and the particle kernels.
+pm_status poisson(pm_ctx* ctx, const double* delta, int n, double fac, double* psi);
+pm_status deposit(pm_ctx* ctx, const double* pos, long long np, int n, long long* acc);
+pm_status density(pm_ctx* ctx, const long long* acc, int n, long long np, double* delta);
+pm_status interp_force(pm_ctx* ctx, const double* psiN, const double* chi, double xi, int n, const double* pos,
+                       long long np, double* acc);
+pm_status kick_drift(pm_ctx* ctx, double* pos, double* vel, const double* acc, long long np, double dt);
+
+// ---------------------------------------------------------------------------------------
+// Device side: the local quadratic of Eq. chi_discrete at one cell (Sec. 3.2.1).
+// Values: c0 centre; ax/ay/az sums of the two face neighbours per axis; exy/exz/eyz the
+// four-corner cross sums (x+y+ - x+y- - x-y+ + x-y-) of the 4h^2 cross differences.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+struct Local {
+    T G, Ep, P, D, L, g;  // g = L_sat - L, the floored gap (valid when kappa != 0)
+};
+
+template <typename T>
+struct Stencil {
+    T c0, ax, ay, az, exy, exz, eyz;
+};
+
+// Load the 19-point stencil around (i, j, k) of a periodic n^3 grid; the centre and the
+// 12 edge neighbours (same red/black colour) come from `own`, the 6 faces from `oth`.
+template <typename T>
+__device__ __forceinline__ Stencil<T> load_stencil(const T* __restrict__ own, const T* __restrict__ oth, int i,
+                                                   int j, int k, int n)
+{
+    const int m = n - 1;
+    const int ip = (i + 1) & m, im = (i - 1) & m, jp = (j + 1) & m, jm = (j - 1) & m, kp = (k + 1) & m,
+              km = (k - 1) & m;
+    const size_t sn = (size_t)n, row = (size_t)k * sn + j;
+    const size_t rk = row * sn;
+    auto at = [&](const T* p, int ii, int jj, int kk) { return p[((size_t)kk * sn + jj) * sn + ii]; };
+    Stencil<T> s;
+    s.c0 = own[rk + i];
+    s.ax = oth[rk + ip] + oth[rk + im];
+    s.ay = at(oth, i, jp, k) + at(oth, i, jm, k);
+    s.az = at(oth, i, j, kp) + at(oth, i, j, km);
+    s.exy = at(own, ip, jp, k) - at(own, ip, jm, k) - at(own, im, jp, k) + at(own, im, jm, k);
+    s.exz = at(own, ip, j, kp) - at(own, ip, j, km) - at(own, im, j, kp) + at(own, im, j, km);
+    s.eyz = at(own, i, jp, kp) - at(own, i, jp, km) - at(own, i, jm, kp) + at(own, i, jm, km);
+    return s;
+}
+
+// N and the local quadratic about the current centre value.  ih2 = 1/h^2 (exact for
+// power-of-two n).  rhs = f + lambda.  lsat = L_sat = 3 nu (1 - eta)/(4 kappa), the
+// Laplacian of the floored root (unused when kappa = 0).
+//
+// With a background b (correction form of the mixed-precision inner cycle) the operator
+// is N(b + u) - N(b), evaluated without cancellation, and L is L(b + u).  On the finest
+// inner level the caller passes gapx = L_sat - L(b) computed in FP64 from the FP64
+// iterate: near convergence it is small in floored cells, so its FP32 rounding is
+// relative, whereas L(b) itself (or the FP32 copy's second differences) would leave an
+// absolute error ~eps |L_sat| under the outer residual.
+template <typename T, bool BG>
+__device__ __forceinline__ Local<T> local_eval(const Stencil<T>& s, const Stencil<T>& b, T ih2, T nu, T kap, T rhs,
+                                               T lsat, bool use_gap = false, T gapx = T(0))
+{
+    const T X = (s.ax - T(2) * s.c0) * ih2;
+    const T Y = (s.ay - T(2) * s.c0) * ih2;
+    const T Z = (s.az - T(2) * s.c0) * ih2;
+    const T q = T(0.25) * ih2;
+    const T cxy = s.exy * q, cxz = s.exz * q, cyz = s.eyz * q;
+    Local<T> o;
+    const T L = X + Y + Z;
+    T q2 = T(2) * (X * Y + Y * Z + Z * X) - T(2) * (cxy * cxy + cxz * cxz + cyz * cyz);
+    T Ltot = L;
+    if (BG) {
+        const T Xb = (b.ax - T(2) * b.c0) * ih2;
+        const T Yb = (b.ay - T(2) * b.c0) * ih2;
+        const T Zb = (b.az - T(2) * b.c0) * ih2;
+        const T bxy = b.exy * q, bxz = b.exz * q, byz = b.eyz * q;
+        // q2(b + u) - q2(b) = q2(u) + 2[Xb(Y+Z) + Yb(X+Z) + Zb(X+Y)] - 4[bxy cxy + bxz cxz + byz cyz]
+        q2 += T(2) * (Xb * (Y + Z) + Yb * (X + Z) + Zb * (X + Y)) - T(4) * (bxy * cxy + bxz * cxz + byz * cyz);
+        Ltot = L + (Xb + Yb + Zb);
+    }
+    if (kap != T(0)) {
+        if (use_gap) {
+            o.g = gapx - L;
+            Ltot = lsat - o.g;
+        } else {
+            o.g = lsat - Ltot;
+        }
+    } else {
+        o.g = T(0);
+    }
+    o.L = Ltot;
+    const T N = nu * L - kap * q2;
+    o.G = N - rhs;
+    o.Ep = (T(-6) * nu + T(8) * kap * o.L) * ih2;
+    o.P = T(-24) * kap * ih2 * ih2;
+    o.D = o.Ep * o.Ep - T(4) * o.P * o.G;
+    return o;
+}
+
+// Correction e = c_new - c0: the root continuing the linear solution (Eq. quadratic),
+// with the discriminant floored at Df (Sec. 3.3).  sp = -sgn(nu).  The floored root is
+// (sp sqrt(Df) - Ep)/(2P), which equals -g h^2/6 exactly (the centre value that puts L on
+// L_sat); the latter form is used because it carries no cancellation.
+template <typename T>
+__device__ __forceinline__ T local_update(const Local<T>& o, T sp, T Df, T ih2)
+{
+    if (o.P == T(0)) return -o.G / o.Ep;
+    if (o.D < Df) return -o.g / (T(6) * ih2);
+    const T sq = sqrt(o.D);
+    if (o.Ep * sp > T(0)) return T(-2) * o.G / (o.Ep + sp * sq);
+    return (sp * sq - o.Ep) / (T(2) * o.P);
+}
+
+}  // namespace pmeft

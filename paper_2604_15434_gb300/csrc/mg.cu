@@ -1,0 +1,733 @@
+// mg.cu -- FAS multigrid for the screened chi equation (Sec. 3.2.1, 3.3, 3.4 of arXiv 2604.15434).
+//
+// Discrete problem (identical to the CPU reference):
+//   N(chi) = nu L(chi) - kappa q2(chi) = f + lambda on the periodic n^3 mesh, <chi> = 0,
+//   with the root of Eq. quadratic that continues the linear solution and the
+//   discriminant floored at D_floor = (eta 6|nu|/h^2)^2 (Sec. 3.3).  Red-black
+//   Newton-Gauss-Seidel: a half-sweep reads the 12 same-colour edge neighbours from the
+//   values at its start (out-of-place ping-pong of two buffers).
+// Residual: f + lambda - N in cells with a real root, nu (L_sat - L) in floored cells; the
+// floored piece belongs to the finest level, coarse levels fix their pieces by the
+// restricted mask (screening off where at least half the children were floored).
+// Two drivers: an FP64 FAS V-cycle, and an FP64 defect-correction loop whose inner
+// FAS V-cycle runs in FP32 on the correction e with the FP64 iterate as background.
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace pmeft {
+
+// ------------------------------------------------------------------ reductions
+
+// 8 running sums per block: [0] sum r, [1] sum r over unfloored, [2] sum r^2,
+// [3] count unfloored, [4] count non-finite, [5] sum x, [6] sum x^2, [7] spare.
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int NV>
+__device__ __forceinline__ void block_sums(double (&v)[NV], double* partials)
+{
+    __shared__ double sh[NV][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double s = warp_sum(v[q]);
+        if (lane == 0) sh[q][wid] = s;
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double s = lane < nw ? sh[q][lane] : 0.0;
+            s = warp_sum(s);
+            if (lane == 0) partials[(size_t)blockIdx.x * 8 + q] = s;
+        }
+    }
+}
+
+// Sum the per-block partials in a fixed order (deterministic), and derive the gauge
+// shift gm = sum r / count unfloored.  out[0..7] sums, out[8] gm.
+__global__ void k_finalize(const double* __restrict__ partials, int nblocks, double* __restrict__ out)
+{
+    __shared__ double sh[8][256];
+    const int t = threadIdx.x;
+    for (int q = 0; q < 8; ++q) {
+        double s = 0.0;
+        for (int b = t; b < nblocks; b += blockDim.x) s += partials[(size_t)b * 8 + q];
+        sh[q][t] = s;
+    }
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (t < w)
+            for (int q = 0; q < 8; ++q) sh[q][t] += sh[q][t + w];
+        __syncthreads();
+    }
+    if (t == 0) {
+        for (int q = 0; q < 8; ++q) out[q] = sh[q][0];
+        out[8] = sh[3][0] > 0.0 ? sh[0][0] / sh[3][0] : 0.0;
+    }
+}
+
+// ------------------------------------------------------------------ smoother
+
+// One colour half-sweep over the n^3/2 cells of `colour` ((i+j+k) & 1 == colour).
+// own: array holding this colour's current values; oth: the other colour's; out:
+// receives the new values of this colour.  rhs = fscale * F + lam.
+template <typename T, bool BG>
+__global__ void __launch_bounds__(256) k_half_sweep(const T* __restrict__ own, const T* __restrict__ oth,
+                                                    T* __restrict__ out, const T* __restrict__ F, T fscale, T lam,
+                                                    const uint8_t* __restrict__ kmask, const T* __restrict__ bg,
+                                                    const T* __restrict__ gap, int n, int colour, T ih2, T nu, T kap,
+                                                    T sp, T Df, T lsat_num)
+{
+    const int hn = n >> 1;
+    const size_t total = (size_t)n * n * hn;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const int m = (int)(t % hn);
+        const size_t row = t / hn;
+        const int j = (int)(row % n), k = (int)(row / n);
+        const int i = 2 * m + ((j + k + colour) & 1);
+        const size_t c = row * n + i;
+        Stencil<T> s = load_stencil(own, oth, i, j, k, n);
+        Stencil<T> b;
+        if (BG) b = load_stencil(bg, bg, i, j, k, n);
+        const T kc = (kmask && kmask[c]) ? T(0) : kap;
+        const T lsat = kc != T(0) ? lsat_num / kc : T(0);
+        Local<T> o = local_eval<T, BG>(s, b, ih2, nu, kc, fscale * F[c] + lam, lsat, gap != nullptr, gap ? gap[c] : T(0));
+        out[c] = s.c0 + local_update(o, sp, Df, ih2);
+    }
+}
+
+// ------------------------------------------------------------------ residual
+
+// r = f + lam - N (real root) or nu (L_sat - L) (floored), its floored flag, and the
+// block sums used for the gauge update and the norm.  MIXED (FP64 level 0 of the
+// defect-correction loop) also writes the FP32 copies: the plain residual -G for the
+// inner right-hand side, and the iterate as the inner background.
+template <typename T, bool BG, bool WRITE_R, bool MIXED>
+__global__ void __launch_bounds__(256) k_residual(const T* __restrict__ u, const T* __restrict__ F, T fscale, T lam,
+                                                  const uint8_t* __restrict__ kmask, const T* __restrict__ bg,
+                                                  const T* __restrict__ gap, int n, T ih2, T nu, T kap, T Df,
+                                                  T lsat_num, bool floor_piece, T* __restrict__ r,
+                                                  uint8_t* __restrict__ sat,
+                                                  double* __restrict__ partials, float* __restrict__ rplain,
+                                                  float* __restrict__ chi32, float* __restrict__ gap32)
+{
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    const size_t total = (size_t)n * n * n;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(c % n);
+        const size_t row = c / n;
+        const int j = (int)(row % n), k = (int)(row / n);
+        Stencil<T> s = load_stencil(u, u, i, j, k, n);
+        Stencil<T> b;
+        if (BG) b = load_stencil(bg, bg, i, j, k, n);
+        const bool masked = kmask && kmask[c];
+        const T kc = masked ? T(0) : kap;
+        const T lsat = kc != T(0) ? lsat_num / kc : T(0);
+        Local<T> o = local_eval<T, BG>(s, b, ih2, nu, kc, fscale * F[c] + lam, lsat, gap != nullptr, gap ? gap[c] : T(0));
+        // the floored piece exists on the finest level only; coarse levels take their
+        // pieces from the restricted mask (linear where masked, quadratic elsewhere), so
+        // their right-hand side and their smoother solve the same equation (FAS consistency)
+        const bool fl = floor_piece && (o.P != T(0)) && (o.D < Df);
+        // floored piece nu (L_sat - L) = nu g
+        const T rv = fl ? nu * o.g : -o.G;
+        if (WRITE_R) r[c] = rv;
+        if (sat) sat[c] = fl ? 1 : 0;
+        if (MIXED) {
+            rplain[c] = (float)(-o.G);
+            chi32[c] = (float)s.c0;
+            gap32[c] = (float)o.g;
+        }
+        const double d = (double)rv;
+        if (!isfinite(d)) {
+            acc[4] += 1.0;
+        } else {
+            acc[0] += d;
+            acc[2] += d * d;
+            if (!fl) {
+                acc[1] += d;
+                acc[3] += 1.0;
+            }
+        }
+    }
+    block_sums<5>(acc, partials);
+}
+
+// ------------------------------------------------------------------ transfers
+
+// Coarse cell = average of its 8 children, for the iterate (-> ur and the coarse start
+// value) and the gauge-projected residual r - gm * [unfloored]; the coarse screening mask
+// is set where at least 4 children were floored or masked.
+template <typename T>
+__global__ void __launch_bounds__(256) k_restrict_fas(const T* __restrict__ uf, const T* __restrict__ rf,
+                                                      const uint8_t* __restrict__ satf,
+                                                      const uint8_t* __restrict__ kmf, const double* __restrict__ gm_ptr,
+                                                      int nc, T* __restrict__ ur, T* __restrict__ uc,
+                                                      T* __restrict__ rc, uint8_t* __restrict__ kmc)
+{
+    const int nf = 2 * nc;
+    const size_t total = (size_t)nc * nc * nc;
+    const T gm = gm_ptr ? (T)(*gm_ptr) : T(0);
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x) {
+        const int I = (int)(c % nc);
+        const size_t row = c / nc;
+        const int J = (int)(row % nc), K = (int)(row / nc);
+        T su = T(0), sr = T(0);
+        int cnt = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int di = q & 1, dj = (q >> 1) & 1, dk = (q >> 2) & 1;
+            const size_t f = ((size_t)(2 * K + dk) * nf + (2 * J + dj)) * nf + (2 * I + di);
+            su += uf[f];
+            const bool fl = satf[f] != 0;
+            sr += fl ? rf[f] : rf[f] - gm;
+            cnt += (fl || (kmf && kmf[f])) ? 1 : 0;
+        }
+        su *= T(0.125);
+        ur[c] = su;
+        uc[c] = su;
+        rc[c] = sr * T(0.125);
+        kmc[c] = cnt >= 4 ? 1 : 0;
+    }
+}
+
+// Plain 8-child average (background field of the correction form).
+template <typename T>
+__global__ void k_restrict(const T* __restrict__ uf, int nc, T* __restrict__ uc)
+{
+    const int nf = 2 * nc;
+    const size_t total = (size_t)nc * nc * nc;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x) {
+        const int I = (int)(c % nc);
+        const size_t row = c / nc;
+        const int J = (int)(row % nc), K = (int)(row / nc);
+        T su = T(0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int di = q & 1, dj = (q >> 1) & 1, dk = (q >> 2) & 1;
+            su += uf[((size_t)(2 * K + dk) * nf + (2 * J + dj)) * nf + (2 * I + di)];
+        }
+        uc[c] = su * T(0.125);
+    }
+}
+
+// FAS right-hand side f_H = N_H(R u) + R r (no gauge term on coarse levels).
+template <typename T, bool BG>
+__global__ void __launch_bounds__(256) k_fas_rhs(const T* __restrict__ uc, const T* __restrict__ rc,
+                                                 const uint8_t* __restrict__ kmask, const T* __restrict__ bg, int n,
+                                                 T ih2, T nu, T kap, T* __restrict__ fc)
+{
+    const size_t total = (size_t)n * n * n;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(c % n);
+        const size_t row = c / n;
+        const int j = (int)(row % n), k = (int)(row / n);
+        Stencil<T> s = load_stencil(uc, uc, i, j, k, n);
+        Stencil<T> b;
+        if (BG) b = load_stencil(bg, bg, i, j, k, n);
+        const T kc = kmask[c] ? T(0) : kap;
+        Local<T> o = local_eval<T, BG>(s, b, ih2, nu, kc, T(0), T(0));
+        fc[c] = o.G + rc[c];
+    }
+}
+
+// fine += trilinear cell-centred prolongation of (uc - ur), periodic.
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong_add(const T* __restrict__ uc, const T* __restrict__ ur, int nc,
+                                                     T* __restrict__ uf)
+{
+    const int nf = 2 * nc, mc = nc - 1;
+    const size_t total = (size_t)nf * nf * nf;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(c % nf);
+        const size_t row = c / nf;
+        const int j = (int)(row % nf), k = (int)(row / nf);
+        const int P0 = i >> 1, P1 = j >> 1, P2 = k >> 1;
+        const int Q0 = (i & 1) ? ((P0 + 1) & mc) : ((P0 - 1) & mc);
+        const int Q1 = (j & 1) ? ((P1 + 1) & mc) : ((P1 - 1) & mc);
+        const int Q2 = (k & 1) ? ((P2 + 1) & mc) : ((P2 - 1) & mc);
+        T s = T(0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int ii = (q & 1) ? Q0 : P0, jj = (q & 2) ? Q1 : P1, kk = (q & 4) ? Q2 : P2;
+            const T w = ((q & 1) ? T(0.25) : T(0.75)) * ((q & 2) ? T(0.25) : T(0.75)) * ((q & 4) ? T(0.25) : T(0.75));
+            const size_t g = ((size_t)kk * nc + jj) * nc + ii;
+            s += w * (ur ? uc[g] - ur[g] : uc[g]);
+        }
+        uf[c] += s;
+    }
+}
+
+// ------------------------------------------------------------------ coarsest level
+
+// Exact-enough solve of the coarsest level (at most 8^3 cells) in one thread block, in
+// FP64 whatever the storage type: `sweeps` red-black sweeps, each followed by the gauge
+// update lambda -= sum r / #unfloored.
+template <typename T, bool BG>
+__global__ void __launch_bounds__(256) k_coarsest(T* __restrict__ u, const T* __restrict__ F, T fscale,
+                                                  const uint8_t* __restrict__ kmask, const T* __restrict__ bg, int n,
+                                                  double ih2, double nu, double kap, double eta, int sweeps,
+                                                  bool floor_piece)
+{
+    __shared__ double su[512], ss[512], sf[512], sb[512];
+    __shared__ uint8_t sk[512];
+    __shared__ double red[2][256];
+    const int cells = n * n * n, t = threadIdx.x;
+    for (int c = t; c < cells; c += blockDim.x) {
+        su[c] = (double)u[c];
+        sf[c] = (double)fscale * (double)F[c];
+        sk[c] = kmask ? kmask[c] : 0;
+        sb[c] = BG ? (double)bg[c] : 0.0;
+    }
+    __syncthreads();
+    const double sp = nu >= 0.0 ? -1.0 : 1.0;
+    const double sqDf = eta * 6.0 * fabs(nu) * ih2, Df = sqDf * sqDf;
+    const double lsat_num = 0.75 * nu * (1.0 - eta);
+    double lam = 0.0;
+    for (int it = 0; it < sweeps; ++it) {
+        for (int colour = 0; colour < 2; ++colour) {
+            for (int c = t; c < cells; c += blockDim.x) ss[c] = su[c];
+            __syncthreads();
+            for (int c = t; c < cells; c += blockDim.x) {
+                const int i = c % n, j = (c / n) % n, k = c / (n * n);
+                if (((i + j + k) & 1) != colour) continue;
+                Stencil<double> s = load_stencil<double>(ss, ss, i, j, k, n);
+                Stencil<double> b;
+                if (BG) b = load_stencil<double>(sb, sb, i, j, k, n);
+                const double kc = sk[c] ? 0.0 : kap;
+                Local<double> o = local_eval<double, BG>(s, b, ih2, nu, kc, sf[c] + lam, kc != 0.0 ? lsat_num / kc : 0.0);
+                su[c] = s.c0 + local_update(o, sp, Df, ih2);
+            }
+            __syncthreads();
+        }
+        // gauge update from the residual
+        double a0 = 0.0, a1 = 0.0;
+        for (int c = t; c < cells; c += blockDim.x) {
+            const int i = c % n, j = (c / n) % n, k = c / (n * n);
+            Stencil<double> s = load_stencil<double>(su, su, i, j, k, n);
+            Stencil<double> b;
+            if (BG) b = load_stencil<double>(sb, sb, i, j, k, n);
+            const double kc = sk[c] ? 0.0 : kap;
+            Local<double> o = local_eval<double, BG>(s, b, ih2, nu, kc, sf[c] + lam, kc != 0.0 ? lsat_num / kc : 0.0);
+            const bool fl = floor_piece && (o.P != 0.0) && (o.D < Df);
+            a0 += fl ? nu * o.g : -o.G;
+            a1 += fl ? 0.0 : 1.0;
+        }
+        red[0][t] = a0;
+        red[1][t] = a1;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (t < w) {
+                red[0][t] += red[0][t + w];
+                red[1][t] += red[1][t + w];
+            }
+            __syncthreads();
+        }
+        if (red[1][0] > 0.0) lam -= red[0][0] / red[1][0];
+        __syncthreads();
+    }
+    for (int c = t; c < cells; c += blockDim.x) u[c] = (T)su[c];
+}
+
+// ------------------------------------------------------------------ misc
+
+template <typename T>
+__global__ void k_sum(const T* __restrict__ x, size_t total, double* __restrict__ partials)
+{
+    double v[2] = {0.0, 0.0};
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x) {
+        const double d = (double)x[c];
+        v[0] += d;
+        v[1] += d * d;
+    }
+    block_sums<2>(v, partials);
+}
+
+// sum of (x - mean)^2 with the mean read from the device
+__global__ void k_sum_centred(const double* __restrict__ x, size_t total, const double* __restrict__ sums,
+                              double* __restrict__ partials)
+{
+    const double mean = sums[0] / (double)total;
+    double v[1] = {0.0};
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x) {
+        const double d = x[c] - mean;
+        v[0] += d * d;
+    }
+    block_sums<1>(v, partials);
+}
+
+template <typename T>
+__global__ void k_sub_mean(T* __restrict__ x, size_t total, const double* __restrict__ sums)
+{
+    const T mean = (T)(sums[0] / (double)total);
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x)
+        x[c] -= mean;
+}
+
+__global__ void k_add_correction(double* __restrict__ x, const float* __restrict__ e, size_t total)
+{
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x)
+        x[c] += (double)e[c];
+}
+
+// ------------------------------------------------------------------ host drivers
+
+struct Coef {
+    double nu, kap, eta, src;
+};
+
+template <typename T>
+static void sweep(pm_ctx* ctx, Level<T>& L, const T* F, T fscale, T lam, const Coef& c)
+{
+    const int n = L.n;
+    const T h2inv = (T)((double)n * (double)n);
+    const T sp = c.nu >= 0.0 ? T(-1) : T(1);
+    const double sqDf = c.eta * 6.0 * std::fabs(c.nu) * (double)n * (double)n;
+    const T lsn = (T)(0.75 * c.nu * (1.0 - c.eta));
+    const int grid = grid_for(ctx, L.cells / 2);
+    T* A = L.u[L.cur];
+    T* B = L.u[1 - L.cur];
+    const bool bg = L.bg != nullptr;
+    for (int colour = 0; colour < 2; ++colour) {
+        const T* own = A;
+        const T* oth = colour == 0 ? A : B;
+        if (bg) {
+            ctx->begin(sizeof(T) == 8 ? PM_K_SWEEP64 : PM_K_SWEEP32, L.fine, (long long)(L.cells / 2));
+            k_half_sweep<T, true><<<grid, kThreads, 0, ctx->stream>>>(own, oth, B, F, fscale, lam, L.kmask, L.bg,
+                                                                      L.gap, n, colour, h2inv, (T)c.nu, (T)c.kap, sp,
+                                                                      (T)(sqDf * sqDf), lsn);
+            ctx->end();
+        } else {
+            ctx->begin(sizeof(T) == 8 ? PM_K_SWEEP64 : PM_K_SWEEP32, L.fine, (long long)(L.cells / 2));
+            k_half_sweep<T, false><<<grid, kThreads, 0, ctx->stream>>>(own, oth, B, F, fscale, lam, L.kmask, nullptr,
+                                                                       nullptr, n, colour, h2inv, (T)c.nu, (T)c.kap,
+                                                                       sp, (T)(sqDf * sqDf), lsn);
+            ctx->end();
+        }
+    }
+    L.cur = 1 - L.cur;
+}
+
+template <typename T, bool WRITE_R, bool MIXED>
+static int residual(pm_ctx* ctx, Level<T>& L, const T* u, const T* F, T fscale, T lam, const Coef& c, float* rplain,
+                    float* chi32, float* gap32 = nullptr)
+{
+    const int n = L.n;
+    const T h2inv = (T)((double)n * (double)n);
+    const double sqDf = c.eta * 6.0 * std::fabs(c.nu) * (double)n * (double)n;
+    int grid = grid_for(ctx, L.cells);
+    if (grid > kMaxPartials) grid = kMaxPartials;
+    const T lsn = (T)(0.75 * c.nu * (1.0 - c.eta));
+    if (L.bg) {
+        ctx->begin(sizeof(T) == 8 ? PM_K_RESID64 : PM_K_RESID32, L.fine, (long long)L.cells);
+        k_residual<T, true, WRITE_R, MIXED><<<grid, kThreads, 0, ctx->stream>>>(
+            u, F, fscale, lam, L.kmask, L.bg, L.gap, n, h2inv, (T)c.nu, (T)c.kap, (T)(sqDf * sqDf), lsn, L.fine, L.r,
+            L.sat, ctx->red_partials, rplain, chi32, gap32);
+        ctx->end();
+    } else {
+        ctx->begin(sizeof(T) == 8 ? PM_K_RESID64 : PM_K_RESID32, L.fine, (long long)L.cells);
+        k_residual<T, false, WRITE_R, MIXED><<<grid, kThreads, 0, ctx->stream>>>(
+            u, F, fscale, lam, L.kmask, nullptr, nullptr, n, h2inv, (T)c.nu, (T)c.kap, (T)(sqDf * sqDf), lsn, L.fine,
+            L.r, L.sat, ctx->red_partials, rplain, chi32, gap32);
+        ctx->end();
+    }
+    ctx->begin(PM_K_REDUCE, false, 0);
+    k_finalize<<<1, 256, 0, ctx->stream>>>(ctx->red_partials, grid, ctx->red_out);
+    ctx->end();
+    return grid;
+}
+
+template <typename T>
+static void vcycle(pm_ctx* ctx, std::vector<Level<T>>& lv, int l, const T* F0, T fs0, T lam0, const Coef& c)
+{
+    Level<T>& L = lv[l];
+    const T* F = l == 0 ? F0 : L.f;
+    const T fs = l == 0 ? fs0 : T(1);
+    const T lam = l == 0 ? lam0 : T(0);
+    const int nlev = (int)lv.size();
+    if (l == nlev - 1) {
+        const double ih2 = (double)L.n * (double)L.n;
+        if (L.bg) {
+            ctx->begin(PM_K_COARSEST, false, 0);
+            k_coarsest<T, true><<<1, 256, 0, ctx->stream>>>(L.u[L.cur], F, fs, L.kmask, L.bg, L.n, ih2, c.nu, c.kap,
+                                                            c.eta, ctx->prm.coarse_sweeps, L.fine);
+            ctx->end();
+        } else {
+            ctx->begin(PM_K_COARSEST, false, 0);
+            k_coarsest<T, false><<<1, 256, 0, ctx->stream>>>(L.u[L.cur], F, fs, L.kmask, nullptr, L.n, ih2, c.nu,
+                                                             c.kap, c.eta, ctx->prm.coarse_sweeps, L.fine);
+            ctx->end();
+        }
+        return;
+    }
+    for (int s = 0; s < ctx->prm.npre; ++s) sweep(ctx, L, F, fs, lam, c);
+    residual<T, true, false>(ctx, L, L.u[L.cur], F, fs, lam, c, nullptr, nullptr);
+    Level<T>& C = lv[l + 1];
+    C.cur = 0;
+    const int gc = grid_for(ctx, C.cells);
+    ctx->begin(PM_K_TRANSFER, false, 0);
+    k_restrict_fas<T><<<gc, kThreads, 0, ctx->stream>>>(L.u[L.cur], L.r, L.sat, L.kmask, ctx->red_out + 8, C.n, C.ur,
+                                                        C.u[0], C.r, C.kmask);
+    ctx->end();
+    const T ih2c = (T)((double)C.n * (double)C.n);
+    if (C.bg) {
+        ctx->begin(PM_K_TRANSFER, false, 0);
+        k_fas_rhs<T, true><<<gc, kThreads, 0, ctx->stream>>>(C.u[0], C.r, C.kmask, C.bg, C.n, ih2c, (T)c.nu,
+                                                             (T)c.kap, C.f);
+        ctx->end();
+    } else {
+        ctx->begin(PM_K_TRANSFER, false, 0);
+        k_fas_rhs<T, false><<<gc, kThreads, 0, ctx->stream>>>(C.u[0], C.r, C.kmask, nullptr, C.n, ih2c, (T)c.nu,
+                                                              (T)c.kap, C.f);
+        ctx->end();
+    }
+    vcycle(ctx, lv, l + 1, F0, fs0, lam0, c);
+    ctx->begin(PM_K_TRANSFER, false, 0);
+    k_prolong_add<T><<<grid_for(ctx, L.cells), kThreads, 0, ctx->stream>>>(C.u[C.cur], C.ur, C.n, L.u[L.cur]);
+    ctx->end();
+    for (int s = 0; s < ctx->prm.npost; ++s) sweep(ctx, L, F, fs, lam, c);
+}
+
+template <typename T>
+static void recentre(pm_ctx* ctx, T* x, size_t cells)
+{
+    int grid = grid_for(ctx, cells);
+    if (grid > kMaxPartials) grid = kMaxPartials;
+    ctx->begin(PM_K_REDUCE, false, 0);
+    k_sum<T><<<grid, kThreads, 0, ctx->stream>>>(x, cells, ctx->red_partials);
+    ctx->end();
+    ctx->begin(PM_K_REDUCE, false, 0);
+    k_finalize<<<1, 256, 0, ctx->stream>>>(ctx->red_partials, grid, ctx->red_out + 16);
+    ctx->end();
+    ctx->begin(PM_K_REDUCE, false, 0);
+    k_sub_mean<T><<<grid_for(ctx, cells), kThreads, 0, ctx->stream>>>(x, cells, ctx->red_out + 16);
+    ctx->end();
+}
+
+static pm_status read_sums(pm_ctx* ctx, int count)
+{
+    PM_CUDA(cudaMemcpyAsync(ctx->host_out, ctx->red_out, sizeof(double) * count, cudaMemcpyDeviceToHost, ctx->stream));
+    PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    return PM_OK;
+}
+
+// |f - <f>|_2 for f = src * delta
+static pm_status source_norm(pm_ctx* ctx, const double* delta, size_t cells, double src, double* out)
+{
+    int grid = grid_for(ctx, cells);
+    if (grid > kMaxPartials) grid = kMaxPartials;
+    ctx->begin(PM_K_REDUCE, false, 0);
+    k_sum<double><<<grid, kThreads, 0, ctx->stream>>>(delta, cells, ctx->red_partials);
+    ctx->end();
+    ctx->begin(PM_K_REDUCE, false, 0);
+    k_finalize<<<1, 256, 0, ctx->stream>>>(ctx->red_partials, grid, ctx->red_out + 32);
+    ctx->end();
+    ctx->begin(PM_K_REDUCE, false, 0);
+    k_sum_centred<<<grid, kThreads, 0, ctx->stream>>>(delta, cells, ctx->red_out + 32, ctx->red_partials);
+    ctx->end();
+    ctx->begin(PM_K_REDUCE, false, 0);
+    k_finalize<<<1, 256, 0, ctx->stream>>>(ctx->red_partials, grid, ctx->red_out + 48);
+    ctx->end();
+    PM_CUDA(cudaMemcpyAsync(ctx->host_out, ctx->red_out + 48, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    *out = std::fabs(src) * std::sqrt(ctx->host_out[0]);
+    return PM_OK;
+}
+
+pm_status mg_solve(pm_ctx* ctx, const double* delta, int n, const pm_coeffs& cf, double tol, double* phi,
+                   pm_solve_info* info)
+{
+    const pm_params& P = ctx->prm;
+    pm_solve_info local{};
+    pm_solve_info* inf = info ? info : &local;
+    *inf = pm_solve_info{};
+    inf->unstable_nu = cf.nu <= 0.0 ? 1 : 0;
+    const size_t cells = (size_t)n * n * n;
+    if (cf.xi == 0.0) {  // no coupling: chi = 0 solves the equation exactly
+        PM_CUDA(cudaMemsetAsync(phi, 0, cells * sizeof(double), ctx->stream));
+        inf->status = PM_OK;
+        return PM_OK;
+    }
+    if (cf.nu == 0.0 || !std::isfinite(cf.nu) || !std::isfinite(cf.kappa)) {
+        ctx->set_error("nu = 0: the chi operator is degenerate");
+        return PM_ERR_INVALID_ARG;
+    }
+    Workspace* w = nullptr;
+    PM_TRY(get_workspace(ctx, n, &w));
+    const bool mixed = P.precision == 1;
+    PM_TRY(ensure_mg(ctx, w, mixed));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, ctx->stream);
+    Coef c{cf.nu, cf.kappa, P.eta, cf.src};
+    double fnorm = 0.0;
+    PM_TRY(source_norm(ctx, delta, cells, cf.src, &fnorm));
+    Level<double>& L0 = w->d[0];
+    L0.cur = 0;
+    PM_CUDA(cudaMemcpyAsync(L0.u[0], phi, cells * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    double lam = 0.0, rr = 0.0;
+    int cyc = 0;
+    pm_status st = PM_ERR_NOCONV;
+    for (;;) {
+        if (mixed)
+            residual<double, false, true>(ctx, L0, L0.u[L0.cur], delta, cf.src, lam, c, w->rplain, w->s[0].bg,
+                                          w->s[0].gap);
+        else
+            residual<double, false, false>(ctx, L0, L0.u[L0.cur], delta, cf.src, lam, c, nullptr, nullptr);
+        PM_TRY(read_sums(ctx, 9));
+        const double* h = ctx->host_out;
+        const double gm = h[3] > 0.0 ? h[0] / h[3] : 0.0;
+        lam -= gm;
+        const double r2 = h[2] - 2.0 * gm * h[1] + gm * gm * h[3];
+        rr = fnorm > 0.0 ? std::sqrt(r2 > 0.0 ? r2 : 0.0) / fnorm : std::sqrt(r2 > 0.0 ? r2 : 0.0);
+        inf->floored_cells = (long long)((double)cells - h[3]);
+        if (cyc < 64) inf->rel_res_hist[cyc] = rr;
+        if (h[4] > 0.0 || !std::isfinite(rr)) {
+            st = PM_ERR_NONFINITE;
+            ctx->set_error("non-finite residual");
+            break;
+        }
+        if (rr <= tol || fnorm == 0.0) {
+            st = PM_OK;
+            break;
+        }
+        if (cyc >= P.max_cycles) {
+            ctx->set_error("max_cycles reached before the tolerance");
+            break;
+        }
+        if (mixed) {
+            // inner FP32 FAS V-cycle on the correction e, background chi32, rhs rplain - gm
+            std::vector<Level<float>>& s = w->s;
+            for (size_t l = 0; l + 1 < s.size(); ++l) {
+                ctx->begin(PM_K_TRANSFER, false, 0);
+                k_restrict<float><<<grid_for(ctx, s[l + 1].cells), kThreads, 0, ctx->stream>>>(s[l].bg, s[l + 1].n,
+                                                                                               s[l + 1].bg);
+                ctx->end();
+            }
+            s[0].cur = 0;
+            PM_CUDA(cudaMemsetAsync(s[0].u[0], 0, cells * sizeof(float), ctx->stream));
+            vcycle<float>(ctx, s, 0, w->rplain, 1.0f, (float)(-gm), c);
+            ctx->begin(PM_K_REDUCE, false, 0);
+            k_add_correction<<<grid_for(ctx, cells), kThreads, 0, ctx->stream>>>(L0.u[L0.cur], s[0].u[s[0].cur],
+                                                                                 cells);
+            ctx->end();
+        } else {
+            vcycle<double>(ctx, w->d, 0, delta, cf.src, lam, c);
+        }
+        recentre<double>(ctx, L0.u[L0.cur], cells);
+        ++cyc;
+    }
+    PM_CUDA(cudaMemcpyAsync(phi, L0.u[L0.cur], cells * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    cudaEventRecord(e1, ctx->stream);
+    PM_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    inf->cycles = cyc;
+    inf->rel_res = rr;
+    inf->lambda = lam;
+    inf->ms_total = ms;
+    inf->status = st;
+    return st;
+}
+
+}  // namespace pmeft
+
+using namespace pmeft;
+
+// ------------------------------------------------------------------ single-operation ABI
+
+static pm_status check_mg_args(pm_ctx* ctx, int n)
+{
+    if (!ctx) return PM_ERR_INVALID_ARG;
+    if (!valid_n(n)) {
+        ctx->set_error("n must be a power of two >= 8");
+        return PM_ERR_INVALID_ARG;
+    }
+    return PM_OK;
+}
+
+extern "C" pm_status pm_mg_sweep(pm_ctx* ctx, double* u, const double* f, double lambda, int n, double nu,
+                                 double kappa, double eta, const unsigned char* kmask)
+{
+    PM_TRY(check_mg_args(ctx, n));
+    if (!u || !f) return PM_ERR_INVALID_ARG;
+    Workspace* w = nullptr;
+    PM_TRY(get_workspace(ctx, n, &w));
+    PM_TRY(ensure_mg(ctx, w, false));
+    Level<double> L = w->d[0];  // borrow the buffers, with the caller's mask
+    L.kmask = (uint8_t*)kmask;
+    L.bg = nullptr;
+    L.cur = 0;
+    const size_t cells = L.cells;
+    PM_CUDA(cudaMemcpyAsync(L.u[0], u, cells * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    Coef c{nu, kappa, eta, 1.0};
+    sweep<double>(ctx, L, f, 1.0, lambda, c);
+    PM_CUDA(cudaMemcpyAsync(u, L.u[L.cur], cells * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    PM_CUDA(cudaGetLastError());
+    return PM_OK;
+}
+
+extern "C" pm_status pm_mg_residual(pm_ctx* ctx, const double* u, const double* f, double lambda, int n, double nu,
+                                    double kappa, double eta, const unsigned char* kmask, double* r,
+                                    unsigned char* floored)
+{
+    PM_TRY(check_mg_args(ctx, n));
+    if (!u || !f || !r) return PM_ERR_INVALID_ARG;
+    Workspace* w = nullptr;
+    PM_TRY(get_workspace(ctx, n, &w));
+    PM_TRY(ensure_mg(ctx, w, false));
+    Level<double> L = w->d[0];
+    L.kmask = (uint8_t*)kmask;
+    L.bg = nullptr;
+    L.r = r;
+    L.sat = floored ? floored : w->d[0].sat;
+    Coef c{nu, kappa, eta, 1.0};
+    residual<double, true, false>(ctx, L, u, f, 1.0, lambda, c, nullptr, nullptr);
+    PM_CUDA(cudaGetLastError());
+    return PM_OK;
+}
+
+extern "C" pm_status pm_mg_restrict(pm_ctx* ctx, const double* fine, int n, double* coarse)
+{
+    PM_TRY(check_mg_args(ctx, n));
+    if (!fine || !coarse) return PM_ERR_INVALID_ARG;
+    const int nc = n / 2;
+    ctx->begin(PM_K_TRANSFER, false, 0);
+    k_restrict<double><<<grid_for(ctx, (size_t)nc * nc * nc), kThreads, 0, ctx->stream>>>(fine, nc, coarse);
+    ctx->end();
+    PM_CUDA(cudaGetLastError());
+    return PM_OK;
+}
+
+extern "C" pm_status pm_mg_prolong_add(pm_ctx* ctx, const double* coarse, int n, double* fine)
+{
+    PM_TRY(check_mg_args(ctx, n));
+    if (!fine || !coarse) return PM_ERR_INVALID_ARG;
+    const int nc = n / 2;
+    ctx->begin(PM_K_TRANSFER, false, 0);
+    k_prolong_add<double><<<grid_for(ctx, (size_t)n * n * n), kThreads, 0, ctx->stream>>>(coarse, nullptr, nc, fine);
+    ctx->end();
+    PM_CUDA(cudaGetLastError());
+    return PM_OK;
+}
+
+extern "C" pm_status scalar_mg_solve(pm_ctx* ctx, const double* delta, int n, double alpha_B0, double alpha_M0,
+                                     double a, double tol, double* phi_inout, pm_solve_info* info)
+{
+    PM_TRY(check_mg_args(ctx, n));
+    if (!delta || !phi_inout || !(tol > 0.0) || !(a > 0.0)) {
+        ctx->set_error("scalar_mg_solve: null buffer, tol <= 0 or a <= 0");
+        return PM_ERR_INVALID_ARG;
+    }
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return PM_ERR_CUDA;
+    pm_coeffs cf;
+    coefficients(alpha_B0, alpha_M0, a, ctx->prm.omega_m0, ctx->prm.include_dot_alphaB, &cf);
+    return mg_solve(ctx, delta, n, cf, tol, phi_inout, info);
+}

@@ -1,0 +1,305 @@
+// pm.cu -- particle-mesh steps around the chi solve (arXiv 2604.15434, Sec. 3.1, 3.5, 3.6):
+// CIC deposit in 2^40 fixed point, the FFT Poisson solve of Eq. phipsi_mod, the five-point
+// gradient of Psi = Psi_N + (alpha_B - alpha_M) chi interpolated to particles (Eq. force),
+// and one kick-drift.
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace pmeft {
+
+// Cell-centred CIC weights of one coordinate; every operation rounded as written
+// (no contraction) so that the weights are identical on every machine.
+__device__ __forceinline__ void cic_1d(double x, int n, int& i0, int& i1, double& w0, double& w1)
+{
+    const double u = __dmul_rn(x, (double)n);
+    const double s = __dsub_rn(u, 0.5);
+    const double fl = floor(s);
+    const double d = __dsub_rn(s, fl);
+    const int i = (int)fl;
+    i0 = i & (n - 1);
+    i1 = (i + 1) & (n - 1);
+    w0 = __dsub_rn(1.0, d);
+    w1 = d;
+}
+
+__global__ void __launch_bounds__(256) k_deposit(const double* __restrict__ pos, long long np, int n,
+                                                 unsigned long long* __restrict__ acc)
+{
+    const double scale = 1099511627776.0;  // 2^40
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (long long)gridDim.x * blockDim.x) {
+        int ix[2], iy[2], iz[2];
+        double wx[2], wy[2], wz[2];
+        cic_1d(pos[p], n, ix[0], ix[1], wx[0], wx[1]);
+        cic_1d(pos[np + p], n, iy[0], iy[1], wy[0], wy[1]);
+        cic_1d(pos[2 * np + p], n, iz[0], iz[1], wz[0], wz[1]);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int a = c & 1, b = (c >> 1) & 1, e = (c >> 2) & 1;
+            const double w = __dmul_rn(__dmul_rn(wx[a], wy[b]), wz[e]);
+            const long long q = __double2ll_rn(__dmul_rn(w, scale));
+            atomicAdd(&acc[((size_t)iz[e] * n + iy[b]) * n + ix[a]], (unsigned long long)q);
+        }
+    }
+}
+
+// delta = acc 2^-40 (n^3/np) - 1; a negative accumulator means the int64 capacity
+// (2^23 particles at full weight in one cell) was exceeded.
+__global__ void k_density(const long long* __restrict__ acc, size_t cells, double fac, double* __restrict__ delta,
+                          int* __restrict__ flag)
+{
+    const double inv = 1.0 / 1099511627776.0;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < cells; c += (size_t)gridDim.x * blockDim.x) {
+        const long long a = acc[c];
+        if (a < 0) flag[0] = 1;
+        delta[c] = __dsub_rn(__dmul_rn(__dmul_rn((double)a, inv), fac), 1.0);
+    }
+}
+
+// Multiply the spectrum by fac / lambda_k with lambda_k = -(4/h^2) sum sin^2(pi m/n), the
+// 7-point Laplacian's eigenvalues; the zero mode is set to 0.  Also folds in 1/n^3.
+__global__ void k_green(double2* __restrict__ spec, int n, double fac)
+{
+    const int nh = n / 2 + 1;
+    const size_t total = (size_t)n * n * nh;
+    const double h2inv = (double)n * (double)n;
+    const double norm = 1.0 / ((double)n * (double)n * (double)n);
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const int mx = (int)(t % nh);
+        const size_t row = t / nh;
+        const int my = (int)(row % n), mz = (int)(row / n);
+        const double sx = sinpi((double)mx / n), sy = sinpi((double)my / n), sz = sinpi((double)mz / n);
+        const double lam = -4.0 * h2inv * (sx * sx + sy * sy + sz * sz);
+        double2 v = spec[t];
+        if (t == 0) {
+            v.x = 0.0;
+            v.y = 0.0;
+        } else {
+            const double g = fac * norm / lam;
+            v.x *= g;
+            v.y *= g;
+        }
+        spec[t] = v;
+    }
+}
+
+// g = -grad(psiN + xi chi) at each particle: for every one of the 8 CIC corners (in the
+// deposit's corner order) the five-point difference (-f+2 + 8 f+1 - 8 f-1 + f-2)/(12 h) per
+// axis, weighted by the corner's CIC weight.  No force grid is written.
+__global__ void __launch_bounds__(256) k_force(const double* __restrict__ psiN, const double* __restrict__ chi,
+                                               double xi, int n, const double* __restrict__ pos, long long np,
+                                               double* __restrict__ acc)
+{
+    const int m = n - 1;
+    const double inv12h = (double)n / 12.0;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (long long)gridDim.x * blockDim.x) {
+        int ix[2], iy[2], iz[2];
+        double wx[2], wy[2], wz[2];
+        cic_1d(pos[p], n, ix[0], ix[1], wx[0], wx[1]);
+        cic_1d(pos[np + p], n, iy[0], iy[1], wy[0], wy[1]);
+        cic_1d(pos[2 * np + p], n, iz[0], iz[1], wz[0], wz[1]);
+        auto psi = [&](int i, int j, int k) {
+            const size_t c = ((size_t)(k & m) * n + (j & m)) * n + (i & m);
+            return chi ? __dadd_rn(psiN[c], __dmul_rn(xi, chi[c])) : psiN[c];
+        };
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int a = c & 1, b = (c >> 1) & 1, e = (c >> 2) & 1;
+            const int i = ix[a], j = iy[b], k = iz[e];
+            const double w = __dmul_rn(__dmul_rn(wx[a], wy[b]), wz[e]);
+            const double gx = (-psi(i + 2, j, k) + 8.0 * psi(i + 1, j, k) - 8.0 * psi(i - 1, j, k) + psi(i - 2, j, k)) * inv12h;
+            const double gy = (-psi(i, j + 2, k) + 8.0 * psi(i, j + 1, k) - 8.0 * psi(i, j - 1, k) + psi(i, j - 2, k)) * inv12h;
+            const double gz = (-psi(i, j, k + 2) + 8.0 * psi(i, j, k + 1) - 8.0 * psi(i, j, k - 1) + psi(i, j, k - 2)) * inv12h;
+            s0 += w * -gx;
+            s1 += w * -gy;
+            s2 += w * -gz;
+        }
+        acc[p] = s0;
+        acc[np + p] = s1;
+        acc[2 * np + p] = s2;
+    }
+}
+
+// v += g dt; x = frac(x + v dt), each product and sum rounded as written.
+__global__ void k_kick_drift(double* __restrict__ pos, double* __restrict__ vel, const double* __restrict__ acc,
+                             long long total, double dt)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const double v = __dadd_rn(vel[i], __dmul_rn(acc[i], dt));
+        vel[i] = v;
+        double x = __dadd_rn(pos[i], __dmul_rn(v, dt));
+        x = __dsub_rn(x, floor(x));
+        if (x >= 1.0) x = 0.0;
+        pos[i] = x;
+    }
+}
+
+pm_status deposit(pm_ctx* ctx, const double* pos, long long np, int n, long long* acc)
+{
+    const size_t cells = (size_t)n * n * n;
+    PM_CUDA(cudaMemsetAsync(acc, 0, cells * sizeof(long long), ctx->stream));
+    ctx->begin(PM_K_PM, false, 0);
+    k_deposit<<<grid_for(ctx, (size_t)np), kThreads, 0, ctx->stream>>>(pos, np, n, (unsigned long long*)acc);
+    ctx->end();
+    PM_CUDA(cudaGetLastError());
+    return PM_OK;
+}
+
+pm_status density(pm_ctx* ctx, const long long* acc, int n, long long np, double* delta)
+{
+    const size_t cells = (size_t)n * n * n;
+    PM_CUDA(cudaMemsetAsync(ctx->flag, 0, sizeof(int), ctx->stream));
+    ctx->begin(PM_K_PM, false, 0);
+    k_density<<<grid_for(ctx, cells), kThreads, 0, ctx->stream>>>(acc, cells, (double)cells / (double)np, delta,
+                                                                   ctx->flag);
+    ctx->end();
+    int hflag = 0;
+    PM_CUDA(cudaMemcpyAsync(&hflag, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (hflag) {
+        ctx->set_error("fixed-point deposit overflow (more than 2^23 particles in one cell)");
+        return PM_ERR_OVERFLOW;
+    }
+    return PM_OK;
+}
+
+pm_status poisson(pm_ctx* ctx, const double* delta, int n, double fac, double* psi)
+{
+    Workspace* w = nullptr;
+    PM_TRY(get_workspace(ctx, n, &w));
+    PM_TRY(ensure_fft(ctx, w));
+    ctx->prof.launches[PM_K_PM] += 2;  // the two cuFFT executions (library kernels)
+    if (cufftExecD2Z(w->plan_r2c, (cufftDoubleReal*)delta, (cufftDoubleComplex*)w->spec) != CUFFT_SUCCESS) {
+        ctx->set_error("cufftExecD2Z failed");
+        return PM_ERR_CUDA;
+    }
+    ctx->begin(PM_K_PM, false, 0);
+    k_green<<<grid_for(ctx, (size_t)n * n * (n / 2 + 1)), kThreads, 0, ctx->stream>>>(w->spec, n, fac);
+    ctx->end();
+    if (cufftExecZ2D(w->plan_c2r, (cufftDoubleComplex*)w->spec, (cufftDoubleReal*)psi) != CUFFT_SUCCESS) {
+        ctx->set_error("cufftExecZ2D failed");
+        return PM_ERR_CUDA;
+    }
+    PM_CUDA(cudaGetLastError());
+    return PM_OK;
+}
+
+pm_status interp_force(pm_ctx* ctx, const double* psiN, const double* chi, double xi, int n, const double* pos,
+                       long long np, double* acc)
+{
+    ctx->begin(PM_K_PM, false, 0);
+    k_force<<<grid_for(ctx, (size_t)np), kThreads, 0, ctx->stream>>>(psiN, chi, xi, n, pos, np, acc);
+    ctx->end();
+    PM_CUDA(cudaGetLastError());
+    return PM_OK;
+}
+
+pm_status kick_drift(pm_ctx* ctx, double* pos, double* vel, const double* acc, long long np, double dt)
+{
+    ctx->begin(PM_K_PM, false, 0);
+    k_kick_drift<<<grid_for(ctx, (size_t)(3 * np)), kThreads, 0, ctx->stream>>>(pos, vel, acc, 3 * np, dt);
+    ctx->end();
+    PM_CUDA(cudaGetLastError());
+    return PM_OK;
+}
+
+}  // namespace pmeft
+
+using namespace pmeft;
+
+static pm_status check_common(pm_ctx* ctx, int n)
+{
+    if (!ctx) return PM_ERR_INVALID_ARG;
+    if (!valid_n(n)) {
+        ctx->set_error("n must be a power of two >= 8");
+        return PM_ERR_INVALID_ARG;
+    }
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return PM_ERR_CUDA;
+    return PM_OK;
+}
+
+extern "C" pm_status pm_deposit_cic_fixed(pm_ctx* ctx, const double* pos, long long np, int n, long long* acc)
+{
+    PM_TRY(check_common(ctx, n));
+    if (!pos || !acc || np < 1) {
+        ctx->set_error("pm_deposit_cic: null buffer or np < 1");
+        return PM_ERR_INVALID_ARG;
+    }
+    return deposit(ctx, pos, np, n, acc);
+}
+
+extern "C" pm_status pm_deposit_cic(pm_ctx* ctx, const double* pos, long long np, int n, double* delta)
+{
+    PM_TRY(check_common(ctx, n));
+    if (!pos || !delta || np < 1) {
+        ctx->set_error("pm_deposit_cic: null buffer or np < 1");
+        return PM_ERR_INVALID_ARG;
+    }
+    Workspace* w = nullptr;
+    PM_TRY(get_workspace(ctx, n, &w));
+    if (!w->acc) PM_CUDA(cudaMalloc(&w->acc, (size_t)n * n * n * sizeof(long long)));
+    PM_TRY(deposit(ctx, pos, np, n, w->acc));
+    return density(ctx, w->acc, n, np, delta);
+}
+
+extern "C" pm_status poisson_solve(pm_ctx* ctx, const double* delta, int n, double a, double alpha_M0, double* psi_N)
+{
+    PM_TRY(check_common(ctx, n));
+    if (!delta || !psi_N || delta == psi_N || !(a > 0.0)) {
+        ctx->set_error("poisson_solve: null or aliased buffer, or a <= 0");
+        return PM_ERR_INVALID_ARG;
+    }
+    pm_coeffs cf;
+    coefficients(0.0, alpha_M0, a, ctx->prm.omega_m0, ctx->prm.include_dot_alphaB, &cf);
+    return poisson(ctx, delta, n, cf.poisson_fac, psi_N);
+}
+
+extern "C" pm_status force_interp(pm_ctx* ctx, const double* psi_N, const double* phi, int n, double alpha_B0,
+                                  double alpha_M0, double a, const double* pos, long long np, double* acc)
+{
+    PM_TRY(check_common(ctx, n));
+    if (!psi_N || !pos || !acc || np < 1 || !(a > 0.0)) {
+        ctx->set_error("force_interp: null buffer, np < 1 or a <= 0");
+        return PM_ERR_INVALID_ARG;
+    }
+    pm_coeffs cf;
+    coefficients(alpha_B0, alpha_M0, a, ctx->prm.omega_m0, ctx->prm.include_dot_alphaB, &cf);
+    return interp_force(ctx, psi_N, phi, cf.xi, n, pos, np, acc);
+}
+
+extern "C" pm_status pm_step(pm_ctx* ctx, double* pos, double* vel, long long np, int n, double alpha_B0,
+                             double alpha_M0, double a, double dt, double tol, double* phi_state, pm_solve_info* info)
+{
+    PM_TRY(check_common(ctx, n));
+    if (!pos || !vel || !phi_state || np < 1 || !(a > 0.0) || !(tol > 0.0)) {
+        ctx->set_error("pm_step: null buffer, np < 1, a <= 0 or tol <= 0");
+        return PM_ERR_INVALID_ARG;
+    }
+    Workspace* w = nullptr;
+    PM_TRY(get_workspace(ctx, n, &w));
+    const size_t cells = (size_t)n * n * n;
+    if (!w->acc) PM_CUDA(cudaMalloc(&w->acc, cells * sizeof(long long)));
+    if (!w->delta) PM_CUDA(cudaMalloc(&w->delta, cells * sizeof(double)));
+    if (!w->psi) PM_CUDA(cudaMalloc(&w->psi, cells * sizeof(double)));
+    pm_coeffs cf;
+    coefficients(alpha_B0, alpha_M0, a, ctx->prm.omega_m0, ctx->prm.include_dot_alphaB, &cf);
+    PM_TRY(deposit(ctx, pos, np, n, w->acc));
+    PM_TRY(density(ctx, w->acc, n, np, w->delta));
+    PM_TRY(poisson(ctx, w->delta, n, cf.poisson_fac, w->psi));
+    pm_status st = mg_solve(ctx, w->delta, n, cf, tol, phi_state, info);
+    if (st != PM_OK) return st;
+    // the acceleration goes into the (now free) fixed-point grid's storage when it fits
+    double* acc = nullptr;
+    const size_t need = (size_t)3 * np * sizeof(double);
+    if (need <= cells * sizeof(long long)) {
+        acc = (double*)w->acc;
+    } else {
+        PM_CUDA(cudaMallocAsync(&acc, need, ctx->stream));
+    }
+    PM_TRY(interp_force(ctx, w->psi, phi_state, cf.xi, n, pos, np, acc));
+    PM_TRY(kick_drift(ctx, pos, vel, acc, np, dt));
+    if ((void*)acc != (void*)w->acc) PM_CUDA(cudaFreeAsync(acc, ctx->stream));
+    PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    return PM_OK;
+}

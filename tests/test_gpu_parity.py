@@ -1,0 +1,242 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the CPU oracle.
+
+Tolerances (the benchmark spec): deposit bit-exact; FP64 chi within 1e-10 relative L2 of the
+oracle when both are converged to relative residual 1e-13; the mixed-precision path
+reaches the requested residual with chi within 1e-6 relative L2 and forces within 1e-5.
+Single kernels (one sweep, residual, transfers, Poisson, force) are compared to
+1e-12, the FP64 rounding of a few dozen operations.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2604_15434_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def cu(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device=DEV, dtype=dtype)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def c1_particles():
+    return synth.zeldovich_particles(32, -1.5, 1.0, 1001, nyquist_cutoff=True)
+
+
+# ------------------------------------------------------------------ deposit
+
+
+@pytest.mark.parametrize("npart", [1, 7, 4099, 32 ** 3])
+def test_deposit_bit_exact(gpu_lib, npart):
+    rng = np.random.default_rng(npart)
+    pos = rng.random((3, npart)) if npart != 32 ** 3 else synth.zeldovich_particles(32, -1.5, 1.0, 1001, True)
+    for n in (8, 32):
+        acc = gpu_lib.pm_deposit_cic_fixed(cu(pos), n).cpu().numpy()
+        assert np.array_equal(acc, O.deposit_cic(pos, n))
+        delta = gpu_lib.pm_deposit_cic(cu(pos), n).cpu().numpy()
+        assert np.array_equal(delta, O.density(O.deposit_cic(pos, n), npart))
+
+
+def test_deposit_edge_positions(gpu_lib):
+    """Particles on cell faces, at 0 and just below 1 (wrap on every axis)."""
+    n = 16
+    vals = np.array([0.0, 1.0 / n, 0.5 / n, 1.0 - 1e-16, 0.5, 15.5 / n, np.nextafter(1.0, 0.0)])
+    pos = np.stack(np.meshgrid(vals, vals, vals, indexing="ij")).reshape(3, -1)
+    acc = gpu_lib.pm_deposit_cic_fixed(cu(pos), n).cpu().numpy()
+    assert np.array_equal(acc, O.deposit_cic(pos, n))
+
+
+def test_deposit_order_independent_on_gpu(gpu_lib, c1_particles):
+    perm = np.random.default_rng(5).permutation(c1_particles.shape[1])
+    a = gpu_lib.pm_deposit_cic_fixed(cu(c1_particles), 32).cpu().numpy()
+    b = gpu_lib.pm_deposit_cic_fixed(cu(c1_particles[:, perm]), 32).cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+# ------------------------------------------------------------------ single multigrid operations
+
+
+def _sweep_inputs(n, seed, amp):
+    rng = np.random.default_rng(seed)
+    d = synth.lognormal_delta(n, -2.0, 1.5, seed)
+    c = O.coefficients(-0.5, 0.0, 1.0)
+    f = O.source(d, c)
+    u = amp * rng.standard_normal((n, n, n)) / n ** 2
+    return u, f, c
+
+
+@pytest.mark.parametrize("n", [8, 16, 32])
+def test_one_sweep_matches_oracle(gpu_lib, n):
+    u, f, c = _sweep_inputs(n, 100 + n, 0.5)
+    eta = O.ETA_DEFAULT
+    want = O.smooth_sweep(u, f, 0.013, c["nu"], c["kappa"], eta)
+    got = gpu_lib.pm_mg_sweep(cu(u), cu(f), 0.013, c["nu"], c["kappa"], eta).cpu().numpy()
+    scale = np.abs(want).max()
+    assert np.abs(got - want).max() <= 1e-12 * scale
+    _, fl = O.residual(want, f, 0.0, c["nu"], c["kappa"], eta)
+    assert fl.sum() > 0  # the floored branch was exercised
+
+
+def test_one_sweep_with_mask_and_nu_negative(gpu_lib):
+    n = 16
+    u, f, _ = _sweep_inputs(n, 7, 0.5)
+    c = O.coefficients(-2.0, 0.5, 1.0)
+    km = (np.random.default_rng(3).random((n, n, n)) < 0.3).astype(np.uint8)
+    want = O.smooth_sweep(u, f, -0.02, c["nu"], c["kappa"], 0.35, kmask=km)
+    got = gpu_lib.pm_mg_sweep(cu(u), cu(f), -0.02, c["nu"], c["kappa"], 0.35, kmask=cu(km, torch.uint8)).cpu().numpy()
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_residual_matches_oracle(gpu_lib):
+    n = 16
+    u, f, c = _sweep_inputs(n, 11, 1.0)
+    for _ in range(3):
+        u = O.smooth_sweep(u, f, 0.0, c["nu"], c["kappa"], 0.35)
+    r_o, fl_o = O.residual(u, f, 0.004, c["nu"], c["kappa"], 0.35)
+    r_g, fl_g = gpu_lib.pm_mg_residual(cu(u), cu(f), 0.004, c["nu"], c["kappa"], 0.35)
+    r_g, fl_g = r_g.cpu().numpy(), fl_g.cpu().numpy()
+    same = fl_o == fl_g
+    assert same.mean() > 0.999 and fl_o.sum() > 0
+    assert np.abs(r_g - r_o)[same].max() <= 1e-10 * np.abs(r_o).max()
+
+
+def test_transfers_match_oracle(gpu_lib):
+    rng = np.random.default_rng(4)
+    fine = rng.standard_normal((32, 32, 32))
+    coarse = rng.standard_normal((16, 16, 16))
+    assert np.abs(gpu_lib.pm_mg_restrict(cu(fine)).cpu().numpy() - O.restrict(fine)).max() < 1e-15
+    got = gpu_lib.pm_mg_prolong_add(cu(coarse), cu(fine)).cpu().numpy()
+    assert np.abs(got - O.prolong_add(coarse, fine)).max() < 1e-14
+
+
+# ------------------------------------------------------------------ Poisson and force
+
+
+def test_poisson_matches_oracle(gpu_lib, c1_particles):
+    for n, aM0, a in ((32, 0.0, 1.0), (64, 0.2, 0.6)):
+        d = synth.lognormal_delta(n, -2.0, 1.0, 9 + n)
+        want = O.poisson_fft(d, O.coefficients(0.0, aM0, a), a)
+        got = gpu_lib.poisson_solve(cu(d), a, aM0).cpu().numpy()
+        assert rel(got, want) < 1e-12
+
+
+def test_force_matches_oracle(gpu_lib, c1_particles):
+    n = 32
+    rng = np.random.default_rng(8)
+    psi = rng.standard_normal((n, n, n))
+    chi = rng.standard_normal((n, n, n))
+    pos = np.concatenate([c1_particles, rng.random((3, 1001))], axis=1)  # ragged count
+    c = O.coefficients(-1.0, 0.2, 1.0)
+    want = O.interp_cic(O.accel_grid(psi, chi, c["xi"], n), pos)
+    got = gpu_lib.force_interp(cu(psi), cu(chi), -1.0, 0.2, 1.0, cu(pos)).cpu().numpy()
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+# ------------------------------------------------------------------ solves
+
+
+def _c1_delta(c1_particles):
+    return O.density(O.deposit_cic(c1_particles, 32), c1_particles.shape[1])
+
+
+@pytest.mark.parametrize("case", ["c1", "logn-0.5,0", "logn-2,0.5", "logn-2,0"])
+def test_fp64_solve_matches_oracle(gpu_lib, c1_particles, case):
+    if case == "c1":
+        d, aB0, aM0, a = _c1_delta(c1_particles), -0.5, 0.0, 1.0
+    else:
+        aB0, aM0 = map(float, case[4:].split(","))
+        d, a = synth.lognormal_delta(32, -2.0, 1.5, 1003), 1.0
+    want, info_o, st = O.scalar_solve(d, aB0, aM0, a, 1e-13)
+    assert st == 0
+    ctx = gpu_lib.Context(precision=0, max_cycles=200)
+    got, info = gpu_lib.scalar_mg_solve(cu(d), aB0, aM0, a, 1e-13, ctx=ctx)
+    assert info["rel_res"] <= 1e-13
+    assert rel(got.cpu().numpy(), want) < 1e-10, (info, info_o["cycles"])
+
+
+@pytest.mark.parametrize("case", ["c1", "logn-0.5,0", "logn-2,0.5"])
+def test_mixed_precision_solve(gpu_lib, c1_particles, case):
+    if case == "c1":
+        d, aB0, aM0 = _c1_delta(c1_particles), -0.5, 0.0
+    else:
+        aB0, aM0 = map(float, case[4:].split(","))
+        d = synth.lognormal_delta(32, -2.0, 1.5, 1003)
+    want, _, st = O.scalar_solve(d, aB0, aM0, 1.0, 1e-13)
+    ctx = gpu_lib.Context(precision=1, max_cycles=200)
+    got, info = gpu_lib.scalar_mg_solve(cu(d), aB0, aM0, 1.0, 1e-8, ctx=ctx)
+    assert info["rel_res"] <= 1e-8
+    assert rel(got.cpu().numpy(), want) < 1e-6
+
+
+def test_solve_zero_coupling_and_errors(gpu_lib):
+    n = 16
+    d = cu(synth.lognormal_delta(n, -2.0, 1.0, 1))
+    phi, info = gpu_lib.scalar_mg_solve(d, 0.0, 0.0, 1.0, 1e-10)
+    assert float(phi.abs().max()) == 0.0
+    with pytest.raises(gpu_lib.PMError) as e:
+        gpu_lib.scalar_mg_solve(cu(np.zeros((12, 12, 12))), -0.5, 0.0, 1.0, 1e-8)
+    assert e.value.status == gpu_lib.PM_ERR_INVALID_ARG
+    bad = d.clone()
+    bad[3, 3, 3] = float("nan")
+    with pytest.raises(gpu_lib.PMError) as e:
+        gpu_lib.scalar_mg_solve(bad, -0.5, 0.0, 1.0, 1e-8)
+    assert e.value.status == gpu_lib.PM_ERR_NONFINITE
+    ctx = gpu_lib.Context(max_cycles=2)
+    with pytest.raises(gpu_lib.PMError) as e:
+        gpu_lib.scalar_mg_solve(d, -0.5, 0.0, 1.0, 1e-14, ctx=ctx)
+    assert e.value.status == gpu_lib.PM_ERR_NOCONV
+
+
+def test_pm_step_matches_oracle(gpu_lib, c1_particles):
+    n = 32
+    pos = c1_particles
+    vel = 0.01 * np.random.default_rng(2).standard_normal(pos.shape)
+    want = O.pm_step(pos, vel, n, -0.5, 0.0, 1.0, 1e-3, 1e-13)
+    p, v = cu(pos), cu(vel)
+    phi = torch.zeros((n, n, n), dtype=torch.float64, device=DEV)
+    ctx = gpu_lib.Context(precision=0, max_cycles=200)
+    info = gpu_lib.pm_step(p, v, n, -0.5, 0.0, 1.0, 1e-3, 1e-13, phi, ctx=ctx)
+    assert rel(phi.cpu().numpy(), want["chi"]) < 1e-10
+    assert rel(v.cpu().numpy(), want["vel"]) < 1e-10
+    assert np.abs(p.cpu().numpy() - want["pos"]).max() < 1e-12
+
+
+@pytest.mark.slow
+def test_config2_pm_step_256(gpu_lib):
+    """The 256^3 mesh / 256^3 particle step of the full-size configuration: deposit bit-exact
+    and Poisson against the oracle on the whole grid; chi by the oracle's residual of the
+    GPU field (any size); acceleration and kick-drift on a sample of particles."""
+    n = 256
+    pos = synth.zeldovich_particles(n, -1.5, 2.0, 1002)
+    acc = gpu_lib.pm_deposit_cic_fixed(cu(pos), n).cpu().numpy()
+    acc_o = O.deposit_cic(pos, n)
+    assert np.array_equal(acc, acc_o)
+    d = O.density(acc_o, pos.shape[1])
+    c = O.coefficients(-1.0, 0.2, 1.0)
+    psi_o = O.poisson_fft(d, c, 1.0)
+    p, v = cu(pos), torch.zeros((3, pos.shape[1]), dtype=torch.float64, device=DEV)
+    phi = torch.zeros((n, n, n), dtype=torch.float64, device=DEV)
+    ctx = gpu_lib.Context(precision=0, max_cycles=200)
+    psi_g = gpu_lib.poisson_solve(cu(d), 1.0, 0.2, ctx=ctx).cpu().numpy()
+    assert rel(psi_g, psi_o) < 1e-12
+    info = gpu_lib.pm_step(p, v, n, -1.0, 0.2, 1.0, 1e-3, 1e-10, phi, ctx=ctx)
+    chi = phi.cpu().numpy()
+    f = O.source(d, c)
+    r, fl = O.residual(chi, f, info["lambda"], c["nu"], c["kappa"], 0.35)
+    w = fl == 0
+    r_proj = r - w * (r.sum() / w.sum())
+    assert np.linalg.norm(r_proj) / np.linalg.norm(f - f.mean()) < 2e-10
+    sample = np.random.default_rng(0).choice(pos.shape[1], 4096, replace=False)
+    g = O.accel_grid(psi_o, chi, c["xi"], n)
+    acc_s = O.interp_cic(g, pos[:, sample])
+    p2, v2 = O.kick_drift(pos[:, sample], np.zeros((3, sample.size)), acc_s, 1e-3)
+    assert np.abs(v.cpu().numpy()[:, sample] - v2).max() <= 1e-10 * np.abs(v2).max()
+    assert np.abs(p.cpu().numpy()[:, sample] - p2).max() < 1e-12
