@@ -34,7 +34,8 @@ typedef enum {
     PM_ERR_NONFINITE = 4,   /* a NaN or Inf appeared in the input or the iteration */
     PM_ERR_NOCONV = 5,      /* max_cycles reached before the tolerance */
     PM_ERR_TIMEOUT = 6,     /* a device-side wait gave up (bounded spin) */
-    PM_ERR_OVERFLOW = 7     /* fixed-point deposit capacity exceeded */
+    PM_ERR_OVERFLOW = 7,    /* fixed-point deposit capacity exceeded */
+    PM_ERR_TOO_LARGE = 8    /* the request exceeds a fixed-size buffer of the library */
 } pm_status;
 
 /* Solver parameters.  pm_default_params fills the defaults noted here. */
@@ -131,6 +132,28 @@ pm_status force_interp(pm_ctx* ctx, const double* psi_N, const double* phi, int 
  */
 pm_status pm_step(pm_ctx* ctx, double* pos, double* vel, long long np, int n, double alpha_B0, double alpha_M0,
                   double a, double dt, double tol, double* phi_state, pm_solve_info* info);
+
+/*
+ * Allocation-free CIC deposit.  The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory themselves, such as a host
+ * application that hands the library a fixed, pre-reserved memory budget, or a
+ * plug-in environment that forbids allocations once it is running.  It computes the
+ * same delta as pm_deposit_cic (bit for bit) without a context and without calling
+ * cudaMalloc, cudaFree or any allocating routine: the int64 accumulator is a
+ * file-scope device array of 128^3 entries (16 MiB), which every GPU that loads the
+ * library holds until the process exits.
+ *   pos: device [3][np] in [0,1); delta: device n^3 (caller-owned, written);
+ *   cuda_stream: the cudaStream_t to enqueue on (NULL = legacy default stream).
+ *   n must be a power of two with 8 <= n <= 128: n > 128 returns PM_ERR_TOO_LARGE,
+ *   other bad arguments PM_ERR_INVALID_ARG; PM_ERR_OVERFLOW as for pm_deposit_cic.
+ * The current device must be the one that holds pos and delta.  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  Every call uses
+ * the same array and clears the part it needs, so calls whose work overlaps on the
+ * GPU (other streams, other threads) race with each other.  The call synchronises
+ * the stream to read the overflow flag.
+ */
+pm_status pm_deposit_cic_static(const double* pos, long long np, int n, double* delta, void* cuda_stream);
 
 /* ---- tracing: per-kernel-class device time and launch counts ----
  * With tracing on, the library records a CUDA event pair around each of its kernel

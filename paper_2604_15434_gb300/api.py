@@ -17,9 +17,9 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libpmeft.so")
 
 PM_OK, PM_ERR_INVALID_ARG, PM_ERR_CUDA, PM_ERR_OOM, PM_ERR_NONFINITE, PM_ERR_NOCONV, PM_ERR_TIMEOUT, \
-    PM_ERR_OVERFLOW = range(8)
+    PM_ERR_OVERFLOW, PM_ERR_TOO_LARGE = range(9)
 _STATUS = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_CUDA", 3: "PM_ERR_OOM", 4: "PM_ERR_NONFINITE",
-           5: "PM_ERR_NOCONV", 6: "PM_ERR_TIMEOUT", 7: "PM_ERR_OVERFLOW"}
+           5: "PM_ERR_NOCONV", 6: "PM_ERR_TIMEOUT", 7: "PM_ERR_OVERFLOW", 8: "PM_ERR_TOO_LARGE"}
 
 
 class PMError(RuntimeError):
@@ -78,6 +78,7 @@ SIGNATURES = {
     "pm_trace_get": (_I, [_P, _P]),
     "pm_trace_reset": (_I, [_P]),
     "pm_probe_fma": (_I, [_P, _P, _P]),
+    "pm_deposit_cic_static": (_I, [_P, _LL, _I, _P, _P]),
 }
 
 KERNEL_CLASSES = ("sweep64", "sweep32", "resid64", "resid32", "transfer", "coarsest", "reduce", "pm")
@@ -302,3 +303,15 @@ def pm_mg_prolong_add(coarse, fine, ctx=None):
     n = fine.shape[0]
     ctx._check(load().pm_mg_prolong_add(ctx._h, _ptr(coarse, shape=(n // 2,) * 3), n, _ptr(fine, shape=(n, n, n))))
     return fine
+
+
+def pm_deposit_cic_static(pos, n, delta=None, stream=None):
+    """Allocation-free deposit (see pm_deposit_cic_static in pmeft.h): n <= 128, no context.
+
+    Returns (delta, status) without raising, so callers can handle PM_ERR_TOO_LARGE."""
+    if delta is None:
+        delta = torch.empty((n, n, n), dtype=torch.float64, device=pos.device)
+    s = stream if stream is not None else torch.cuda.current_stream(pos.device)
+    st = load().pm_deposit_cic_static(_ptr(pos, name="pos"), pos.shape[1], n, _ptr(delta, shape=(n, n, n)),
+                                      ctypes.c_void_p(s.cuda_stream))
+    return delta, st

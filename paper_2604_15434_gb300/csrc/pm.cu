@@ -204,6 +204,24 @@ pm_status kick_drift(pm_ctx* ctx, double* pos, double* vel, const double* acc, l
     return PM_OK;
 }
 
+// Launchers on a bare stream (no context), used by the allocation-free deposit.
+static int grid_on(int sms, size_t work)
+{
+    size_t blocks = (work + kThreads - 1) / kThreads, cap = (size_t)(sms > 0 ? sms : 152) * 16;
+    return (int)(blocks < 1 ? 1 : (blocks > cap ? cap : blocks));
+}
+
+void launch_deposit_on(cudaStream_t s, int sms, const double* pos, long long np, int n, unsigned long long* acc)
+{
+    k_deposit<<<grid_on(sms, (size_t)np), kThreads, 0, s>>>(pos, np, n, acc);
+}
+
+void launch_density_on(cudaStream_t s, int sms, const long long* acc, int n, long long np, double* delta, int* flag)
+{
+    const size_t cells = (size_t)n * n * n;
+    k_density<<<grid_on(sms, cells), kThreads, 0, s>>>(acc, cells, (double)cells / (double)np, delta, flag);
+}
+
 }  // namespace pmeft
 
 using namespace pmeft;
