@@ -255,12 +255,13 @@ def main():
     fine = prof["sweep32"]
     if fine["fine_launches"] > 0 and fine["fine_ms"] > 0:
         avg_ms = fine["fine_ms"] / fine["fine_launches"]
-        # algorithmic bytes of one finest-level half-sweep of the FP32 correction-form smoother:
-        # read e (4 B) and the background (4 B) on every cell, the right-hand side (4 B) and
-        # the background Laplacian (4 B) of the updated half, write e of the updated half (4 B)
-        bytes_launch = cells * (4 + 4) + (cells // 2) * (4 + 4 + 4)
+        # algorithmic bytes of one finest-level launch of the single-pass FP32 sweep of the
+        # correction e (both colours): read e, the background, the right-hand side and the
+        # floored gap once (4 x 4 B), write e once (4 B): 20 B per cell
+        bytes_launch = cells * 20
         ach = bytes_launch / (avg_ms * 1e-3) / 1e9
-        roof = {"kernel": "k_half_sweep<float> (finest level)", "bound": "hbm", "achieved": ach, "peak": hbm,
+        roof = {"kernel": "k_sweep_fused<float> (finest level, one red-black sweep)", "bound": "hbm",
+                "achieved": ach, "peak": hbm,
                 "unit": "GB/s", "frac": ach / hbm, "traffic": None, "peak_source": src,
                 "bytes_per_launch": bytes_launch, "avg_launch_ms": avg_ms, "launches": fine["fine_launches"]}
     r64 = prof["resid64"]

@@ -45,14 +45,17 @@ typedef struct {
     int npre, npost;       /* smoothing sweeps before / after the coarse correction (2, 2) */
     int max_cycles;        /* cap on V-cycles (FP64) or outer iterations (mixed) (100) */
     int coarsest_n;        /* coarsest grid of the V-cycle (4) */
-    int coarse_sweeps;     /* sweeps of the coarsest-level solve (60) */
+    int coarse_sweeps;     /* sweeps of the coarsest-level solve (8) */
     int precision;         /* 0: FP64 FAS cycle; 1: FP32 inner cycle inside an FP64 defect-correction loop */
     int include_dot_alphaB;/* 1: keep alpha_B-dot/H = d alpha_B/d ln a in C2 (Sec. 2.2) */
+    int inner_cycles;      /* precision 1: FP32 V-cycles on the correction per FP64 outer residual (2) */
+    int autotune;          /* 1: time the tile variants of the FP32 sweep on first use of each size (1) */
 } pm_params;
 
 /* Report of one solve.  rel_res = |r|_2 / |f - <f>|_2 of the FP64 residual. */
 typedef struct {
     int cycles;                /* V-cycles (FP64) or outer iterations (mixed) performed */
+    int vcycles;               /* V-cycles performed in total (FP64 or FP32 inner) */
     int status;                /* the pm_status the solve returned */
     double rel_res;            /* final relative residual */
     double lambda;             /* gauge multiplier: N(chi) = f + lambda on a periodic box */
@@ -190,6 +193,10 @@ pm_status pm_trace_reset(pm_ctx* ctx);
  * a small device buffer; synchronises the stream. */
 pm_status pm_probe_fma(pm_ctx* ctx, double* fp64_gflops, double* fp32_gflops);
 
+/* Text report of the autotuner's choices so far (one line per tuned key); NUL-terminated,
+ * truncated to len bytes.  Returns the full length. */
+int pm_tune_log(const pm_ctx* ctx, char* buf, int len);
+
 /* ---- single multigrid operations on a periodic n^3 grid (for testing the kernels
  * one at a time against a reference; same semantics as inside scalar_mg_solve) ---- */
 
@@ -199,6 +206,12 @@ pm_status pm_probe_fma(pm_ctx* ctx, double* fp64_gflops, double* fp32_gflops);
  * term off per cell.  h = 1/n. */
 pm_status pm_mg_sweep(pm_ctx* ctx, double* u, const double* f, double lambda, int n, double nu, double kappa,
                       double eta, const unsigned char* kmask);
+/* The same sweep on an FP32 grid: mode 0 runs the two half-sweep kernels, mode k >= 1
+ * the single-pass fused kernel with tile variant k-1 (pm_tune_log lists the variants the
+ * autotuner chose; the inner FP32 cycle uses the fused kernel for grids >= 256^3).  A
+ * variant that does not tile n falls back to mode 0.  u, f: device n^3 float. */
+pm_status pm_mg_sweep_f32(pm_ctx* ctx, float* u, const float* f, float lambda, int n, double nu, double kappa,
+                          double eta, const unsigned char* kmask, int mode);
 /* Residual: r = f + lambda - N(u) in cells with a real root, nu (L_sat - L(u)) in floored
  * cells; floored (device n^3 bytes, nullable) receives the floored-cell flags. */
 pm_status pm_mg_residual(pm_ctx* ctx, const double* u, const double* f, double lambda, int n, double nu,

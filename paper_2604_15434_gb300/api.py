@@ -31,17 +31,18 @@ class PMError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("omega_m0", ctypes.c_double), ("eta", ctypes.c_double), ("npre", ctypes.c_int),
                 ("npost", ctypes.c_int), ("max_cycles", ctypes.c_int), ("coarsest_n", ctypes.c_int),
-                ("coarse_sweeps", ctypes.c_int), ("precision", ctypes.c_int), ("include_dot_alphaB", ctypes.c_int)]
+                ("coarse_sweeps", ctypes.c_int), ("precision", ctypes.c_int), ("include_dot_alphaB", ctypes.c_int),
+                ("inner_cycles", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
-    _fields_ = [("cycles", ctypes.c_int), ("status", ctypes.c_int), ("rel_res", ctypes.c_double),
+    _fields_ = [("cycles", ctypes.c_int), ("vcycles", ctypes.c_int), ("status", ctypes.c_int), ("rel_res", ctypes.c_double),
                 ("lam", ctypes.c_double), ("floored_cells", ctypes.c_longlong), ("unstable_nu", ctypes.c_int),
                 ("rel_res_hist", ctypes.c_double * 64), ("ms_total", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         k = min(self.cycles + 1, 64)
-        return {"cycles": self.cycles, "status": self.status, "rel_res": self.rel_res, "lambda": self.lam,
+        return {"cycles": self.cycles, "vcycles": self.vcycles, "status": self.status, "rel_res": self.rel_res, "lambda": self.lam,
                 "floored_cells": self.floored_cells, "unstable_nu": self.unstable_nu,
                 "hist": list(self.rel_res_hist[:k]), "ms_total": self.ms_total}
 
@@ -79,6 +80,8 @@ SIGNATURES = {
     "pm_trace_reset": (_I, [_P]),
     "pm_probe_fma": (_I, [_P, _P, _P]),
     "pm_deposit_cic_static": (_I, [_P, _LL, _I, _P, _P]),
+    "pm_mg_sweep_f32": (_I, [_P, _P, _P, ctypes.c_float, _I, _D, _D, _D, _P, _I]),
+    "pm_tune_log": (_I, [_P, _P, _I]),
 }
 
 KERNEL_CLASSES = ("sweep64", "sweep32", "resid64", "resid32", "transfer", "coarsest", "reduce", "pm")
@@ -165,6 +168,11 @@ class Context:
 
     def trace_reset(self):
         self._check(load().pm_trace_reset(self._h))
+
+    def tune_log(self) -> str:
+        buf = ctypes.create_string_buffer(8192)
+        load().pm_tune_log(self._h, buf, 8192)
+        return buf.value.decode()
 
     def probe_fma(self):
         """(FP64, FP32) FMA throughput of this device in GFLOP/s."""
@@ -277,6 +285,15 @@ def pm_mg_sweep(u, f, lam, nu, kappa, eta, kmask=None, ctx=None):
     n = u.shape[0]
     ctx._check(load().pm_mg_sweep(ctx._h, _ptr(u, shape=(n, n, n)), _ptr(f, shape=(n, n, n)), lam, n, nu, kappa, eta,
                                   _ptr(kmask, torch.uint8, (n, n, n), "kmask")))
+    return u
+
+
+def pm_mg_sweep_f32(u, f, lam, nu, kappa, eta, kmask=None, mode=1, ctx=None):
+    """One red-black sweep of an FP32 grid in place; mode 0: two half-sweep launches, 1: single pass."""
+    ctx = ctx or default_context()
+    n = u.shape[0]
+    ctx._check(load().pm_mg_sweep_f32(ctx._h, _ptr(u, torch.float32, (n, n, n)), _ptr(f, torch.float32, (n, n, n)),
+                                      lam, n, nu, kappa, eta, _ptr(kmask, torch.uint8, (n, n, n), "kmask"), mode))
     return u
 
 

@@ -162,9 +162,11 @@ extern "C" void pm_default_params(pm_params* p)
     p->npost = 2;
     p->max_cycles = 100;
     p->coarsest_n = 4;
-    p->coarse_sweeps = 60;
+    p->coarse_sweeps = 8;
     p->precision = 0;
     p->include_dot_alphaB = 1;
+    p->inner_cycles = 2;
+    p->autotune = 1;
 }
 
 static bool params_ok(const pm_params* p)
@@ -172,7 +174,8 @@ static bool params_ok(const pm_params* p)
     return p->omega_m0 > 0.0 && p->omega_m0 < 1.0 && p->eta >= 0.0 && p->eta < 1.0 && p->npre >= 0 &&
            p->npost >= 0 && p->npre + p->npost > 0 && p->max_cycles >= 0 && p->coarsest_n >= 2 &&
            p->coarsest_n <= 8 && (p->coarsest_n & (p->coarsest_n - 1)) == 0 && p->coarse_sweeps >= 1 &&
-           (p->precision == 0 || p->precision == 1);
+           (p->precision == 0 || p->precision == 1) && p->inner_cycles >= 1 && p->inner_cycles <= 16 &&
+           (p->autotune == 0 || p->autotune == 1);
 }
 
 extern "C" pm_status pm_coefficients(double aB0, double aM0, double a, double om0, int include_dot, pm_coeffs* out)
@@ -287,4 +290,16 @@ extern "C" pm_status pm_trace_get(pm_ctx* ctx, pm_profile* out)
     ctx->recs.clear();
     *out = ctx->prof;
     return PM_OK;
+}
+
+extern "C" int pm_tune_log(const pm_ctx* ctx, char* buf, int len)
+{
+    if (!ctx) return 0;
+    const int full = (int)ctx->tune_log.size();
+    if (buf && len > 0) {
+        const int k = full < len - 1 ? full : len - 1;
+        memcpy(buf, ctx->tune_log.data(), (size_t)k);
+        buf[k] = 0;
+    }
+    return full;
 }

@@ -76,6 +76,8 @@ struct pm_ctx {
     double* host_out = nullptr;      // pinned host mirror (64 doubles)
     int* flag = nullptr;             // device error flag
     int num_sms = 152;
+    std::map<int, int> tuned;  // autotuned tile variant per (level size, inputs)
+    std::string tune_log;
     // tracing (pm_trace_*): event pairs per launch, summed per class on read-out
     bool tracing = false;
     pm_profile prof{};
@@ -197,27 +199,30 @@ template <typename T, bool BG>
 __device__ __forceinline__ Local<T> local_eval(const Stencil<T>& s, const Stencil<T>& b, T ih2, T nu, T kap, T rhs,
                                                T lsat, bool use_gap = false, T gapx = T(0))
 {
-    const T X = (s.ax - T(2) * s.c0) * ih2;
-    const T Y = (s.ay - T(2) * s.c0) * ih2;
-    const T Z = (s.az - T(2) * s.c0) * ih2;
-    const T q = T(0.25) * ih2;
-    const T cxy = s.exy * q, cxz = s.exz * q, cyz = s.eyz * q;
+    // Work in h = 1 units: X = h^2 chi_xx, cross terms h^2 chi_xy = exy/4, and fold 1/h^2
+    // and 1/h^4 into nu and kappa.  n is a power of two, so h^2 is a power of two and
+    // every rescaled product rounds exactly as the unscaled one would.
+    const T X = s.ax - T(2) * s.c0;
+    const T Y = s.ay - T(2) * s.c0;
+    const T Z = s.az - T(2) * s.c0;
     Local<T> o;
-    const T L = X + Y + Z;
-    T q2 = T(2) * (X * Y + Y * Z + Z * X) - T(2) * (cxy * cxy + cxz * cxz + cyz * cyz);
-    T Ltot = L;
+    const T L1 = X + Y + Z;  // h^2 L
+    // h^4 q2 = 2 (XY + YZ + ZX) - 2 (exy^2 + exz^2 + eyz^2)/16
+    T q2 = T(2) * (X * Y + Y * Z + Z * X) - T(0.125) * (s.exy * s.exy + s.exz * s.exz + s.eyz * s.eyz);
+    T L1tot = L1;
     if (BG) {
-        const T Xb = (b.ax - T(2) * b.c0) * ih2;
-        const T Yb = (b.ay - T(2) * b.c0) * ih2;
-        const T Zb = (b.az - T(2) * b.c0) * ih2;
-        const T bxy = b.exy * q, bxz = b.exz * q, byz = b.eyz * q;
+        const T Xb = b.ax - T(2) * b.c0;
+        const T Yb = b.ay - T(2) * b.c0;
+        const T Zb = b.az - T(2) * b.c0;
         // q2(b + u) - q2(b) = q2(u) + 2[Xb(Y+Z) + Yb(X+Z) + Zb(X+Y)] - 4[bxy cxy + bxz cxz + byz cyz]
-        q2 += T(2) * (Xb * (Y + Z) + Yb * (X + Z) + Zb * (X + Y)) - T(4) * (bxy * cxy + bxz * cxz + byz * cyz);
-        Ltot = L + (Xb + Yb + Zb);
+        q2 += T(2) * (Xb * (Y + Z) + Yb * (X + Z) + Zb * (X + Y)) -
+              T(0.25) * (b.exy * s.exy + b.exz * s.exz + b.eyz * s.eyz);
+        L1tot = L1 + (Xb + Yb + Zb);
     }
+    T Ltot = L1tot * ih2;
     if (kap != T(0)) {
         if (use_gap) {
-            o.g = gapx - L;
+            o.g = gapx - L1 * ih2;
             Ltot = lsat - o.g;
         } else {
             o.g = lsat - Ltot;
@@ -226,10 +231,11 @@ __device__ __forceinline__ Local<T> local_eval(const Stencil<T>& s, const Stenci
         o.g = T(0);
     }
     o.L = Ltot;
-    const T N = nu * L - kap * q2;
+    const T nu1 = nu * ih2, kap1 = kap * ih2 * ih2;
+    const T N = nu1 * L1 - kap1 * q2;
     o.G = N - rhs;
     o.Ep = (T(-6) * nu + T(8) * kap * o.L) * ih2;
-    o.P = T(-24) * kap * ih2 * ih2;
+    o.P = T(-24) * kap1;
     o.D = o.Ep * o.Ep - T(4) * o.P * o.G;
     return o;
 }
@@ -246,6 +252,20 @@ __device__ __forceinline__ T local_update(const Local<T>& o, T sp, T Df, T ih2)
     const T sq = sqrt(o.D);
     if (o.Ep * sp > T(0)) return T(-2) * o.G / (o.Ep + sp * sq);
     return (sp * sq - o.Ep) / (T(2) * o.P);
+}
+
+// FP32 variant for the inner cycle of the defect-correction loop: the same branches with
+// the approximate hardware reciprocal and square root (relative error ~1e-7), and the
+// constant divisions folded into multiplications.  The FP64 outer residual is the judge
+// of accuracy, so the inner update only has to be a good correction.
+__device__ __forceinline__ float local_update_fast(const Local<float>& o, float sp, float Df, float h2over6,
+                                                   float inv2P)
+{
+    if (o.P == 0.f) return __fdividef(-o.G, o.Ep);
+    if (o.D < Df) return -o.g * h2over6;
+    const float sq = __fsqrt_rn(o.D);
+    if (o.Ep * sp > 0.f) return __fdividef(-2.f * o.G, o.Ep + sp * sq);
+    return (sp * sq - o.Ep) * inv2P;
 }
 
 }  // namespace pmeft

@@ -14,6 +14,7 @@
 #include <cmath>
 
 #include "internal.cuh"
+#include "sweep_fused.cuh"
 
 namespace pmeft {
 
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(256) k_half_sweep(const T* __restrict__ own, c
                                                     T* __restrict__ out, const T* __restrict__ F, T fscale, T lam,
                                                     const uint8_t* __restrict__ kmask, const T* __restrict__ bg,
                                                     const T* __restrict__ gap, int n, int colour, T ih2, T nu, T kap,
-                                                    T sp, T Df, T lsat_num)
+                                                    T sp, T Df, T lsat_c)
 {
     const int hn = n >> 1;
     const size_t total = (size_t)n * n * hn;
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(256) k_half_sweep(const T* __restrict__ own, c
         Stencil<T> b;
         if (BG) b = load_stencil(bg, bg, i, j, k, n);
         const T kc = (kmask && kmask[c]) ? T(0) : kap;
-        const T lsat = kc != T(0) ? lsat_num / kc : T(0);
+        const T lsat = kc != T(0) ? lsat_c : T(0);
         Local<T> o = local_eval<T, BG>(s, b, ih2, nu, kc, fscale * F[c] + lam, lsat, gap != nullptr, gap ? gap[c] : T(0));
         out[c] = s.c0 + local_update(o, sp, Df, ih2);
     }
@@ -111,12 +112,12 @@ template <typename T, bool BG, bool WRITE_R, bool MIXED>
 __global__ void __launch_bounds__(256) k_residual(const T* __restrict__ u, const T* __restrict__ F, T fscale, T lam,
                                                   const uint8_t* __restrict__ kmask, const T* __restrict__ bg,
                                                   const T* __restrict__ gap, int n, T ih2, T nu, T kap, T Df,
-                                                  T lsat_num, bool floor_piece, T* __restrict__ r,
+                                                  T lsat_c, bool floor_piece, T* __restrict__ r,
                                                   uint8_t* __restrict__ sat,
                                                   double* __restrict__ partials, float* __restrict__ rplain,
                                                   float* __restrict__ chi32, float* __restrict__ gap32)
 {
-    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    float fa[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     const size_t total = (size_t)n * n * n;
     for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(c % n);
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(256) k_residual(const T* __restrict__ u, const
         if (BG) b = load_stencil(bg, bg, i, j, k, n);
         const bool masked = kmask && kmask[c];
         const T kc = masked ? T(0) : kap;
-        const T lsat = kc != T(0) ? lsat_num / kc : T(0);
+        const T lsat = kc != T(0) ? lsat_c : T(0);
         Local<T> o = local_eval<T, BG>(s, b, ih2, nu, kc, fscale * F[c] + lam, lsat, gap != nullptr, gap ? gap[c] : T(0));
         // the floored piece exists on the finest level only; coarse levels take their
         // pieces from the restricted mask (linear where masked, quadratic elsewhere), so
@@ -142,18 +143,23 @@ __global__ void __launch_bounds__(256) k_residual(const T* __restrict__ u, const
             chi32[c] = (float)s.c0;
             gap32[c] = (float)o.g;
         }
-        const double d = (double)rv;
+        // per-thread partial sums in FP32 (a few hundred terms each); the block and grid
+        // reductions are FP64.  The sums only set the gauge shift and the stopping norm.
+        const float d = (float)rv;
         if (!isfinite(d)) {
-            acc[4] += 1.0;
+            fa[4] += 1.f;
         } else {
-            acc[0] += d;
-            acc[2] += d * d;
+            fa[0] += d;
+            fa[2] += d * d;
             if (!fl) {
-                acc[1] += d;
-                acc[3] += 1.0;
+                fa[1] += d;
+                fa[3] += 1.f;
             }
         }
     }
+    double acc[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) acc[q] = (double)fa[q];
     block_sums<5>(acc, partials);
 }
 
@@ -286,7 +292,7 @@ __global__ void __launch_bounds__(256) k_coarsest(T* __restrict__ u, const T* __
     __syncthreads();
     const double sp = nu >= 0.0 ? -1.0 : 1.0;
     const double sqDf = eta * 6.0 * fabs(nu) * ih2, Df = sqDf * sqDf;
-    const double lsat_num = 0.75 * nu * (1.0 - eta);
+    const double lsat_c = kap != 0.0 ? 0.75 * nu * (1.0 - eta) / kap : 0.0;  // L_sat
     double lam = 0.0;
     for (int it = 0; it < sweeps; ++it) {
         for (int colour = 0; colour < 2; ++colour) {
@@ -299,7 +305,7 @@ __global__ void __launch_bounds__(256) k_coarsest(T* __restrict__ u, const T* __
                 Stencil<double> b;
                 if (BG) b = load_stencil<double>(sb, sb, i, j, k, n);
                 const double kc = sk[c] ? 0.0 : kap;
-                Local<double> o = local_eval<double, BG>(s, b, ih2, nu, kc, sf[c] + lam, kc != 0.0 ? lsat_num / kc : 0.0);
+                Local<double> o = local_eval<double, BG>(s, b, ih2, nu, kc, sf[c] + lam, kc != 0.0 ? lsat_c : 0.0);
                 su[c] = s.c0 + local_update(o, sp, Df, ih2);
             }
             __syncthreads();
@@ -312,7 +318,7 @@ __global__ void __launch_bounds__(256) k_coarsest(T* __restrict__ u, const T* __
             Stencil<double> b;
             if (BG) b = load_stencil<double>(sb, sb, i, j, k, n);
             const double kc = sk[c] ? 0.0 : kap;
-            Local<double> o = local_eval<double, BG>(s, b, ih2, nu, kc, sf[c] + lam, kc != 0.0 ? lsat_num / kc : 0.0);
+            Local<double> o = local_eval<double, BG>(s, b, ih2, nu, kc, sf[c] + lam, kc != 0.0 ? lsat_c : 0.0);
             const bool fl = floor_piece && (o.P != 0.0) && (o.D < Df);
             a0 += fl ? nu * o.g : -o.G;
             a1 += fl ? 0.0 : 1.0;
@@ -380,14 +386,136 @@ struct Coef {
     double nu, kap, eta, src;
 };
 
-template <typename T>
-static void sweep(pm_ctx* ctx, Level<T>& L, const T* F, T fscale, T lam, const Coef& c)
+constexpr int kFusedMinN = 256;
+
+// Tile variants of the single-pass FP32 sweep: (TX, TY) x-y tile, NZ planes per block.
+struct FusedCfg {
+    int tx, ty, nz;
+};
+static const FusedCfg kFusedCfgs[] = {{64, 16, 32}, {64, 8, 32}, {64, 8, 64}, {32, 8, 32}, {32, 8, 64}, {64, 4, 64},
+                                     {64, 16, 16}, {64, 8, 16}};
+constexpr int kNumFusedCfgs = sizeof(kFusedCfgs) / sizeof(kFusedCfgs[0]);
+
+template <int TX, int TY, bool BG, bool GAP>
+static void launch_fused(pm_ctx* ctx, const float* A, float* B, const float* F, float fscale, float lam,
+                         const Level<float>& L, int nz, float h2inv, const Coef& c, float sp, float Df, float lsn)
 {
+    const int n = L.n;
+    constexpr size_t sm = fused_smem_bytes<float, TX, TY, BG, GAP>();
+    auto k = k_sweep_fused<float, TX, TY, BG, GAP>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const dim3 grid(n / TX, n / TY, n / nz);
+    k<<<grid, 256, sm, ctx->stream>>>(A, B, F, fscale, lam, L.kmask, L.bg, L.gap, n, nz, h2inv, (float)c.nu,
+                                      (float)c.kap, sp, Df, lsn);
+}
+
+template <bool BG, bool GAP>
+static void launch_fused_cfg(pm_ctx* ctx, int cfg, const float* A, float* B, const float* F, float fscale, float lam,
+                             const Level<float>& L, float h2inv, const Coef& c, float sp, float Df, float lsn)
+{
+    const FusedCfg& g = kFusedCfgs[cfg];
+#define PM_FUSED_CASE(TX_, TY_)                                                                        \
+    if (g.tx == TX_ && g.ty == TY_) {                                                                  \
+        launch_fused<TX_, TY_, BG, GAP>(ctx, A, B, F, fscale, lam, L, g.nz, h2inv, c, sp, Df, lsn);    \
+        return;                                                                                        \
+    }
+    PM_FUSED_CASE(64, 16)
+    PM_FUSED_CASE(64, 8)
+    PM_FUSED_CASE(32, 8)
+    PM_FUSED_CASE(64, 4)
+#undef PM_FUSED_CASE
+}
+
+static bool fused_cfg_fits(int cfg, int n)
+{
+    const FusedCfg& g = kFusedCfgs[cfg];
+    return n >= g.tx && n >= g.ty && n >= g.nz && n % g.tx == 0 && n % g.ty == 0 && n % g.nz == 0;
+}
+
+// One red-black sweep of an FP32 level in a single pass (k_sweep_fused) with tile variant cfg.
+static void sweep_fused_f32(pm_ctx* ctx, Level<float>& L, const float* F, float fscale, float lam, const Coef& c,
+                            int cfg)
+{
+    const int n = L.n;
+    const float h2inv = (float)((double)n * (double)n);
+    const float sp = c.nu >= 0.0 ? -1.f : 1.f;
+    const double sqDf = c.eta * 6.0 * std::fabs(c.nu) * (double)n * (double)n;
+    const float Df = (float)(sqDf * sqDf);
+    const float lsn = c.kap != 0.0 ? (float)(0.75 * c.nu * (1.0 - c.eta) / c.kap) : 0.f;  // L_sat
+    float* A = L.u[L.cur];
+    float* B = L.u[1 - L.cur];
+    ctx->begin(PM_K_SWEEP32, L.fine, (long long)L.cells);
+    if (L.bg && L.gap) launch_fused_cfg<true, true>(ctx, cfg, A, B, F, fscale, lam, L, h2inv, c, sp, Df, lsn);
+    else if (L.bg) launch_fused_cfg<true, false>(ctx, cfg, A, B, F, fscale, lam, L, h2inv, c, sp, Df, lsn);
+    else launch_fused_cfg<false, false>(ctx, cfg, A, B, F, fscale, lam, L, h2inv, c, sp, Df, lsn);
+    ctx->end();
+    L.cur = 1 - L.cur;
+}
+
+// Autotuner: the first time a level of size n (with a given input set) is swept, every
+// fitting tile variant runs once on the real data (out of place, A -> B, so the state is
+// unchanged whichever runs last) and the fastest is kept for that key.
+static int tuned_cfg(pm_ctx* ctx, Level<float>& L, const float* F, float fscale, float lam, const Coef& c)
+{
+    const int key = L.n * 4 + (L.bg ? 2 : 0) + (L.gap ? 1 : 0);
+    auto it = ctx->tuned.find(key);
+    if (it != ctx->tuned.end()) return it->second;
+    int best = 0;
+    if (ctx->prm.autotune) {
+        float best_ms = 1e30f;
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        const bool was = ctx->tracing;
+        ctx->tracing = false;
+        for (int cfg = 0; cfg < kNumFusedCfgs; ++cfg) {
+            if (!fused_cfg_fits(cfg, L.n)) continue;
+            for (int rep = 0; rep < 2; ++rep) {
+                cudaEventRecord(e0, ctx->stream);
+                sweep_fused_f32(ctx, L, F, fscale, lam, c, cfg);
+                L.cur = 1 - L.cur;  // keep A as the input of every trial
+                cudaEventRecord(e1, ctx->stream);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep == 1 && ms < best_ms) {
+                    best_ms = ms;
+                    best = cfg;
+                }
+            }
+        }
+        ctx->tracing = was;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        ctx->tune_log += "sweep32 n=" + std::to_string(L.n) + (L.bg ? " bg" : "") + (L.gap ? " gap" : "") +
+                         ": tile " + std::to_string(kFusedCfgs[best].tx) + "x" + std::to_string(kFusedCfgs[best].ty) +
+                         " nz " + std::to_string(kFusedCfgs[best].nz) + " " + std::to_string(best_ms) + " ms\n";
+    }
+    ctx->tuned[key] = best;
+    return best;
+}
+
+template <typename T>
+static void sweep(pm_ctx* ctx, Level<T>& L, const T* F, T fscale, T lam, const Coef& c, int force_mode = -1)
+{
+    // FP32 levels of at least 256^3 take the single-pass kernel (force_mode 0: two
+    // half-sweep launches, 1: single pass, -1: choose by size)
+    if constexpr (sizeof(T) == 4) {
+        // force_mode >= 1 selects tile variant force_mode - 1
+        if (force_mode >= 1 && force_mode <= kNumFusedCfgs && fused_cfg_fits(force_mode - 1, L.n)) {
+            sweep_fused_f32(ctx, L, F, fscale, lam, c, force_mode - 1);
+            return;
+        }
+        if (force_mode < 0 && L.n >= kFusedMinN && fused_cfg_fits(0, L.n)) {
+            sweep_fused_f32(ctx, L, F, fscale, lam, c, tuned_cfg(ctx, L, F, fscale, lam, c));
+            return;
+        }
+    }
     const int n = L.n;
     const T h2inv = (T)((double)n * (double)n);
     const T sp = c.nu >= 0.0 ? T(-1) : T(1);
     const double sqDf = c.eta * 6.0 * std::fabs(c.nu) * (double)n * (double)n;
-    const T lsn = (T)(0.75 * c.nu * (1.0 - c.eta));
+    const T lsn = c.kap != 0.0 ? (T)(0.75 * c.nu * (1.0 - c.eta) / c.kap) : T(0);  // L_sat
     const int grid = grid_for(ctx, L.cells / 2);
     T* A = L.u[L.cur];
     T* B = L.u[1 - L.cur];
@@ -421,7 +549,7 @@ static int residual(pm_ctx* ctx, Level<T>& L, const T* u, const T* F, T fscale, 
     const double sqDf = c.eta * 6.0 * std::fabs(c.nu) * (double)n * (double)n;
     int grid = grid_for(ctx, L.cells);
     if (grid > kMaxPartials) grid = kMaxPartials;
-    const T lsn = (T)(0.75 * c.nu * (1.0 - c.eta));
+    const T lsn = c.kap != 0.0 ? (T)(0.75 * c.nu * (1.0 - c.eta) / c.kap) : T(0);  // L_sat
     if (L.bg) {
         ctx->begin(sizeof(T) == 8 ? PM_K_RESID64 : PM_K_RESID32, L.fine, (long long)L.cells);
         k_residual<T, true, WRITE_R, MIXED><<<grid, kThreads, 0, ctx->stream>>>(
@@ -571,7 +699,7 @@ pm_status mg_solve(pm_ctx* ctx, const double* delta, int n, const pm_coeffs& cf,
     L0.cur = 0;
     PM_CUDA(cudaMemcpyAsync(L0.u[0], phi, cells * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
     double lam = 0.0, rr = 0.0;
-    int cyc = 0;
+    int cyc = 0, vcyc = 0;
     pm_status st = PM_ERR_NOCONV;
     for (;;) {
         if (mixed)
@@ -611,13 +739,17 @@ pm_status mg_solve(pm_ctx* ctx, const double* delta, int n, const pm_coeffs& cf,
             }
             s[0].cur = 0;
             PM_CUDA(cudaMemsetAsync(s[0].u[0], 0, cells * sizeof(float), ctx->stream));
-            vcycle<float>(ctx, s, 0, w->rplain, 1.0f, (float)(-gm), c);
+            for (int k = 0; k < P.inner_cycles; ++k) {
+                vcycle<float>(ctx, s, 0, w->rplain, 1.0f, (float)(-gm), c);
+                ++vcyc;
+            }
             ctx->begin(PM_K_REDUCE, false, 0);
             k_add_correction<<<grid_for(ctx, cells), kThreads, 0, ctx->stream>>>(L0.u[L0.cur], s[0].u[s[0].cur],
                                                                                  cells);
             ctx->end();
         } else {
             vcycle<double>(ctx, w->d, 0, delta, cf.src, lam, c);
+            ++vcyc;
         }
         recentre<double>(ctx, L0.u[L0.cur], cells);
         ++cyc;
@@ -630,6 +762,7 @@ pm_status mg_solve(pm_ctx* ctx, const double* delta, int n, const pm_coeffs& cf,
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     inf->cycles = cyc;
+    inf->vcycles = vcyc;
     inf->rel_res = rr;
     inf->lambda = lam;
     inf->ms_total = ms;
@@ -670,6 +803,28 @@ extern "C" pm_status pm_mg_sweep(pm_ctx* ctx, double* u, const double* f, double
     Coef c{nu, kappa, eta, 1.0};
     sweep<double>(ctx, L, f, 1.0, lambda, c);
     PM_CUDA(cudaMemcpyAsync(u, L.u[L.cur], cells * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    PM_CUDA(cudaGetLastError());
+    return PM_OK;
+}
+
+extern "C" pm_status pm_mg_sweep_f32(pm_ctx* ctx, float* u, const float* f, float lambda, int n, double nu,
+                                     double kappa, double eta, const unsigned char* kmask, int mode)
+{
+    PM_TRY(check_mg_args(ctx, n));
+    if (!u || !f || mode < 0 || mode > kNumFusedCfgs) return PM_ERR_INVALID_ARG;
+    Workspace* w = nullptr;
+    PM_TRY(get_workspace(ctx, n, &w));
+    PM_TRY(ensure_mg(ctx, w, true));
+    Level<float> L = w->s[0];  // borrow the buffers, with the caller's mask and no background
+    L.kmask = (uint8_t*)kmask;
+    L.bg = nullptr;
+    L.gap = nullptr;
+    L.cur = 0;
+    const size_t cells = L.cells;
+    PM_CUDA(cudaMemcpyAsync(L.u[0], u, cells * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
+    Coef c{nu, kappa, eta, 1.0};
+    sweep<float>(ctx, L, f, 1.0f, lambda, c, mode);
+    PM_CUDA(cudaMemcpyAsync(u, L.u[L.cur], cells * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
     PM_CUDA(cudaGetLastError());
     return PM_OK;
 }

@@ -240,3 +240,38 @@ def test_config2_pm_step_256(gpu_lib):
     p2, v2 = O.kick_drift(pos[:, sample], np.zeros((3, sample.size)), acc_s, 1e-3)
     assert np.abs(v.cpu().numpy()[:, sample] - v2).max() <= 1e-10 * np.abs(v2).max()
     assert np.abs(p.cpu().numpy()[:, sample] - p2).max() < 1e-12
+
+
+# ------------------------------------------------------------------ FP32 smoother kernels
+
+
+@pytest.mark.parametrize("n,masked", [(64, False), (64, True), (256, False)])
+def test_fp32_fused_sweep_matches_half_sweeps_and_oracle(gpu_lib, n, masked):
+    """The single-pass FP32 sweep equals the two half-sweep launches (same arithmetic) and
+    the FP64 reference sweep to FP32 rounding."""
+    u, f, c = _sweep_inputs(n, 300 + n, 0.5)
+    km = (np.random.default_rng(n).random((n, n, n)) < 0.3).astype(np.uint8) if masked else None
+    kmt = None if km is None else cu(km, torch.uint8)
+    a = gpu_lib.pm_mg_sweep_f32(cu(u, torch.float32), cu(f, torch.float32), 0.01, c["nu"], c["kappa"], 0.35,
+                                kmask=kmt, mode=0).cpu().numpy()
+    b = gpu_lib.pm_mg_sweep_f32(cu(u, torch.float32), cu(f, torch.float32), 0.01, c["nu"], c["kappa"], 0.35,
+                                kmask=kmt, mode=1).cpu().numpy()
+    scale = np.abs(a).max()
+    assert np.abs(a - b).max() <= 2e-6 * scale
+    if n <= 64:
+        want = O.smooth_sweep(u.astype(np.float32).astype(np.float64), f.astype(np.float32).astype(np.float64),
+                              0.01, c["nu"], c["kappa"], 0.35, kmask=km)
+        assert np.abs(b - want).max() <= 1e-4 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("inner", [1, 3])
+def test_mixed_precision_solve_256_uses_fused_sweep(gpu_lib, inner):
+    """At 256^3 the inner cycle runs the fused sweep on its finest level; the mixed solve
+    reaches 1e-8 and agrees with the FP64 GPU solve (itself pinned to the oracle) to 1e-6."""
+    n = 256
+    d = cu(synth.lognormal_delta(n, -2.0, 1.5, 1003))
+    ref, info64 = gpu_lib.scalar_mg_solve(d, -0.5, 0.0, 1.0, 1e-11, ctx=gpu_lib.Context(precision=0))
+    got, info = gpu_lib.scalar_mg_solve(d, -0.5, 0.0, 1.0, 1e-8,
+                                        ctx=gpu_lib.Context(precision=1, inner_cycles=inner, max_cycles=100))
+    assert info["rel_res"] <= 1e-8
+    assert float((got - ref).norm() / ref.norm()) < 1e-6
