@@ -119,6 +119,54 @@ def cpu_baseline(n_sample=128, combo=(-0.5, 0.0), target_n=512):
             "sample_seconds": dt}
 
 
+def batched_leg(api, dev, stream, nbox=24, seed=1007):
+    """The 24-box configuration: mesh sizes drawn from {64,128,256}^3, parameters alpha_B0 ~
+    U[-2,0], alpha_M0 ~ U[0,1], a ~ U[0.3,1] (|nu| < 0.1 redrawn), Zel'dovich sources with
+    P ~ k^-1.5 and sigma 1 deposited on the GPU; all boxes solved to 1e-8 by one batched call
+    (one graph launch per outer iteration), and the same boxes one by one for comparison."""
+    import torch
+    from paper_2604_15434_gb300 import synth
+
+    sizes = synth.sample_box_sizes(nbox, seed)
+    params = synth.sample_box_params(nbox, seed, accept=lambda aB, aM, a: abs(api.coefficients(aB, aM, a)["nu"]) >= 0.1)
+    deltas = []
+    for b, n in enumerate(sizes):
+        pos = torch.from_numpy(synth.zeldovich_particles(n, -1.5, 1.0, seed + 1 + b)).to(dev)
+        deltas.append(api.pm_deposit_cic(pos, n))
+        del pos
+    aB = [p[0] for p in params]
+    aM = [p[1] for p in params]
+    aa = [p[2] for p in params]
+    ctx = api.Context(dev.index, stream, precision=1, max_cycles=100)
+    phis = [torch.zeros_like(d) for d in deltas]
+    api.scalar_mg_solve_batched(deltas, aB, aM, aa, TOL, phis=phis, ctx=ctx)  # warm-up (tuning, workspaces)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for p in phis:
+        p.zero_()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    _, infos = api.scalar_mg_solve_batched(deltas, aB, aM, aa, TOL, phis=phis, ctx=ctx)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    batched_ms = e0.elapsed_time(e1)
+    seq_ctx = api.Context(dev.index, stream, precision=1, max_cycles=100)
+    for d, b0, m0, a0 in zip(deltas, aB, aM, aa):  # warm-up of the single-box path
+        api.scalar_mg_solve(d, b0, m0, a0, TOL, phi=torch.zeros_like(d), ctx=seq_ctx)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for d, b0, m0, a0, p in zip(deltas, aB, aM, aa, phis):
+        p.zero_()
+        api.scalar_mg_solve(d, b0, m0, a0, TOL, phi=p, ctx=seq_ctx)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    cells = sum(n ** 3 for n in sizes)
+    return {"boxes": nbox, "sizes": sizes, "batched_ms": batched_ms, "sequential_ms": seq_ms,
+            "speedup_vs_sequential": seq_ms / batched_ms, "cells": cells,
+            "max_rel_res": max(i["rel_res"] for i in infos), "outer_iterations": [i["cycles"] for i in infos],
+            "tune": ctx.tune_log().strip().splitlines()}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -152,6 +200,7 @@ def main():
     ap.add_argument("--sample-n", type=int, default=128)
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 24-box batched-solve leg")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -296,6 +345,8 @@ def main():
         "fma_probe_gflops": {"fp64": fp64_gf, "fp32": fp32_gf},
         "ms_per_step_untraced": ms_untraced,
     }
+    if not args.no_batch:
+        line["batched"] = batched_leg(api, dev, stream)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.sample_n)
     if rank == 0:

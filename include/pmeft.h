@@ -119,6 +119,21 @@ pm_status scalar_mg_solve(pm_ctx* ctx, const double* delta, int n, double alpha_
                           double tol, double* phi_inout, pm_solve_info* info);
 
 /*
+ * Batched scalar-field solve: nbox independent periodic boxes, each with its own mesh size
+ * n[b] (power of two >= 8), density delta[b], parameters (alpha_B0[b], alpha_M0[b], a[b])
+ * and initial guess / result phi_inout[b] (device n[b]^3 doubles).  The arrays of sizes,
+ * pointers and parameters are host arrays of length nbox.  Every box runs the FP32-inner /
+ * FP64-outer defect correction of scalar_mg_solve (precision 1 semantics, whatever
+ * params.precision says) to relative residual <= tol; after one eager iteration, one outer
+ * iteration of all unconverged boxes is a single CUDA graph launch with one branch per box.
+ * infos (host, nullable) receives nbox reports; ms_total is the time of the whole batch.
+ * Returns PM_OK when every box converged, else the first failing box's status.
+ */
+pm_status scalar_mg_solve_batched(pm_ctx* ctx, int nbox, const int* n, const double* const* delta,
+                                  const double* alpha_B0, const double* alpha_M0, const double* a, double tol,
+                                  double* const* phi_inout, pm_solve_info* infos);
+
+/*
  * Force interpolation (Eq. force, Eq. phipsi_mod, Sec. 3.5.2): acc = -grad Psi at the
  * particles, Psi = psi_N + (alpha_B - alpha_M) chi, the five-point fourth-order
  * gradient on the mesh and the CIC weights of the deposit.  phi may be NULL (psi_N

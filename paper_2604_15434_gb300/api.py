@@ -82,6 +82,7 @@ SIGNATURES = {
     "pm_deposit_cic_static": (_I, [_P, _LL, _I, _P, _P]),
     "pm_mg_sweep_f32": (_I, [_P, _P, _P, ctypes.c_float, _I, _D, _D, _D, _P, _I]),
     "pm_tune_log": (_I, [_P, _P, _I]),
+    "scalar_mg_solve_batched": (_I, [_P, _I, _P, _P, _P, _P, _P, _D, _P, _P]),
 }
 
 KERNEL_CLASSES = ("sweep64", "sweep32", "resid64", "resid32", "transfer", "coarsest", "reduce", "pm")
@@ -258,6 +259,26 @@ def scalar_mg_solve(delta, alpha_B0, alpha_M0, a, tol, phi=None, ctx=None, raise
     if st != PM_OK and (raise_on_noconv or st != PM_ERR_NOCONV):
         ctx._check(st)
     return phi, info.as_dict()
+
+
+def scalar_mg_solve_batched(deltas, alpha_B0, alpha_M0, a, tol, phis=None, ctx=None, raise_on_noconv=True):
+    """Solve many boxes at once (see scalar_mg_solve_batched in pmeft.h).  deltas: list of
+    (n_b, n_b, n_b) float64 CUDA tensors; alpha_B0, alpha_M0, a: sequences.  Returns (phis, infos)."""
+    ctx = ctx or default_context()
+    nb = len(deltas)
+    if phis is None:
+        phis = [torch.zeros_like(d) for d in deltas]
+    ns = (ctypes.c_int * nb)(*[d.shape[0] for d in deltas])
+    dp = (ctypes.c_void_p * nb)(*[_ptr(d, shape=(d.shape[0],) * 3, name="delta").value for d in deltas])
+    pp = (ctypes.c_void_p * nb)(*[_ptr(p, shape=(d.shape[0],) * 3, name="phi").value for p, d in zip(phis, deltas)])
+    aB = (ctypes.c_double * nb)(*alpha_B0)
+    aM = (ctypes.c_double * nb)(*alpha_M0)
+    aa = (ctypes.c_double * nb)(*a)
+    infos = (SolveInfo * nb)()
+    st = load().scalar_mg_solve_batched(ctx._h, nb, ns, dp, aB, aM, aa, tol, pp, infos)
+    if st != PM_OK and (raise_on_noconv or st != PM_ERR_NOCONV):
+        ctx._check(st)
+    return phis, [i.as_dict() for i in infos]
 
 
 def force_interp(psi_N, phi, alpha_B0, alpha_M0, a, pos, acc=None, ctx=None):

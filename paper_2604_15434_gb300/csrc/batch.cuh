@@ -1,0 +1,273 @@
+// batch.cuh -- many boxes with their own sizes and EFT parameters in one graph launch per
+// outer iteration (included by mg.cu; uses its kernels and host helpers).
+//
+// Each box runs the mixed-precision defect-correction loop of the single-box solve: an
+// FP64 residual (its gauge multiplier kept on the device), then `inner_cycles` FP32 FAS
+// V-cycles on the correction, the FP64 update and the re-centring.  One outer iteration of
+// every unconverged box is captured into a single CUDA graph with one branch per box, so
+// the small boxes' kernels run side by side and the host issues one launch per iteration.
+// The host reads all boxes' residual norms after each launch (one synchronisation) and
+// rebuilds the graph only when a box converges.  The first iteration runs eagerly so the
+// autotuner has chosen every tile before capture.
+#pragma once
+
+namespace pmeft {
+
+__global__ void k_update_shift(const double* __restrict__ sums, double* __restrict__ lam, float* __restrict__ shift)
+{
+    const double gm = sums[3] > 0.0 ? sums[0] / sums[3] : 0.0;
+    *lam -= gm;
+    *shift = (float)(-gm);
+}
+
+struct BoxRun {
+    Workspace* w = nullptr;
+    pm_coeffs cf{};
+    Coef c{};
+    const double* delta = nullptr;
+    double* phi = nullptr;
+    double fnorm = 0.0, rr = 0.0;
+    int cyc = 0, vcyc = 0;
+    pm_status st = PM_ERR_NOCONV;
+    bool active = false, trivial = false;
+    size_t cells = 0;
+    double hist[64] = {};
+};
+
+static pm_status box_prepare(pm_ctx* ctx, Workspace* w)
+{
+    if (!w->stream) PM_CUDA(cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking));
+    if (!w->partials) PM_CUDA(cudaMalloc(&w->partials, sizeof(double) * kMaxPartials * 8));
+    if (!w->out) PM_CUDA(cudaMalloc(&w->out, sizeof(double) * 64));
+    if (!w->host) PM_CUDA(cudaMallocHost(&w->host, sizeof(double) * 64));
+    if (!w->lam) PM_CUDA(cudaMalloc(&w->lam, sizeof(double)));
+    if (!w->shift) PM_CUDA(cudaMalloc(&w->shift, sizeof(float)));
+    return PM_OK;
+}
+
+// FP64 residual of the box's iterate with the device-side gauge multiplier; updates the
+// multiplier and the inner shift on the device and copies the sums to pinned host memory.
+static void box_residual(Exec* x, BoxRun& B)
+{
+    Workspace* w = B.w;
+    Level<double>& L0 = w->d[0];
+    L0.lamp = w->lam;
+    residual<double, false, true>(x, L0, L0.u[0], B.delta, B.cf.src, 0.0, B.c, w->rplain, w->s[0].bg, w->s[0].gap);
+    x->begin(PM_K_REDUCE);
+    k_update_shift<<<1, 1, 0, x->stream>>>(x->red_out, w->lam, w->shift);
+    x->end();
+    cudaMemcpyAsync(w->host, x->red_out, sizeof(double) * 9, cudaMemcpyDeviceToHost, x->stream);
+}
+
+// One outer iteration after a residual: inner V-cycles, correction, re-centring, residual.
+static void box_iteration(Exec* x, BoxRun& B)
+{
+    Workspace* w = B.w;
+    auto& s = w->s;
+    Level<double>& L0 = w->d[0];
+    for (size_t l = 0; l + 1 < s.size(); ++l) {
+        x->begin(PM_K_TRANSFER);
+        k_restrict<float><<<grid_for(x, s[l + 1].cells), kThreads, 0, x->stream>>>(s[l].bg, s[l + 1].n, s[l + 1].bg);
+        x->end();
+    }
+    s[0].cur = 0;
+    s[0].lamp = w->shift;
+    cudaMemsetAsync(s[0].u[0], 0, B.cells * sizeof(float), x->stream);
+    for (int k = 0; k < x->prm.inner_cycles; ++k) vcycle<float>(x, s, 0, w->rplain, 1.0f, 0.0f, B.c);
+    x->begin(PM_K_REDUCE);
+    k_add_correction<<<grid_for(x, B.cells), kThreads, 0, x->stream>>>(L0.u[0], s[0].u[s[0].cur], B.cells);
+    x->end();
+    recentre<double>(x, L0.u[0], B.cells);
+    box_residual(x, B);
+}
+
+// Host side of the stopping test from the sums of the last residual.
+static void box_check(const pm_params& P, BoxRun& B, double tol)
+{
+    const double* h = B.w->host;
+    const double gm = h[3] > 0.0 ? h[0] / h[3] : 0.0;
+    const double r2 = h[2] - 2.0 * gm * h[1] + gm * gm * h[3];
+    B.rr = B.fnorm > 0.0 ? std::sqrt(r2 > 0.0 ? r2 : 0.0) / B.fnorm : std::sqrt(r2 > 0.0 ? r2 : 0.0);
+    if (B.cyc < 64) B.hist[B.cyc] = B.rr;
+    if (h[4] > 0.0 || !std::isfinite(B.rr)) {
+        B.st = PM_ERR_NONFINITE;
+        B.active = false;
+    } else if (B.rr <= tol || B.fnorm == 0.0) {
+        B.st = PM_OK;
+        B.active = false;
+    } else if (B.cyc >= P.max_cycles) {
+        B.st = PM_ERR_NOCONV;
+        B.active = false;
+    }
+}
+
+pm_status mg_solve_batched(pm_ctx* ctx, int nbox, const int* nn, const double* const* delta, const double* aB0,
+                           const double* aM0, const double* aa, double tol, double* const* phi, pm_solve_info* infos)
+{
+    const pm_params& P = ctx->prm;
+    if ((int)ctx->batch.size() < nbox) ctx->batch.resize(nbox, nullptr);
+    std::vector<BoxRun> B(nbox);
+    cudaEvent_t start, stop, ready;
+    cudaEventCreate(&start);
+    cudaEventCreate(&stop);
+    cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+    cudaEventRecord(start, ctx->stream);
+    cudaEventRecord(ready, ctx->stream);
+    if (!ctx->batch_stream) PM_CUDA(cudaStreamCreateWithFlags(&ctx->batch_stream, cudaStreamNonBlocking));
+    // per-box set-up, eager: workspaces, norms, first residual
+    for (int b = 0; b < nbox; ++b) {
+        BoxRun& R = B[b];
+        coefficients(aB0[b], aM0[b], aa[b], P.omega_m0, P.include_dot_alphaB, &R.cf);
+        R.cells = (size_t)nn[b] * nn[b] * nn[b];
+        R.delta = delta[b];
+        R.phi = phi[b];
+        R.c = Coef{R.cf.nu, R.cf.kappa, P.eta, R.cf.src};
+        if (R.cf.xi == 0.0) {
+            R.trivial = true;
+            R.st = PM_OK;
+            PM_CUDA(cudaMemsetAsync(R.phi, 0, R.cells * sizeof(double), ctx->stream));
+            continue;
+        }
+        if (R.cf.nu == 0.0 || !std::isfinite(R.cf.nu) || !std::isfinite(R.cf.kappa)) {
+            ctx->set_error("box " + std::to_string(b) + ": nu = 0");
+            return PM_ERR_INVALID_ARG;
+        }
+        Workspace*& w = ctx->batch[b];
+        if (w && w->n != nn[b]) {
+            delete_workspace(w);
+            w = nullptr;
+        }
+        if (!w) {
+            w = new Workspace();
+            w->n = nn[b];
+        }
+        R.w = w;
+        PM_TRY(ensure_mg(ctx, w, true));
+        PM_TRY(box_prepare(ctx, w));
+        PM_CUDA(cudaStreamWaitEvent(w->stream, ready, 0));
+        Exec x(ctx, w->stream, w->partials, w->out, w->host, false);
+        PM_TRY(source_norm(&x, R.delta, R.cells, R.cf.src, &R.fnorm));
+        w->d[0].cur = 0;
+        PM_CUDA(cudaMemcpyAsync(w->d[0].u[0], R.phi, R.cells * sizeof(double), cudaMemcpyDeviceToDevice, w->stream));
+        PM_CUDA(cudaMemsetAsync(w->lam, 0, sizeof(double), w->stream));
+        box_residual(&x, R);
+        R.active = true;
+    }
+    for (int b = 0; b < nbox; ++b)
+        if (B[b].active) PM_CUDA(cudaStreamSynchronize(B[b].w->stream));
+    for (int b = 0; b < nbox; ++b)
+        if (B[b].active) box_check(P, B[b], tol);
+    // first iteration eagerly on the boxes' own streams (the autotuner runs here)
+    for (int b = 0; b < nbox; ++b) {
+        if (!B[b].active) continue;
+        Exec x(ctx, B[b].w->stream, B[b].w->partials, B[b].w->out, B[b].w->host, false);
+        box_iteration(&x, B[b]);
+    }
+    for (int b = 0; b < nbox; ++b)
+        if (B[b].active) {
+            PM_CUDA(cudaStreamSynchronize(B[b].w->stream));
+            ++B[b].cyc;
+            B[b].vcyc += P.inner_cycles;
+            box_check(P, B[b], tol);
+        }
+    // graph-captured iterations
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int> members;
+    pm_profile per_launch{};
+    for (;;) {
+        std::vector<int> act;
+        for (int b = 0; b < nbox; ++b)
+            if (B[b].active) act.push_back(b);
+        if (act.empty()) break;
+        if (!exec || act != members) {
+            if (exec) cudaGraphExecDestroy(exec);
+            exec = nullptr;
+            members = act;
+            const pm_profile before = ctx->prof;
+            cudaStream_t ms = ctx->batch_stream;
+            cudaEvent_t fork, join;
+            cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+            PM_CUDA(cudaStreamBeginCapture(ms, cudaStreamCaptureModeThreadLocal));
+            cudaEventRecord(fork, ms);
+            std::vector<cudaEvent_t> joins;
+            for (int b : act) {
+                Workspace* w = B[b].w;
+                cudaStreamWaitEvent(w->stream, fork, 0);
+                Exec x(ctx, w->stream, w->partials, w->out, w->host, false);
+                box_iteration(&x, B[b]);
+                cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+                cudaEventRecord(join, w->stream);
+                cudaStreamWaitEvent(ms, join, 0);
+                joins.push_back(join);
+            }
+            cudaGraph_t g = nullptr;
+            cudaError_t ce = cudaStreamEndCapture(ms, &g);
+            for (auto e : joins) cudaEventDestroy(e);
+            cudaEventDestroy(fork);
+            if (ce != cudaSuccess) {
+                ctx->set_error(std::string("graph capture failed: ") + cudaGetErrorString(ce));
+                return PM_ERR_CUDA;
+            }
+            PM_CUDA(cudaGraphInstantiate(&exec, g, 0));
+            cudaGraphDestroy(g);
+            for (int k = 0; k < PM_K_COUNT; ++k) {
+                per_launch.launches[k] = ctx->prof.launches[k] - before.launches[k];
+                per_launch.fine_launches[k] = ctx->prof.fine_launches[k] - before.fine_launches[k];
+                per_launch.cells[k] = ctx->prof.cells[k] - before.cells[k];
+            }
+            ctx->prof = before;  // capture launched nothing; replays are counted below
+        }
+        PM_CUDA(cudaGraphLaunch(exec, ctx->batch_stream));
+        PM_CUDA(cudaStreamSynchronize(ctx->batch_stream));
+        for (int k = 0; k < PM_K_COUNT; ++k) {
+            ctx->prof.launches[k] += per_launch.launches[k];
+            ctx->prof.fine_launches[k] += per_launch.fine_launches[k];
+            ctx->prof.cells[k] += per_launch.cells[k];
+        }
+        for (int b : act) {
+            ++B[b].cyc;
+            B[b].vcyc += P.inner_cycles;
+            box_check(P, B[b], tol);
+        }
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    // results back to the callers' buffers, ordered after everything on the context stream
+    for (int b = 0; b < nbox; ++b) {
+        if (B[b].trivial) continue;
+        Workspace* w = B[b].w;
+        PM_CUDA(cudaMemcpyAsync(B[b].phi, w->d[0].u[0], B[b].cells * sizeof(double), cudaMemcpyDeviceToDevice,
+                                w->stream));
+        double lam = 0.0;
+        PM_CUDA(cudaMemcpyAsync(&lam, w->lam, sizeof(double), cudaMemcpyDeviceToHost, w->stream));
+        PM_CUDA(cudaStreamSynchronize(w->stream));
+        if (infos) {
+            pm_solve_info& I = infos[b];
+            I = pm_solve_info{};
+            I.cycles = B[b].cyc;
+            I.vcycles = B[b].vcyc;
+            I.status = B[b].st;
+            I.rel_res = B[b].rr;
+            I.lambda = lam;
+            I.floored_cells = (long long)((double)B[b].cells - w->host[3]);
+            I.unstable_nu = B[b].cf.nu <= 0.0;
+            for (int k = 0; k < 64; ++k) I.rel_res_hist[k] = B[b].hist[k];
+        }
+    }
+    cudaEventRecord(stop, ctx->stream);
+    cudaEventSynchronize(stop);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, start, stop);
+    cudaEventDestroy(start);
+    cudaEventDestroy(stop);
+    cudaEventDestroy(ready);
+    pm_status worst = PM_OK;
+    for (int b = 0; b < nbox; ++b) {
+        if (infos) infos[b].ms_total = ms;
+        if (B[b].st != PM_OK && worst == PM_OK) worst = B[b].st;
+    }
+    if (worst == PM_ERR_NOCONV) ctx->set_error("a box reached max_cycles before the tolerance");
+    if (worst == PM_ERR_NONFINITE) ctx->set_error("non-finite residual in a box");
+    return worst;
+}
+
+}  // namespace pmeft

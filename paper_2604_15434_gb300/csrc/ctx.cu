@@ -135,8 +135,10 @@ pm_status ensure_fft(pm_ctx* ctx, Workspace* w)
     return PM_OK;
 }
 
-static void free_workspace(Workspace* w)
+void delete_workspace(Workspace* w)
 {
+    if (!w) return;
+    if (w->stream) cudaStreamSynchronize(w->stream);
     for (auto& L : w->d) free_level(L);
     for (auto& L : w->s) free_level(L);
     cudaFree(w->rplain);
@@ -146,6 +148,13 @@ static void free_workspace(Workspace* w)
     cudaFree(w->spec);
     if (w->plan_r2c) cufftDestroy(w->plan_r2c);
     if (w->plan_c2r) cufftDestroy(w->plan_c2r);
+    cudaFree(w->partials);
+    cudaFree(w->out);
+    cudaFreeHost(w->host);
+    cudaFree(w->lam);
+    cudaFree(w->shift);
+    if (w->graph) cudaGraphExecDestroy(w->graph);
+    if (w->stream) cudaStreamDestroy(w->stream);
     delete w;
 }
 
@@ -227,7 +236,9 @@ extern "C" void pm_destroy(pm_ctx* ctx)
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
-    for (auto& kv : ctx->ws) free_workspace(kv.second);
+    for (auto& kv : ctx->ws) delete_workspace(kv.second);
+    for (auto* w : ctx->batch) delete_workspace(w);
+    if (ctx->batch_stream) cudaStreamDestroy(ctx->batch_stream);
     for (auto& r : ctx->recs) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);

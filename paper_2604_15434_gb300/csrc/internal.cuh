@@ -44,6 +44,7 @@ struct Level {
     T* ur = nullptr;        // restriction of the finer iterate (for the FAS correction)
     T* bg = nullptr;        // background field of the correction form (mixed precision), or null
     T* gap = nullptr;       // L_sat - L(background) from the FP64 iterate (finest inner level), or null
+    const T* lamp = nullptr;   // device scalar added to the right-hand side (graph-captured solves), or null
     uint8_t* kmask = nullptr;  // 1: screening term off (coarse levels)
     uint8_t* sat = nullptr;    // 1: floored piece used by the last residual
     bool fine = false;         // finest level of its hierarchy (for tracing)
@@ -61,6 +62,14 @@ struct Workspace {
     cufftHandle plan_r2c = 0, plan_c2r = 0;
     double2* spec = nullptr;       // n*n*(n/2+1) complex
     bool fft_ready = false;
+    // own stream, reductions and device scalars of one box of a batched solve
+    cudaStream_t stream = nullptr;
+    double* partials = nullptr;    // kMaxPartials * 8
+    double* out = nullptr;         // 64 device results
+    double* host = nullptr;        // 64 pinned host mirror
+    double* lam = nullptr;         // gauge multiplier (device)
+    float* shift = nullptr;        // rhs shift of the inner cycle, -gm (device)
+    cudaGraphExec_t graph = nullptr;
 };
 
 }  // namespace pmeft
@@ -71,6 +80,8 @@ struct pm_ctx {
     pm_params prm{};
     std::string err;
     std::map<int, pmeft::Workspace*> ws;
+    std::vector<pmeft::Workspace*> batch;  // one workspace per box of a batched solve
+    cudaStream_t batch_stream = nullptr;    // capture / launch stream of the batched graph
     double* red_partials = nullptr;  // kMaxPartials * 8 doubles
     double* red_out = nullptr;       // device results (64 doubles: [0..8] residual, [16..] mean, [32..] norms)
     double* host_out = nullptr;      // pinned host mirror (64 doubles)
@@ -129,8 +140,71 @@ struct pm_ctx {
 
 namespace pmeft {
 
+// Where one solve enqueues its work: the stream, its reduction buffers, and whether
+// per-launch event tracing is allowed (not while a stream is being captured into a graph).
+// The single-box solve uses the context's own; each box of a batched solve has its own.
+struct Exec {
+    pm_ctx* c;
+    cudaStream_t stream;
+    double* red_partials;
+    double* red_out;
+    double* host_out;
+    bool trace_ok;
+    const pm_params& prm;
+    int num_sms;
+    std::map<int, int>& tuned;
+    std::string& tune_log;
+    Exec(pm_ctx* ctx, cudaStream_t s, double* part, double* out, double* host, bool trace)
+        : c(ctx), stream(s), red_partials(part), red_out(out), host_out(host), trace_ok(trace), prm(ctx->prm),
+          num_sms(ctx->num_sms), tuned(ctx->tuned), tune_log(ctx->tune_log)
+    {
+    }
+    explicit Exec(pm_ctx* ctx)
+        : Exec(ctx, ctx->stream, ctx->red_partials, ctx->red_out, ctx->host_out, true)
+    {
+    }
+    void set_error(const std::string& m) { c->set_error(m); }
+    bool tracing() const { return trace_ok && c->tracing; }
+    int open_cls = -1;
+    bool open_fine = false;
+    cudaEvent_t open_a = nullptr;
+    void begin(int cls, bool fine = false, long long cells = 0)
+    {
+        c->prof.launches[cls] += 1;
+        if (fine) {
+            c->prof.fine_launches[cls] += 1;
+            c->prof.cells[cls] += cells;
+        }
+        if (!tracing()) return;
+        open_cls = cls;
+        open_fine = fine;
+        open_a = c->ev();
+        cudaEventRecord(open_a, stream);
+    }
+    void end()
+    {
+        if (!tracing() || open_cls < 0) return;
+        cudaEvent_t b = c->ev();
+        cudaEventRecord(b, stream);
+        c->recs.push_back({open_cls, open_fine, open_a, b});
+        open_cls = -1;
+    }
+};
+
+inline int grid_for(Exec* x, size_t work, int threads = 256)
+{
+    size_t blocks = (work + threads - 1) / threads;
+    size_t cap = (size_t)x->num_sms * 16;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    return (int)blocks;
+}
+
 pm_status get_workspace(pm_ctx* ctx, int n, Workspace** out);
+void delete_workspace(Workspace* w);
 pm_status ensure_mg(pm_ctx* ctx, Workspace* w, bool want_fp32);
+pm_status mg_solve_batched(pm_ctx* ctx, int nbox, const int* n, const double* const* delta, const double* aB0,
+                           const double* aM0, const double* a, double tol, double* const* phi, pm_solve_info* infos);
 pm_status ensure_fft(pm_ctx* ctx, Workspace* w);
 bool valid_n(int n);
 int grid_for(pm_ctx* ctx, size_t work, int threads = kThreads);

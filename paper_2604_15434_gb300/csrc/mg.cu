@@ -82,8 +82,9 @@ __global__ void __launch_bounds__(256) k_half_sweep(const T* __restrict__ own, c
                                                     T* __restrict__ out, const T* __restrict__ F, T fscale, T lam,
                                                     const uint8_t* __restrict__ kmask, const T* __restrict__ bg,
                                                     const T* __restrict__ gap, int n, int colour, T ih2, T nu, T kap,
-                                                    T sp, T Df, T lsat_c)
+                                                    T sp, T Df, T lsat_c, const T* __restrict__ lamp)
 {
+    if (lamp) lam += *lamp;
     const int hn = n >> 1;
     const size_t total = (size_t)n * n * hn;
     for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
@@ -115,8 +116,10 @@ __global__ void __launch_bounds__(256) k_residual(const T* __restrict__ u, const
                                                   T lsat_c, bool floor_piece, T* __restrict__ r,
                                                   uint8_t* __restrict__ sat,
                                                   double* __restrict__ partials, float* __restrict__ rplain,
-                                                  float* __restrict__ chi32, float* __restrict__ gap32)
+                                                  float* __restrict__ chi32, float* __restrict__ gap32,
+                                                  const T* __restrict__ lamp)
 {
+    if (lamp) lam += *lamp;
     float fa[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     const size_t total = (size_t)n * n * n;
     for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x) {
@@ -397,7 +400,7 @@ static const FusedCfg kFusedCfgs[] = {{64, 16, 32}, {64, 8, 32}, {64, 8, 64}, {3
 constexpr int kNumFusedCfgs = sizeof(kFusedCfgs) / sizeof(kFusedCfgs[0]);
 
 template <int TX, int TY, bool BG, bool GAP>
-static void launch_fused(pm_ctx* ctx, const float* A, float* B, const float* F, float fscale, float lam,
+static void launch_fused(Exec* ctx, const float* A, float* B, const float* F, float fscale, float lam,
                          const Level<float>& L, int nz, float h2inv, const Coef& c, float sp, float Df, float lsn)
 {
     const int n = L.n;
@@ -406,11 +409,11 @@ static void launch_fused(pm_ctx* ctx, const float* A, float* B, const float* F, 
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     const dim3 grid(n / TX, n / TY, n / nz);
     k<<<grid, 256, sm, ctx->stream>>>(A, B, F, fscale, lam, L.kmask, L.bg, L.gap, n, nz, h2inv, (float)c.nu,
-                                      (float)c.kap, sp, Df, lsn);
+                                      (float)c.kap, sp, Df, lsn, L.lamp);
 }
 
 template <bool BG, bool GAP>
-static void launch_fused_cfg(pm_ctx* ctx, int cfg, const float* A, float* B, const float* F, float fscale, float lam,
+static void launch_fused_cfg(Exec* ctx, int cfg, const float* A, float* B, const float* F, float fscale, float lam,
                              const Level<float>& L, float h2inv, const Coef& c, float sp, float Df, float lsn)
 {
     const FusedCfg& g = kFusedCfgs[cfg];
@@ -433,7 +436,7 @@ static bool fused_cfg_fits(int cfg, int n)
 }
 
 // One red-black sweep of an FP32 level in a single pass (k_sweep_fused) with tile variant cfg.
-static void sweep_fused_f32(pm_ctx* ctx, Level<float>& L, const float* F, float fscale, float lam, const Coef& c,
+static void sweep_fused_f32(Exec* ctx, Level<float>& L, const float* F, float fscale, float lam, const Coef& c,
                             int cfg)
 {
     const int n = L.n;
@@ -455,7 +458,7 @@ static void sweep_fused_f32(pm_ctx* ctx, Level<float>& L, const float* F, float 
 // Autotuner: the first time a level of size n (with a given input set) is swept, every
 // fitting tile variant runs once on the real data (out of place, A -> B, so the state is
 // unchanged whichever runs last) and the fastest is kept for that key.
-static int tuned_cfg(pm_ctx* ctx, Level<float>& L, const float* F, float fscale, float lam, const Coef& c)
+static int tuned_cfg(Exec* ctx, Level<float>& L, const float* F, float fscale, float lam, const Coef& c)
 {
     const int key = L.n * 4 + (L.bg ? 2 : 0) + (L.gap ? 1 : 0);
     auto it = ctx->tuned.find(key);
@@ -466,8 +469,8 @@ static int tuned_cfg(pm_ctx* ctx, Level<float>& L, const float* F, float fscale,
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
-        const bool was = ctx->tracing;
-        ctx->tracing = false;
+        const bool was = ctx->c->tracing;
+        ctx->c->tracing = false;
         for (int cfg = 0; cfg < kNumFusedCfgs; ++cfg) {
             if (!fused_cfg_fits(cfg, L.n)) continue;
             for (int rep = 0; rep < 2; ++rep) {
@@ -484,7 +487,7 @@ static int tuned_cfg(pm_ctx* ctx, Level<float>& L, const float* F, float fscale,
                 }
             }
         }
-        ctx->tracing = was;
+        ctx->c->tracing = was;
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         ctx->tune_log += "sweep32 n=" + std::to_string(L.n) + (L.bg ? " bg" : "") + (L.gap ? " gap" : "") +
@@ -496,7 +499,7 @@ static int tuned_cfg(pm_ctx* ctx, Level<float>& L, const float* F, float fscale,
 }
 
 template <typename T>
-static void sweep(pm_ctx* ctx, Level<T>& L, const T* F, T fscale, T lam, const Coef& c, int force_mode = -1)
+static void sweep(Exec* ctx, Level<T>& L, const T* F, T fscale, T lam, const Coef& c, int force_mode = -1)
 {
     // FP32 levels of at least 256^3 take the single-pass kernel (force_mode 0: two
     // half-sweep launches, 1: single pass, -1: choose by size)
@@ -527,13 +530,13 @@ static void sweep(pm_ctx* ctx, Level<T>& L, const T* F, T fscale, T lam, const C
             ctx->begin(sizeof(T) == 8 ? PM_K_SWEEP64 : PM_K_SWEEP32, L.fine, (long long)(L.cells / 2));
             k_half_sweep<T, true><<<grid, kThreads, 0, ctx->stream>>>(own, oth, B, F, fscale, lam, L.kmask, L.bg,
                                                                       L.gap, n, colour, h2inv, (T)c.nu, (T)c.kap, sp,
-                                                                      (T)(sqDf * sqDf), lsn);
+                                                                      (T)(sqDf * sqDf), lsn, L.lamp);
             ctx->end();
         } else {
             ctx->begin(sizeof(T) == 8 ? PM_K_SWEEP64 : PM_K_SWEEP32, L.fine, (long long)(L.cells / 2));
             k_half_sweep<T, false><<<grid, kThreads, 0, ctx->stream>>>(own, oth, B, F, fscale, lam, L.kmask, nullptr,
                                                                        nullptr, n, colour, h2inv, (T)c.nu, (T)c.kap,
-                                                                       sp, (T)(sqDf * sqDf), lsn);
+                                                                       sp, (T)(sqDf * sqDf), lsn, L.lamp);
             ctx->end();
         }
     }
@@ -541,7 +544,7 @@ static void sweep(pm_ctx* ctx, Level<T>& L, const T* F, T fscale, T lam, const C
 }
 
 template <typename T, bool WRITE_R, bool MIXED>
-static int residual(pm_ctx* ctx, Level<T>& L, const T* u, const T* F, T fscale, T lam, const Coef& c, float* rplain,
+static int residual(Exec* ctx, Level<T>& L, const T* u, const T* F, T fscale, T lam, const Coef& c, float* rplain,
                     float* chi32, float* gap32 = nullptr)
 {
     const int n = L.n;
@@ -554,13 +557,13 @@ static int residual(pm_ctx* ctx, Level<T>& L, const T* u, const T* F, T fscale, 
         ctx->begin(sizeof(T) == 8 ? PM_K_RESID64 : PM_K_RESID32, L.fine, (long long)L.cells);
         k_residual<T, true, WRITE_R, MIXED><<<grid, kThreads, 0, ctx->stream>>>(
             u, F, fscale, lam, L.kmask, L.bg, L.gap, n, h2inv, (T)c.nu, (T)c.kap, (T)(sqDf * sqDf), lsn, L.fine, L.r,
-            L.sat, ctx->red_partials, rplain, chi32, gap32);
+            L.sat, ctx->red_partials, rplain, chi32, gap32, L.lamp);
         ctx->end();
     } else {
         ctx->begin(sizeof(T) == 8 ? PM_K_RESID64 : PM_K_RESID32, L.fine, (long long)L.cells);
         k_residual<T, false, WRITE_R, MIXED><<<grid, kThreads, 0, ctx->stream>>>(
             u, F, fscale, lam, L.kmask, nullptr, nullptr, n, h2inv, (T)c.nu, (T)c.kap, (T)(sqDf * sqDf), lsn, L.fine,
-            L.r, L.sat, ctx->red_partials, rplain, chi32, gap32);
+            L.r, L.sat, ctx->red_partials, rplain, chi32, gap32, L.lamp);
         ctx->end();
     }
     ctx->begin(PM_K_REDUCE, false, 0);
@@ -570,7 +573,7 @@ static int residual(pm_ctx* ctx, Level<T>& L, const T* u, const T* F, T fscale, 
 }
 
 template <typename T>
-static void vcycle(pm_ctx* ctx, std::vector<Level<T>>& lv, int l, const T* F0, T fs0, T lam0, const Coef& c)
+static void vcycle(Exec* ctx, std::vector<Level<T>>& lv, int l, const T* F0, T fs0, T lam0, const Coef& c)
 {
     Level<T>& L = lv[l];
     const T* F = l == 0 ? F0 : L.f;
@@ -621,7 +624,7 @@ static void vcycle(pm_ctx* ctx, std::vector<Level<T>>& lv, int l, const T* F0, T
 }
 
 template <typename T>
-static void recentre(pm_ctx* ctx, T* x, size_t cells)
+static void recentre(Exec* ctx, T* x, size_t cells)
 {
     int grid = grid_for(ctx, cells);
     if (grid > kMaxPartials) grid = kMaxPartials;
@@ -636,7 +639,7 @@ static void recentre(pm_ctx* ctx, T* x, size_t cells)
     ctx->end();
 }
 
-static pm_status read_sums(pm_ctx* ctx, int count)
+static pm_status read_sums(Exec* ctx, int count)
 {
     PM_CUDA(cudaMemcpyAsync(ctx->host_out, ctx->red_out, sizeof(double) * count, cudaMemcpyDeviceToHost, ctx->stream));
     PM_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -644,7 +647,7 @@ static pm_status read_sums(pm_ctx* ctx, int count)
 }
 
 // |f - <f>|_2 for f = src * delta
-static pm_status source_norm(pm_ctx* ctx, const double* delta, size_t cells, double src, double* out)
+static pm_status source_norm(Exec* ctx, const double* delta, size_t cells, double src, double* out)
 {
     int grid = grid_for(ctx, cells);
     if (grid > kMaxPartials) grid = kMaxPartials;
@@ -666,9 +669,11 @@ static pm_status source_norm(pm_ctx* ctx, const double* delta, size_t cells, dou
     return PM_OK;
 }
 
-pm_status mg_solve(pm_ctx* ctx, const double* delta, int n, const pm_coeffs& cf, double tol, double* phi,
+pm_status mg_solve(pm_ctx* pctx, const double* delta, int n, const pm_coeffs& cf, double tol, double* phi,
                    pm_solve_info* info)
 {
+    Exec ex(pctx);
+    Exec* ctx = &ex;
     const pm_params& P = ctx->prm;
     pm_solve_info local{};
     pm_solve_info* inf = info ? info : &local;
@@ -685,9 +690,9 @@ pm_status mg_solve(pm_ctx* ctx, const double* delta, int n, const pm_coeffs& cf,
         return PM_ERR_INVALID_ARG;
     }
     Workspace* w = nullptr;
-    PM_TRY(get_workspace(ctx, n, &w));
+    PM_TRY(get_workspace(pctx, n, &w));
     const bool mixed = P.precision == 1;
-    PM_TRY(ensure_mg(ctx, w, mixed));
+    PM_TRY(ensure_mg(pctx, w, mixed));
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -772,6 +777,8 @@ pm_status mg_solve(pm_ctx* ctx, const double* delta, int n, const pm_coeffs& cf,
 
 }  // namespace pmeft
 
+#include "batch.cuh"
+
 using namespace pmeft;
 
 // ------------------------------------------------------------------ single-operation ABI
@@ -801,7 +808,8 @@ extern "C" pm_status pm_mg_sweep(pm_ctx* ctx, double* u, const double* f, double
     const size_t cells = L.cells;
     PM_CUDA(cudaMemcpyAsync(L.u[0], u, cells * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
     Coef c{nu, kappa, eta, 1.0};
-    sweep<double>(ctx, L, f, 1.0, lambda, c);
+    Exec ex(ctx);
+    sweep<double>(&ex, L, f, 1.0, lambda, c);
     PM_CUDA(cudaMemcpyAsync(u, L.u[L.cur], cells * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
     PM_CUDA(cudaGetLastError());
     return PM_OK;
@@ -823,7 +831,8 @@ extern "C" pm_status pm_mg_sweep_f32(pm_ctx* ctx, float* u, const float* f, floa
     const size_t cells = L.cells;
     PM_CUDA(cudaMemcpyAsync(L.u[0], u, cells * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
     Coef c{nu, kappa, eta, 1.0};
-    sweep<float>(ctx, L, f, 1.0f, lambda, c, mode);
+    Exec ex(ctx);
+    sweep<float>(&ex, L, f, 1.0f, lambda, c, mode);
     PM_CUDA(cudaMemcpyAsync(u, L.u[L.cur], cells * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
     PM_CUDA(cudaGetLastError());
     return PM_OK;
@@ -844,7 +853,8 @@ extern "C" pm_status pm_mg_residual(pm_ctx* ctx, const double* u, const double* 
     L.r = r;
     L.sat = floored ? floored : w->d[0].sat;
     Coef c{nu, kappa, eta, 1.0};
-    residual<double, true, false>(ctx, L, u, f, 1.0, lambda, c, nullptr, nullptr);
+    Exec ex(ctx);
+    residual<double, true, false>(&ex, L, u, f, 1.0, lambda, c, nullptr, nullptr);
     PM_CUDA(cudaGetLastError());
     return PM_OK;
 }
@@ -885,4 +895,23 @@ extern "C" pm_status scalar_mg_solve(pm_ctx* ctx, const double* delta, int n, do
     pm_coeffs cf;
     coefficients(alpha_B0, alpha_M0, a, ctx->prm.omega_m0, ctx->prm.include_dot_alphaB, &cf);
     return mg_solve(ctx, delta, n, cf, tol, phi_inout, info);
+}
+
+extern "C" pm_status scalar_mg_solve_batched(pm_ctx* ctx, int nbox, const int* n, const double* const* delta,
+                                             const double* alpha_B0, const double* alpha_M0, const double* a,
+                                             double tol, double* const* phi_inout, pm_solve_info* infos)
+{
+    if (!ctx) return PM_ERR_INVALID_ARG;
+    if (nbox < 1 || !n || !delta || !alpha_B0 || !alpha_M0 || !a || !phi_inout || !(tol > 0.0)) {
+        ctx->set_error("scalar_mg_solve_batched: bad arguments");
+        return PM_ERR_INVALID_ARG;
+    }
+    for (int b = 0; b < nbox; ++b) {
+        if (!valid_n(n[b]) || !delta[b] || !phi_inout[b] || !(a[b] > 0.0)) {
+            ctx->set_error("scalar_mg_solve_batched: bad box " + std::to_string(b));
+            return PM_ERR_INVALID_ARG;
+        }
+    }
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return PM_ERR_CUDA;
+    return mg_solve_batched(ctx, nbox, n, delta, alpha_B0, alpha_M0, a, tol, phi_inout, infos);
 }

@@ -36,8 +36,9 @@ __global__ void __launch_bounds__(256) k_sweep_fused(const T* __restrict__ U, T*
                                                      const T* __restrict__ F, T fscale, T lam,
                                                      const uint8_t* __restrict__ kmask, const T* __restrict__ bg,
                                                      const T* __restrict__ gap, int n, int NZ, T ih2, T nu, T kap,
-                                                     T sp, T Df, T lsat)
+                                                     T sp, T Df, T lsat, const T* __restrict__ lamp)
 {
+    if (lamp) lam += *lamp;
     using G = FusedGeom<TX, TY>;
     extern __shared__ unsigned char smem_raw[];
     T* su = reinterpret_cast<T*>(smem_raw);            // [4][HU][WU] old values

@@ -275,3 +275,42 @@ def test_mixed_precision_solve_256_uses_fused_sweep(gpu_lib, inner):
                                         ctx=gpu_lib.Context(precision=1, inner_cycles=inner, max_cycles=100))
     assert info["rel_res"] <= 1e-8
     assert float((got - ref).norm() / ref.norm()) < 1e-6
+
+
+# ------------------------------------------------------------------ batched solve
+
+
+def _box_set(sizes, seed):
+    """Zel'dovich sources (P ~ k^-1.5, sigma 1) on mixed sizes, with parameters drawn from
+    alpha_B0 ~ U[-2,0], alpha_M0 ~ U[0,1], a ~ U[0.3,1] and near-singular nu rejected."""
+    params = synth.sample_box_params(len(sizes), seed,
+                                     accept=lambda aB, aM, a: abs(O.coefficients(aB, aM, a)["nu"]) >= 0.1)
+    boxes = []
+    for b, (n, (aB, aM, a, _)) in enumerate(zip(sizes, params)):
+        pos = synth.zeldovich_particles(n, -1.5, 1.0, seed + b)
+        boxes.append((O.density(O.deposit_cic(pos, n), pos.shape[1]), aB, aM, a))
+    return boxes
+
+
+def test_batched_solve_matches_oracle_per_box(gpu_lib):
+    sizes = [16, 32, 64, 32, 16, 64]
+    boxes = _box_set(sizes, 4242)
+    ctx = gpu_lib.Context(max_cycles=100)
+    phis, infos = gpu_lib.scalar_mg_solve_batched([cu(d) for d, *_ in boxes], [b[1] for b in boxes],
+                                                  [b[2] for b in boxes], [b[3] for b in boxes], 1e-8, ctx=ctx)
+    for (d, aB, aM, a), phi, info in zip(boxes, phis, infos):
+        want, _, st = O.scalar_solve(d, aB, aM, a, 1e-12)
+        assert st == 0 and info["status"] == 0 and info["rel_res"] <= 1e-8
+        assert rel(phi.cpu().numpy(), want) < 1e-6, (aB, aM, a, info)
+
+
+def test_batched_solve_equals_single_box_solves(gpu_lib):
+    sizes = [32, 64, 32]
+    boxes = _box_set(sizes, 777)
+    ctx = gpu_lib.Context(max_cycles=100)
+    phis, infos = gpu_lib.scalar_mg_solve_batched([cu(d) for d, *_ in boxes], [b[1] for b in boxes],
+                                                  [b[2] for b in boxes], [b[3] for b in boxes], 1e-9, ctx=ctx)
+    for (d, aB, aM, a), phi, info in zip(boxes, phis, infos):
+        single, sinfo = gpu_lib.scalar_mg_solve(cu(d), aB, aM, a, 1e-9, ctx=gpu_lib.Context(precision=1))
+        assert info["cycles"] == sinfo["cycles"]
+        assert float((phi - single).norm() / single.norm()) < 1e-7
