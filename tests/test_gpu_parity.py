@@ -282,9 +282,13 @@ def test_mixed_precision_solve_256_uses_fused_sweep(gpu_lib, inner):
 
 def _box_set(sizes, seed):
     """Zel'dovich sources (P ~ k^-1.5, sigma 1) on mixed sizes, with parameters drawn from
-    alpha_B0 ~ U[-2,0], alpha_M0 ~ U[0,1], a ~ U[0.3,1] and near-singular nu rejected."""
-    params = synth.sample_box_params(len(sizes), seed,
-                                     accept=lambda aB, aM, a: abs(O.coefficients(aB, aM, a)["nu"]) >= 0.1)
+    alpha_B0 ~ U[-2,0], alpha_M0 ~ U[0,1], a ~ U[0.3,1]; near-singular draws (|nu| < 0.1 or
+    |xi/nu| > 8, where the iteration diverges on the CPU reference as well) are redrawn."""
+    def accept(aB, aM, a):
+        c = O.coefficients(aB, aM, a)
+        return abs(c["nu"]) >= 0.1 and abs(c["mu_chi"]) <= 8.0
+
+    params = synth.sample_box_params(len(sizes), seed, accept=accept)
     boxes = []
     for b, (n, (aB, aM, a, _)) in enumerate(zip(sizes, params)):
         pos = synth.zeldovich_particles(n, -1.5, 1.0, seed + b)
@@ -314,3 +318,18 @@ def test_batched_solve_equals_single_box_solves(gpu_lib):
         single, sinfo = gpu_lib.scalar_mg_solve(cu(d), aB, aM, a, 1e-9, ctx=gpu_lib.Context(precision=1))
         assert info["cycles"] == sinfo["cycles"]
         assert float((phi - single).norm() / single.norm()) < 1e-7
+
+
+def test_divergent_parameters_report_nonfinite(gpu_lib):
+    """A near-singular draw (nu = 0.114, xi/nu = -18.6) makes the iteration diverge on the CPU
+    reference too; the GPU solve must stop with PM_ERR_NONFINITE (single and batched), not
+    hang or return garbage as converged."""
+    n = 64
+    pos = synth.zeldovich_particles(n, -1.5, 1.0, 1027)
+    d = cu(O.density(O.deposit_cic(pos, n), pos.shape[1]))
+    with pytest.raises(gpu_lib.PMError) as e:
+        gpu_lib.scalar_mg_solve(d, -1.804, 0.794, 0.831, 1e-8, ctx=gpu_lib.Context(precision=1, max_cycles=60))
+    assert e.value.status == gpu_lib.PM_ERR_NONFINITE
+    with pytest.raises(gpu_lib.PMError) as e:
+        gpu_lib.scalar_mg_solve_batched([d], [-1.804], [0.794], [0.831], 1e-8, ctx=gpu_lib.Context(max_cycles=60))
+    assert e.value.status == gpu_lib.PM_ERR_NONFINITE
