@@ -63,6 +63,8 @@ typedef struct {
     int unstable_nu;           /* 1 when nu <= 0 (non-viable model, Sec. 2.5) */
     double rel_res_hist[64];   /* rel_res before each cycle, [0..min(cycles, 63)] */
     double ms_total;           /* wall time of the solve on the stream, milliseconds */
+    double guess_rel_res;      /* rel_res of the caller's initial guess */
+    int guess_rejected;        /* 1 when that guess was replaced by chi = 0 (see scalar_mg_solve) */
 } pm_solve_info;
 
 /* EFT coefficients at scale factor a (Sec. 2.2, Eq. alpha-a, G_eff/G, Eq. linearised,
@@ -112,7 +114,10 @@ pm_status poisson_solve(pm_ctx* ctx, const double* delta, int n, double a, doubl
  * phi_inout: device n^3, initial guess on entry (zeros for a cold start), chi on
  * exit.  info (host, nullable) receives the report.  Returns PM_ERR_NOCONV when
  * max_cycles is reached (phi_inout then holds the last iterate), PM_ERR_NONFINITE
- * if the iteration produced NaN/Inf.  params.precision selects the FP64 cycle or the
+ * if the iteration produced NaN/Inf.  An initial guess whose relative residual is not
+ * finite or exceeds 2 (twice the residual of chi = 0 without floored cells, which is f
+ * itself) is replaced by chi = 0 before the first cycle; info.guess_rejected reports it and rel_res_hist then
+ * starts from chi = 0.  params.precision selects the FP64 cycle or the
  * FP32-inner / FP64-outer defect correction.  xi = 0 returns chi = 0 at once.
  */
 pm_status scalar_mg_solve(pm_ctx* ctx, const double* delta, int n, double alpha_B0, double alpha_M0, double a,
@@ -172,6 +177,41 @@ pm_status pm_step(pm_ctx* ctx, double* pos, double* vel, long long np, int n, do
  * the stream to read the overflow flag.
  */
 pm_status pm_deposit_cic_static(const double* pos, long long np, int n, double* delta, void* cuda_stream);
+
+/* ---- learned warm start (spec systems pattern; not in the paper) ----
+ * A periodic 3D U-Net (3 levels, 16/32/64 channels, 3x3x3 convolutions, ReLU) maps
+ * (asinh delta, alpha_B0, alpha_M0, a) to the screened source T = nu L(chi) / src, which is
+ * delta where screening is off.  The warm start is chi_0 = (src/nu) L^-1 T_hat (one FFT
+ * Poisson solve).  Convolutions run on BF16 tensor cores with FP32 accumulation; weights
+ * are kept in FP32 (flat: per conv W[tap][ci][co] then b[co], taps t = (dz+1)*9 + (dy+1)*3
+ * + (dx+1); then the 1x1x1 head w[16], b) and repacked to BF16 after every update.
+ * Grids: n a power of two >= 16.  All buffers device memory unless stated. */
+typedef struct pm_unet pm_unet;
+long long pm_unet_num_params(void);
+pm_status pm_unet_create(pm_ctx* ctx, pm_unet** net);   /* parameters start at zero */
+void pm_unet_destroy(pm_unet* net);
+/* host <-> device copies of the FP32 parameters (which = 0) or accumulated gradients (which = 1) */
+pm_status pm_unet_set_params(pm_unet* net, const float* host, long long count);
+pm_status pm_unet_get_params(pm_unet* net, float* host, long long count, int which);
+/* T_out (n^3 doubles) = network output for delta */
+pm_status pm_unet_forward(pm_unet* net, const double* delta, int n, double alpha_B0, double alpha_M0, double a,
+                          double* T_out);
+/* forward + backward of the loss mean((T_hat - target)^2); gradients are added to the
+ * accumulator; *loss (host) receives the loss.  target: n^3 float. */
+pm_status pm_unet_loss_grad(pm_unet* net, const double* delta, const float* target, int n, double alpha_B0,
+                            double alpha_M0, double a, double* loss);
+/* one Adam step on the accumulated gradients (which it then zeroes) */
+pm_status pm_unet_adam_step(pm_unet* net, float lr, float beta1, float beta2, float eps);
+pm_status pm_unet_zero_grad(pm_unet* net);
+/* training target T = nu L(chi) / src of a solved chi (7-point Laplacian); T_out n^3 float */
+pm_status pm_unet_target(pm_ctx* ctx, const double* chi, int n, double alpha_B0, double alpha_M0, double a,
+                         float* T_out);
+/* initial guesses for scalar_mg_solve: the learned one, and the linear solution
+ * L chi_0 = (xi / nu)(3/2)(G_eff/G) a Omega_m0 delta that the paper's PySCo-EFT starts from (Sec. 3.5.1) */
+pm_status pm_unet_warm_start(pm_unet* net, const double* delta, int n, double alpha_B0, double alpha_M0, double a,
+                             double* phi_out);
+pm_status pm_linear_start(pm_ctx* ctx, const double* delta, int n, double alpha_B0, double alpha_M0, double a,
+                          double* phi_out);
 
 /* ---- tracing: per-kernel-class device time and launch counts ----
  * With tracing on, the library records a CUDA event pair around each of its kernel

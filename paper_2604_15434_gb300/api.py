@@ -38,13 +38,15 @@ class Params(ctypes.Structure):
 class SolveInfo(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int), ("vcycles", ctypes.c_int), ("status", ctypes.c_int), ("rel_res", ctypes.c_double),
                 ("lam", ctypes.c_double), ("floored_cells", ctypes.c_longlong), ("unstable_nu", ctypes.c_int),
-                ("rel_res_hist", ctypes.c_double * 64), ("ms_total", ctypes.c_double)]
+                ("rel_res_hist", ctypes.c_double * 64), ("ms_total", ctypes.c_double),
+                ("guess_rel_res", ctypes.c_double), ("guess_rejected", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         k = min(self.cycles + 1, 64)
         return {"cycles": self.cycles, "vcycles": self.vcycles, "status": self.status, "rel_res": self.rel_res, "lambda": self.lam,
                 "floored_cells": self.floored_cells, "unstable_nu": self.unstable_nu,
-                "hist": list(self.rel_res_hist[:k]), "ms_total": self.ms_total}
+                "hist": list(self.rel_res_hist[:k]), "ms_total": self.ms_total,
+                "guess_rel_res": self.guess_rel_res, "guess_rejected": self.guess_rejected}
 
 
 class Coeffs(ctypes.Structure):
@@ -83,6 +85,18 @@ SIGNATURES = {
     "pm_mg_sweep_f32": (_I, [_P, _P, _P, ctypes.c_float, _I, _D, _D, _D, _P, _I]),
     "pm_tune_log": (_I, [_P, _P, _I]),
     "scalar_mg_solve_batched": (_I, [_P, _I, _P, _P, _P, _P, _P, _D, _P, _P]),
+    "pm_unet_num_params": (_LL, []),
+    "pm_unet_create": (_I, [_P, _P]),
+    "pm_unet_destroy": (None, [_P]),
+    "pm_unet_set_params": (_I, [_P, _P, _LL]),
+    "pm_unet_get_params": (_I, [_P, _P, _LL, _I]),
+    "pm_unet_forward": (_I, [_P, _P, _I, _D, _D, _D, _P]),
+    "pm_unet_loss_grad": (_I, [_P, _P, _P, _I, _D, _D, _D, _P]),
+    "pm_unet_adam_step": (_I, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+    "pm_unet_zero_grad": (_I, [_P]),
+    "pm_unet_target": (_I, [_P, _P, _I, _D, _D, _D, _P]),
+    "pm_unet_warm_start": (_I, [_P, _P, _I, _D, _D, _D, _P]),
+    "pm_linear_start": (_I, [_P, _P, _I, _D, _D, _D, _P]),
 }
 
 KERNEL_CLASSES = ("sweep64", "sweep32", "resid64", "resid32", "transfer", "coarsest", "reduce", "pm")
@@ -353,3 +367,91 @@ def pm_deposit_cic_static(pos, n, delta=None, stream=None):
     st = load().pm_deposit_cic_static(_ptr(pos, name="pos"), pos.shape[1], n, _ptr(delta, shape=(n, n, n)),
                                       ctypes.c_void_p(s.cuda_stream))
     return delta, st
+
+
+class UNet:
+    """The warm-start network (pm_unet): FP32 master parameters on the device, BF16 kernels."""
+
+    def __init__(self, ctx=None):
+        self.ctx = ctx or default_context()
+        h = ctypes.c_void_p()
+        self.ctx._check(load().pm_unet_create(self.ctx._h, ctypes.byref(h)))
+        self._h = h
+        self.num_params = int(load().pm_unet_num_params())
+
+    def set_params(self, p):
+        import numpy as np
+
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        if p.size != self.num_params:
+            raise ValueError(f"expected {self.num_params} parameters, got {p.size}")
+        self.ctx._check(load().pm_unet_set_params(self._h, p.ctypes.data_as(ctypes.c_void_p), p.size))
+
+    def get_params(self, grads=False):
+        import numpy as np
+
+        out = np.empty(self.num_params, dtype=np.float32)
+        self.ctx._check(load().pm_unet_get_params(self._h, out.ctypes.data_as(ctypes.c_void_p), out.size,
+                                                  1 if grads else 0))
+        return out
+
+    def forward(self, delta, alpha_B0, alpha_M0, a):
+        n = delta.shape[0]
+        out = torch.empty_like(delta)
+        self.ctx._check(load().pm_unet_forward(self._h, _ptr(delta, shape=(n, n, n)), n, alpha_B0, alpha_M0, a,
+                                               _ptr(out)))
+        return out
+
+    def loss_grad(self, delta, target, alpha_B0, alpha_M0, a):
+        n = delta.shape[0]
+        loss = ctypes.c_double()
+        self.ctx._check(load().pm_unet_loss_grad(self._h, _ptr(delta, shape=(n, n, n)),
+                                                 _ptr(target, torch.float32, (n, n, n), "target"), n, alpha_B0,
+                                                 alpha_M0, a, ctypes.byref(loss)))
+        return loss.value
+
+    def adam_step(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        self.ctx._check(load().pm_unet_adam_step(self._h, lr, beta1, beta2, eps))
+
+    def zero_grad(self):
+        self.ctx._check(load().pm_unet_zero_grad(self._h))
+
+    def warm_start(self, delta, alpha_B0, alpha_M0, a, phi=None):
+        n = delta.shape[0]
+        if phi is None:
+            phi = torch.empty_like(delta)
+        self.ctx._check(load().pm_unet_warm_start(self._h, _ptr(delta, shape=(n, n, n)), n, alpha_B0, alpha_M0, a,
+                                                  _ptr(phi, shape=(n, n, n))))
+        return phi
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pm_unet_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def unet_target(chi, alpha_B0, alpha_M0, a, ctx=None):
+    """Training target T = nu L(chi) / src of a solved chi (float32 n^3)."""
+    ctx = ctx or default_context()
+    n = chi.shape[0]
+    out = torch.empty((n, n, n), dtype=torch.float32, device=chi.device)
+    ctx._check(load().pm_unet_target(ctx._h, _ptr(chi, shape=(n, n, n)), n, alpha_B0, alpha_M0, a,
+                                     _ptr(out, torch.float32)))
+    return out
+
+
+def linear_start(delta, alpha_B0, alpha_M0, a, phi=None, ctx=None):
+    """The linearised solution the paper's PySCo-EFT starts from (Sec. 3.5.1)."""
+    ctx = ctx or default_context()
+    n = delta.shape[0]
+    if phi is None:
+        phi = torch.empty_like(delta)
+    ctx._check(load().pm_linear_start(ctx._h, _ptr(delta, shape=(n, n, n)), n, alpha_B0, alpha_M0, a,
+                                      _ptr(phi, shape=(n, n, n))))
+    return phi

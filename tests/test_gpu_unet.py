@@ -1,0 +1,116 @@
+"""The warm-start network on the GPU (BF16 tensor cores, FP32 accumulation) against the
+FP64 reference, its training, and what it gains over starting the solve without it."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from oracle import unet as U
+from paper_2604_15434_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def cu(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+@pytest.fixture(scope="module")
+def case():
+    rng = np.random.default_rng(7)
+    n = 16
+    delta = synth.lognormal_delta(n, -2.0, 1.2, 11)
+    target = delta + 0.3 * rng.standard_normal((n, n, n))
+    p = U.init_params(5)
+    p[-1] = 0.1
+    return n, delta, target, p
+
+
+def test_forward_matches_reference(gpu_lib, case):
+    n, delta, target, p = case
+    net = gpu_lib.UNet()
+    net.set_params(p)
+    got = net.forward(cu(delta), -0.8, 0.4, 0.9).cpu().numpy()
+    want, _ = U.forward(p, delta, -0.8, 0.4, 0.9)
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 3e-2  # BF16 activations and weights
+
+
+def test_gradients_match_reference(gpu_lib, case):
+    n, delta, target, p = case
+    net = gpu_lib.UNet()
+    net.set_params(p)
+    net.zero_grad()
+    loss = net.loss_grad(cu(delta), cu(target, torch.float32), -0.8, 0.4, 0.9)
+    g = net.get_params(grads=True).astype(np.float64)
+    loss_o, g_o = U.loss_grad(p, delta, target, -0.8, 0.4, 0.9)
+    assert loss == pytest.approx(loss_o, rel=3e-2)
+    offs = np.cumsum([0] + [27 * ci * co + co for ci, co in U.CONVS] + [17])
+    for k in range(11):
+        a, b = g[offs[k]:offs[k + 1]], g_o[offs[k]:offs[k + 1]]
+        cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-300)
+        assert cos > 0.99, (k, cos)
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) < 0.1, k
+
+
+def test_target_and_linear_start(gpu_lib):
+    n = 32
+    d = synth.lognormal_delta(n, -2.0, 1.5, 3)
+    c = O.coefficients(-0.5, 0.0, 1.0)
+    chi, _, st = O.scalar_solve(d, -0.5, 0.0, 1.0, 1e-12)
+    T = gpu_lib.unet_target(cu(chi), -0.5, 0.0, 1.0).cpu().numpy()
+    want = c["nu"] * O.apply_N(chi, 1.0, 0.0) / c["src"]
+    assert np.abs(T - want).max() <= 1e-5 * np.abs(want).max()
+    lin = gpu_lib.linear_start(cu(d), -0.5, 0.0, 1.0).cpu().numpy()
+    f = O.source(d, c)
+    chi_lin, _, st = O.mg_solve(f, c["nu"], 0.0, 1e-13)
+    assert np.linalg.norm(lin - chi_lin) / np.linalg.norm(chi_lin) < 1e-10
+
+
+def test_training_reduces_the_loss(gpu_lib):
+    from paper_2604_15434_gb300 import learned
+
+    ctx = gpu_lib.Context(precision=1)
+    net = gpu_lib.UNet(ctx)
+    net.set_params(learned.init_params(1))
+    pairs = learned.make_pairs(8, 32, 99, ctx, log=None)
+    first = sum(net.loss_grad(d, T, *p) for d, p, T in pairs) / len(pairs)
+    net.zero_grad()
+    assert len(pairs) >= 6
+    learned.train(net, pairs, epochs=8, lr=3e-3, batch=2, log=None, decay=1.0)  # >= 24 Adam steps
+    last = sum(net.loss_grad(d, T, *p) for d, p, T in pairs) / len(pairs)
+    net.zero_grad()
+    assert last < 0.7 * first
+
+
+WEIGHTS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2604_15434_gb300",
+                       "weights", "unet_128")
+
+
+@pytest.mark.skipif(not os.path.exists(WEIGHTS + ".bin"), reason="trained weights not present")
+def test_trained_warm_start(gpu_lib):
+    """On held-out fields (seeds outside the training range) the learned initial guess has a
+    smaller residual than chi = 0 and than the paper's linear start, takes no more than one
+    extra outer iteration, and converges to the same chi as the cold start."""
+    from paper_2604_15434_gb300 import learned
+
+    ctx = gpu_lib.Context(precision=1, max_cycles=100)
+    net = gpu_lib.UNet(ctx)
+    net.set_params(learned.load_params(WEIGHTS))
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(77777)
+    for kind, aB, aM, a in (("lognormal", -0.5, 0.0, 1.0), ("lognormal", -2.0, 0.0, 1.0),
+                            ("zeldovich", -1.0, 0.2, 1.0), ("zeldovich", -0.8, 0.6, 0.7)):
+        d = learned.gpu_field(128, kind, 1.5, gen, torch.device("cuda"), ctx)
+        chi_cold, cold = gpu_lib.scalar_mg_solve(d, aB, aM, a, 1e-8, ctx=ctx)
+        phi = net.warm_start(d, aB, aM, a)
+        chi_warm, warm = gpu_lib.scalar_mg_solve(d, aB, aM, a, 1e-8, phi=phi, ctx=ctx)
+        phl = gpu_lib.linear_start(d, aB, aM, a)
+        _, lin = gpu_lib.scalar_mg_solve(d, aB, aM, a, 1e-8, phi=phl, ctx=ctx)
+        assert not warm["guess_rejected"]
+        assert warm["guess_rel_res"] < cold["hist"][0]
+        assert warm["guess_rel_res"] < lin["guess_rel_res"]
+        assert warm["cycles"] <= cold["cycles"] + 1
+        err = (chi_warm - chi_cold).norm() / chi_cold.norm()
+        assert err < 1e-6, (kind, aB, aM, a, float(err))
