@@ -1,9 +1,10 @@
 // batch.cuh -- many boxes with their own sizes and EFT parameters in one graph launch per
 // outer iteration (included by mg.cu; uses its kernels and host helpers).
 //
-// Each box runs the mixed-precision defect-correction loop of the single-box solve: an
-// FP64 residual (its gauge multiplier kept on the device), then `inner_cycles` FP32 FAS
-// V-cycles on the correction, the FP64 update and the re-centring.  One outer iteration of
+// Each box runs the mixed-precision defect-correction loop of the single-box solve: a
+// float-float residual (its gauge multiplier kept on the device), then `inner_cycles` FP32
+// FAS V-cycles on the correction and the float-float update; a converged box's result is
+// confirmed by one FP64 residual, as in the single-box solve.  One outer iteration of
 // every unconverged box is captured into a single CUDA graph with one branch per box, so
 // the small boxes' kernels run side by side and the host issues one launch per iteration.
 // The host reads all boxes' residual norms after each launch (one synchronisation) and
@@ -32,6 +33,10 @@ struct BoxRun {
     bool active = false, trivial = false;
     size_t cells = 0;
     double hist[64] = {};
+    double guess_rr = 0.0;
+    bool guess_rejected = false;
+    FFCoef fk{};
+    double lam_fix = 0.0;  // gauge shift found by the confirming FP64 residual
 };
 
 static pm_status box_prepare(pm_ctx* ctx, Workspace* w)
@@ -45,26 +50,24 @@ static pm_status box_prepare(pm_ctx* ctx, Workspace* w)
     return PM_OK;
 }
 
-// FP64 residual of the box's iterate with the device-side gauge multiplier; updates the
-// multiplier and the inner shift on the device and copies the sums to pinned host memory.
+// Float-float residual of the box's iterate with the device-side gauge multiplier;
+// updates the multiplier and the inner shift on the device and copies the sums to pinned
+// host memory.
 static void box_residual(Exec* x, BoxRun& B)
 {
     Workspace* w = B.w;
-    Level<double>& L0 = w->d[0];
-    L0.lamp = w->lam;
-    residual<double, false, true>(x, L0, L0.u[0], B.delta, B.cf.src, 0.0, B.c, w->rplain, w->s[0].bg, w->s[0].gap);
+    residual_ff(x, w, ff_chi(w), ff_rhs(w), 0.0, w->lam, B.fk);
     x->begin(PM_K_REDUCE);
     k_update_shift<<<1, 1, 0, x->stream>>>(x->red_out, w->lam, w->shift);
     x->end();
     cudaMemcpyAsync(w->host, x->red_out, sizeof(double) * 9, cudaMemcpyDeviceToHost, x->stream);
 }
 
-// One outer iteration after a residual: inner V-cycles, correction, re-centring, residual.
+// One outer iteration after a residual: inner V-cycles, the correction, residual.
 static void box_iteration(Exec* x, BoxRun& B)
 {
     Workspace* w = B.w;
     auto& s = w->s;
-    Level<double>& L0 = w->d[0];
     for (size_t l = 0; l + 1 < s.size(); ++l) {
         x->begin(PM_K_TRANSFER);
         k_restrict<float><<<grid_for(x, s[l + 1].cells), kThreads, 0, x->stream>>>(s[l].bg, s[l + 1].n, s[l + 1].bg);
@@ -74,11 +77,22 @@ static void box_iteration(Exec* x, BoxRun& B)
     s[0].lamp = w->shift;
     cudaMemsetAsync(s[0].u[0], 0, B.cells * sizeof(float), x->stream);
     for (int k = 0; k < x->prm.inner_cycles; ++k) vcycle<float>(x, s, 0, w->rplain, 1.0f, 0.0f, B.c);
-    x->begin(PM_K_REDUCE);
-    k_add_correction<<<grid_for(x, B.cells), kThreads, 0, x->stream>>>(L0.u[0], s[0].u[s[0].cur], B.cells);
-    x->end();
-    recentre<double>(x, L0.u[0], B.cells);
+    add_correction_ff(x, ff_chi(w), s[0].u[s[0].cur], B.cells);
     box_residual(x, B);
+}
+
+// FP64 result of a box and its FP64 residual (sums to pinned host memory), eager.
+static void box_confirm(Exec* x, BoxRun& B)
+{
+    Workspace* w = B.w;
+    Level<double>& L0 = w->d[0];
+    x->begin(PM_K_REDUCE);
+    k_from_ff<<<grid_for(x, B.cells), kThreads, 0, x->stream>>>(ff_chi(w), B.cells, L0.u[0]);
+    x->end();
+    L0.lamp = w->lam;
+    residual<double, false, false>(x, L0, L0.u[0], B.delta, B.cf.src, 0.0, B.c, nullptr, nullptr);
+    L0.lamp = nullptr;
+    cudaMemcpyAsync(w->host, x->red_out, sizeof(double) * 9, cudaMemcpyDeviceToHost, x->stream);
 }
 
 // Host side of the stopping test from the sums of the last residual.
@@ -148,15 +162,45 @@ pm_status mg_solve_batched(pm_ctx* ctx, int nbox, const int* nn, const double* c
         Exec x(ctx, w->stream, w->partials, w->out, w->host, false);
         PM_TRY(source_norm(&x, R.delta, R.cells, R.cf.src, &R.fnorm));
         w->d[0].cur = 0;
+        R.fk = make_ffcoef(R.cf.nu, R.cf.kappa, P.eta, nn[b]);
         PM_CUDA(cudaMemcpyAsync(w->d[0].u[0], R.phi, R.cells * sizeof(double), cudaMemcpyDeviceToDevice, w->stream));
+        recentre<double>(&x, w->d[0].u[0], R.cells);
+        x.begin(PM_K_REDUCE);
+        k_to_ff<<<grid_for(&x, R.cells), kThreads, 0, w->stream>>>(R.delta, R.cf.src, R.cells, ff_rhs(w));
+        x.end();
+        x.begin(PM_K_REDUCE);
+        k_to_ff<<<grid_for(&x, R.cells), kThreads, 0, w->stream>>>(w->d[0].u[0], 1.0, R.cells, ff_chi(w));
+        x.end();
         PM_CUDA(cudaMemsetAsync(w->lam, 0, sizeof(double), w->stream));
         box_residual(&x, R);
         R.active = true;
     }
     for (int b = 0; b < nbox; ++b)
         if (B[b].active) PM_CUDA(cudaStreamSynchronize(B[b].w->stream));
-    for (int b = 0; b < nbox; ++b)
-        if (B[b].active) box_check(P, B[b], tol);
+    // a guess worse than chi = 0 (or non-finite) is replaced by zero, as in the single solve
+    bool redo = false;
+    for (int b = 0; b < nbox; ++b) {
+        if (!B[b].active) continue;
+        box_check(P, B[b], tol);
+        B[b].guess_rr = B[b].st == PM_ERR_NONFINITE ? INFINITY : B[b].rr;
+        if (!(B[b].guess_rr <= kGuessLimit)) {
+            BoxRun& R = B[b];
+            R.guess_rejected = true;
+            R.st = PM_ERR_NOCONV;
+            R.active = true;
+            Exec x(ctx, R.w->stream, R.w->partials, R.w->out, R.w->host, false);
+            PM_CUDA(cudaMemsetAsync(ff_chi(R.w), 0, R.cells * sizeof(float2), R.w->stream));
+            PM_CUDA(cudaMemsetAsync(R.w->lam, 0, sizeof(double), R.w->stream));
+            box_residual(&x, R);
+            redo = true;
+        }
+    }
+    if (redo)
+        for (int b = 0; b < nbox; ++b)
+            if (B[b].guess_rejected) {
+                PM_CUDA(cudaStreamSynchronize(B[b].w->stream));
+                box_check(P, B[b], tol);
+            }
     // first iteration eagerly on the boxes' own streams (the autotuner runs here)
     for (int b = 0; b < nbox; ++b) {
         if (!B[b].active) continue;
@@ -231,6 +275,36 @@ pm_status mg_solve_batched(pm_ctx* ctx, int nbox, const int* nn, const double* c
         }
     }
     if (exec) cudaGraphExecDestroy(exec);
+    // FP64 result of every box; a converged box's stop test is confirmed by its FP64
+    // residual (a box that misses it by rounding gets further outer iterations, eagerly)
+    for (int b = 0; b < nbox; ++b) {
+        if (B[b].trivial || !B[b].w) continue;
+        BoxRun& R = B[b];
+        Exec x(ctx, R.w->stream, R.w->partials, R.w->out, R.w->host, false);
+        for (;;) {
+            box_confirm(&x, R);
+            PM_CUDA(cudaStreamSynchronize(R.w->stream));
+            if (R.st != PM_OK) break;
+            double gm64 = 0.0;
+            const double rr64 = rel_from_sums(R.w->host, R.fnorm, &gm64);
+            if (rr64 <= tol || R.fnorm == 0.0) {
+                R.rr = rr64;
+                R.lam_fix = gm64;
+                break;
+            }
+            if (R.cyc >= P.max_cycles) {
+                R.st = PM_ERR_NOCONV;
+                break;
+            }
+            R.active = true;
+            box_iteration(&x, R);
+            PM_CUDA(cudaStreamSynchronize(R.w->stream));
+            ++R.cyc;
+            R.vcyc += P.inner_cycles;
+            R.st = PM_ERR_NOCONV;
+            box_check(P, R, tol);
+        }
+    }
     // results back to the callers' buffers, ordered after everything on the context stream
     for (int b = 0; b < nbox; ++b) {
         if (B[b].trivial) continue;
@@ -247,10 +321,12 @@ pm_status mg_solve_batched(pm_ctx* ctx, int nbox, const int* nn, const double* c
             I.vcycles = B[b].vcyc;
             I.status = B[b].st;
             I.rel_res = B[b].rr;
-            I.lambda = lam;
+            I.lambda = lam - B[b].lam_fix;
             I.floored_cells = (long long)((double)B[b].cells - w->host[3]);
             I.unstable_nu = B[b].cf.nu <= 0.0;
             for (int k = 0; k < 64; ++k) I.rel_res_hist[k] = B[b].hist[k];
+            I.guess_rel_res = B[b].guess_rr;
+            I.guess_rejected = B[b].guess_rejected ? 1 : 0;
         }
     }
     cudaEventRecord(stop, ctx->stream);

@@ -31,6 +31,40 @@ namespace pmeft {
 
 constexpr int kThreads = 256;
 constexpr int kMaxPartials = 4096;  // blocks of a reduction launch (fixed => deterministic)
+// An initial guess whose relative residual exceeds this (the residual of chi = 0 without
+// floored cells is exactly 1) is replaced by chi = 0 before the first cycle.
+constexpr double kGuessLimit = 2.0;
+
+// ------------------------------------------------------------------ block reductions
+
+// 8 running sums per block: [0] sum r, [1] sum r over unfloored, [2] sum r^2,
+// [3] count unfloored, [4] count non-finite, [5] sum x, [6] sum x^2, [7] spare.
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int NV>
+__device__ __forceinline__ void block_sums(double (&v)[NV], double* partials)
+{
+    __shared__ double sh[NV][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double s = warp_sum(v[q]);
+        if (lane == 0) sh[q][wid] = s;
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double s = lane < nw ? sh[q][lane] : 0.0;
+            s = warp_sum(s);
+            if (lane == 0) partials[(size_t)blockIdx.x * 8 + q] = s;
+        }
+    }
+}
 
 // One multigrid level of one precision.  u[0]/u[1] ping-pong under the red-black sweep.
 template <typename T>

@@ -15,39 +15,11 @@
 
 #include "internal.cuh"
 #include "sweep_fused.cuh"
+#include "outer_ff.cuh"
 
 namespace pmeft {
 
 // ------------------------------------------------------------------ reductions
-
-// 8 running sums per block: [0] sum r, [1] sum r over unfloored, [2] sum r^2,
-// [3] count unfloored, [4] count non-finite, [5] sum x, [6] sum x^2, [7] spare.
-__device__ __forceinline__ double warp_sum(double v)
-{
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-template <int NV>
-__device__ __forceinline__ void block_sums(double (&v)[NV], double* partials)
-{
-    __shared__ double sh[NV][32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-        double s = warp_sum(v[q]);
-        if (lane == 0) sh[q][wid] = s;
-    }
-    __syncthreads();
-    if (wid == 0) {
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            double s = lane < nw ? sh[q][lane] : 0.0;
-            s = warp_sum(s);
-            if (lane == 0) partials[(size_t)blockIdx.x * 8 + q] = s;
-        }
-    }
-}
 
 // Sum the per-block partials in a fixed order (deterministic), and derive the gauge
 // shift gm = sum r / count unfloored.  out[0..7] sums, out[8] gm.
@@ -669,6 +641,54 @@ static pm_status source_norm(Exec* ctx, const double* delta, size_t cells, doubl
     return PM_OK;
 }
 
+// float-float outer residual of the mixed path (outer_ff.cuh); sums into red_out[0..8]
+static void residual_ff(Exec* ctx, Workspace* w, const float2* xff, const float2* fff, double lam,
+                        const double* lamp, const FFCoef& fk)
+{
+    const int n = w->n;
+    const size_t cells = (size_t)n * n * n;
+    int grid = grid_for(ctx, cells);
+    if (grid > kMaxPartials) grid = kMaxPartials;
+    ctx->begin(PM_K_RESID64, true, (long long)cells);
+    k_residual_ff<<<grid, kThreads, 0, ctx->stream>>>(xff, fff, lam, lamp, n, fk, w->rplain, w->s[0].bg, w->s[0].gap,
+                                                      ctx->red_partials);
+    ctx->end();
+    ctx->begin(PM_K_REDUCE, false, 0);
+    k_finalize<<<1, 256, 0, ctx->stream>>>(ctx->red_partials, grid, ctx->red_out);
+    ctx->end();
+}
+
+// chi += e - <e> on the float-float iterate
+static void add_correction_ff(Exec* ctx, float2* xff, const float* e, size_t cells)
+{
+    int grid = grid_for(ctx, cells);
+    if (grid > kMaxPartials) grid = kMaxPartials;
+    ctx->begin(PM_K_REDUCE, false, 0);
+    k_sum<float><<<grid, kThreads, 0, ctx->stream>>>(e, cells, ctx->red_partials);
+    ctx->end();
+    ctx->begin(PM_K_REDUCE, false, 0);
+    k_finalize<<<1, 256, 0, ctx->stream>>>(ctx->red_partials, grid, ctx->red_out + 16);
+    ctx->end();
+    ctx->begin(PM_K_REDUCE, false, 0);
+    k_add_correction_ff<<<grid_for(ctx, cells), kThreads, 0, ctx->stream>>>(xff, e, cells, ctx->red_out + 16);
+    ctx->end();
+}
+
+// the float-float iterate and right-hand side of the mixed path live in the FP64 level-0
+// buffers that path does not otherwise use (8 bytes per cell each)
+static float2* ff_chi(Workspace* w) { return reinterpret_cast<float2*>(w->d[0].u[1]); }
+static float2* ff_rhs(Workspace* w) { return reinterpret_cast<float2*>(w->d[0].r); }
+
+// relative residual from the sums of a residual launch (red_out[0..8] as read back)
+static double rel_from_sums(const double* h, double fnorm, double* gm_out)
+{
+    const double gm = h[3] > 0.0 ? h[0] / h[3] : 0.0;
+    const double r2 = h[2] - 2.0 * gm * h[1] + gm * gm * h[3];
+    if (gm_out) *gm_out = gm;
+    const double r = std::sqrt(r2 > 0.0 ? r2 : 0.0);
+    return fnorm > 0.0 ? r / fnorm : r;
+}
+
 pm_status mg_solve(pm_ctx* pctx, const double* delta, int n, const pm_coeffs& cf, double tol, double* phi,
                    pm_solve_info* info)
 {
@@ -703,22 +723,45 @@ pm_status mg_solve(pm_ctx* pctx, const double* delta, int n, const pm_coeffs& cf
     Level<double>& L0 = w->d[0];
     L0.cur = 0;
     PM_CUDA(cudaMemcpyAsync(L0.u[0], phi, cells * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    float2* xff = mixed ? ff_chi(w) : nullptr;
+    float2* fff = mixed ? ff_rhs(w) : nullptr;
+    const FFCoef fk = make_ffcoef(cf.nu, cf.kappa, P.eta, n);
+    if (mixed) {
+        recentre<double>(ctx, L0.u[0], cells);
+        ctx->begin(PM_K_REDUCE, false, 0);
+        k_to_ff<<<grid_for(ctx, cells), kThreads, 0, ctx->stream>>>(delta, cf.src, cells, fff);
+        ctx->end();
+        ctx->begin(PM_K_REDUCE, false, 0);
+        k_to_ff<<<grid_for(ctx, cells), kThreads, 0, ctx->stream>>>(L0.u[0], 1.0, cells, xff);
+        ctx->end();
+    }
     double lam = 0.0, rr = 0.0;
     int cyc = 0, vcyc = 0;
     pm_status st = PM_ERR_NOCONV;
     for (;;) {
         if (mixed)
-            residual<double, false, true>(ctx, L0, L0.u[L0.cur], delta, cf.src, lam, c, w->rplain, w->s[0].bg,
-                                          w->s[0].gap);
+            residual_ff(ctx, w, xff, fff, lam, nullptr, fk);
         else
             residual<double, false, false>(ctx, L0, L0.u[L0.cur], delta, cf.src, lam, c, nullptr, nullptr);
         PM_TRY(read_sums(ctx, 9));
         const double* h = ctx->host_out;
-        const double gm = h[3] > 0.0 ? h[0] / h[3] : 0.0;
+        double gm = 0.0;
+        rr = rel_from_sums(h, fnorm, &gm);
         lam -= gm;
-        const double r2 = h[2] - 2.0 * gm * h[1] + gm * gm * h[3];
-        rr = fnorm > 0.0 ? std::sqrt(r2 > 0.0 ? r2 : 0.0) / fnorm : std::sqrt(r2 > 0.0 ? r2 : 0.0);
         inf->floored_cells = (long long)((double)cells - h[3]);
+        if (cyc == 0 && !inf->guess_rejected) {
+            inf->guess_rel_res = (h[4] > 0.0 || !std::isfinite(rr)) ? INFINITY : rr;
+            if (!(inf->guess_rel_res <= kGuessLimit)) {
+                // the guess is far worse than chi = 0: start from zero instead
+                inf->guess_rejected = 1;
+                lam = 0.0;
+                if (mixed)
+                    PM_CUDA(cudaMemsetAsync(xff, 0, cells * sizeof(float2), ctx->stream));
+                else
+                    PM_CUDA(cudaMemsetAsync(L0.u[L0.cur], 0, cells * sizeof(double), ctx->stream));
+                continue;
+            }
+        }
         if (cyc < 64) inf->rel_res_hist[cyc] = rr;
         if (h[4] > 0.0 || !std::isfinite(rr)) {
             st = PM_ERR_NONFINITE;
@@ -726,8 +769,24 @@ pm_status mg_solve(pm_ctx* pctx, const double* delta, int n, const pm_coeffs& cf
             break;
         }
         if (rr <= tol || fnorm == 0.0) {
-            st = PM_OK;
-            break;
+            if (!mixed) {
+                st = PM_OK;
+                break;
+            }
+            // confirm the float-float stop test with the FP64 residual of the FP64 result
+            ctx->begin(PM_K_REDUCE, false, 0);
+            k_from_ff<<<grid_for(ctx, cells), kThreads, 0, ctx->stream>>>(xff, cells, L0.u[0]);
+            ctx->end();
+            residual<double, false, false>(ctx, L0, L0.u[0], delta, cf.src, lam, c, nullptr, nullptr);
+            PM_TRY(read_sums(ctx, 9));
+            double gm64 = 0.0;
+            const double rr64 = rel_from_sums(ctx->host_out, fnorm, &gm64);
+            if (rr64 <= tol || fnorm == 0.0) {
+                lam -= gm64;
+                rr = rr64;
+                st = PM_OK;
+                break;
+            }
         }
         if (cyc >= P.max_cycles) {
             ctx->set_error("max_cycles reached before the tolerance");
@@ -748,16 +807,18 @@ pm_status mg_solve(pm_ctx* pctx, const double* delta, int n, const pm_coeffs& cf
                 vcycle<float>(ctx, s, 0, w->rplain, 1.0f, (float)(-gm), c);
                 ++vcyc;
             }
-            ctx->begin(PM_K_REDUCE, false, 0);
-            k_add_correction<<<grid_for(ctx, cells), kThreads, 0, ctx->stream>>>(L0.u[L0.cur], s[0].u[s[0].cur],
-                                                                                 cells);
-            ctx->end();
+            add_correction_ff(ctx, xff, s[0].u[s[0].cur], cells);
         } else {
             vcycle<double>(ctx, w->d, 0, delta, cf.src, lam, c);
             ++vcyc;
+            recentre<double>(ctx, L0.u[L0.cur], cells);
         }
-        recentre<double>(ctx, L0.u[L0.cur], cells);
         ++cyc;
+    }
+    if (mixed && st != PM_OK) {
+        ctx->begin(PM_K_REDUCE, false, 0);
+        k_from_ff<<<grid_for(ctx, cells), kThreads, 0, ctx->stream>>>(xff, cells, L0.u[0]);
+        ctx->end();
     }
     PM_CUDA(cudaMemcpyAsync(phi, L0.u[L0.cur], cells * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
     cudaEventRecord(e1, ctx->stream);

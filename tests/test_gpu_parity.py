@@ -333,3 +333,23 @@ def test_divergent_parameters_report_nonfinite(gpu_lib):
     with pytest.raises(gpu_lib.PMError) as e:
         gpu_lib.scalar_mg_solve_batched([d], [-1.804], [0.794], [0.831], 1e-8, ctx=gpu_lib.Context(max_cycles=60))
     assert e.value.status == gpu_lib.PM_ERR_NONFINITE
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_bad_initial_guess_is_replaced_by_zero(gpu_lib, precision):
+    """A guess far worse than chi = 0 (here the unscreened linear solution scaled up, whose
+    nonlinear term blows up) is dropped before the first cycle: the solve reports it and
+    converges to the same chi as the cold start."""
+    n = 32
+    d = synth.lognormal_delta(n, -2.0, 1.5, 1003)
+    ctx = gpu_lib.Context(precision=precision, max_cycles=100)
+    chi_cold, cold = gpu_lib.scalar_mg_solve(cu(d), -2.0, 0.0, 1.0, 1e-9, ctx=ctx)
+    assert not cold["guess_rejected"] and cold["guess_rel_res"] == cold["hist"][0]
+    bad = 50.0 * gpu_lib.linear_start(cu(d), -2.0, 0.0, 1.0, ctx=ctx)
+    chi, info = gpu_lib.scalar_mg_solve(cu(d), -2.0, 0.0, 1.0, 1e-9, phi=bad.clone(), ctx=ctx)
+    assert info["guess_rejected"] == 1 and info["guess_rel_res"] > 2.0
+    assert info["cycles"] == cold["cycles"]
+    assert float((chi - chi_cold).norm() / chi_cold.norm()) < 1e-10
+    phis, infos = gpu_lib.scalar_mg_solve_batched([cu(d)], [-2.0], [0.0], [1.0], 1e-9, phis=[bad.clone()],
+                                                  ctx=gpu_lib.Context(max_cycles=100))
+    assert infos[0]["guess_rejected"] == 1
