@@ -264,9 +264,13 @@ pm_status pm_mg_sweep(pm_ctx* ctx, double* u, const double* f, double lambda, in
 /* The same sweep on an FP32 grid: mode 0 runs the two half-sweep kernels, mode k >= 1
  * the single-pass fused kernel with tile variant k-1 (pm_tune_log lists the variants the
  * autotuner chose; the inner FP32 cycle uses the fused kernel for grids >= 256^3).  A
- * variant that does not tile n falls back to mode 0.  u, f: device n^3 float. */
+ * variant that does not tile n falls back to mode 0.  u, f: device n^3 float.
+ * bg (nullable): the correction form of the mixed-precision inner cycle, where u is the
+ * correction to the background bg and the operator is N(bg + u) - N(bg); gap (nullable,
+ * needs bg): L_sat - L(bg) per cell, as the finest inner level receives it from the outer
+ * residual. */
 pm_status pm_mg_sweep_f32(pm_ctx* ctx, float* u, const float* f, float lambda, int n, double nu, double kappa,
-                          double eta, const unsigned char* kmask, int mode);
+                          double eta, const unsigned char* kmask, const float* bg, const float* gap, int mode);
 /* Residual: r = f + lambda - N(u) in cells with a real root, nu (L_sat - L(u)) in floored
  * cells; floored (device n^3 bytes, nullable) receives the floored-cell flags. */
 pm_status pm_mg_residual(pm_ctx* ctx, const double* u, const double* f, double lambda, int n, double nu,

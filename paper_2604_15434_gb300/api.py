@@ -82,7 +82,7 @@ SIGNATURES = {
     "pm_trace_reset": (_I, [_P]),
     "pm_probe_fma": (_I, [_P, _P, _P]),
     "pm_deposit_cic_static": (_I, [_P, _LL, _I, _P, _P]),
-    "pm_mg_sweep_f32": (_I, [_P, _P, _P, ctypes.c_float, _I, _D, _D, _D, _P, _I]),
+    "pm_mg_sweep_f32": (_I, [_P, _P, _P, ctypes.c_float, _I, _D, _D, _D, _P, _P, _P, _I]),
     "pm_tune_log": (_I, [_P, _P, _I]),
     "scalar_mg_solve_batched": (_I, [_P, _I, _P, _P, _P, _P, _P, _D, _P, _P]),
     "pm_unet_num_params": (_LL, []),
@@ -323,12 +323,15 @@ def pm_mg_sweep(u, f, lam, nu, kappa, eta, kmask=None, ctx=None):
     return u
 
 
-def pm_mg_sweep_f32(u, f, lam, nu, kappa, eta, kmask=None, mode=1, ctx=None):
-    """One red-black sweep of an FP32 grid in place; mode 0: two half-sweep launches, 1: single pass."""
+def pm_mg_sweep_f32(u, f, lam, nu, kappa, eta, kmask=None, mode=1, bg=None, gap=None, ctx=None):
+    """One red-black sweep of an FP32 grid in place; mode 0: two half-sweep launches, k >= 1: the
+    single-pass kernel with tile variant k-1.  bg / gap: the correction form (see pmeft.h)."""
     ctx = ctx or default_context()
     n = u.shape[0]
     ctx._check(load().pm_mg_sweep_f32(ctx._h, _ptr(u, torch.float32, (n, n, n)), _ptr(f, torch.float32, (n, n, n)),
-                                      lam, n, nu, kappa, eta, _ptr(kmask, torch.uint8, (n, n, n), "kmask"), mode))
+                                      lam, n, nu, kappa, eta, _ptr(kmask, torch.uint8, (n, n, n), "kmask"),
+                                      _ptr(bg, torch.float32, (n, n, n), "bg"), _ptr(gap, torch.float32, (n, n, n), "gap"),
+                                      mode))
     return u
 
 

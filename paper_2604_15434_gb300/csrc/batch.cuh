@@ -89,6 +89,7 @@ static void box_confirm(Exec* x, BoxRun& B)
     x->begin(PM_K_REDUCE);
     k_from_ff<<<grid_for(x, B.cells), kThreads, 0, x->stream>>>(ff_chi(w), B.cells, L0.u[0]);
     x->end();
+    recentre<double>(x, L0.u[0], B.cells);
     L0.lamp = w->lam;
     residual<double, false, false>(x, L0, L0.u[0], B.delta, B.cf.src, 0.0, B.c, nullptr, nullptr);
     L0.lamp = nullptr;

@@ -46,7 +46,7 @@ __device__ __forceinline__ double warp_sum(double v)
 }
 
 template <int NV>
-__device__ __forceinline__ void block_sums(double (&v)[NV], double* partials)
+__device__ __forceinline__ void block_sums(double (&v)[NV], double* partials, unsigned block)
 {
     __shared__ double sh[NV][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -61,9 +61,15 @@ __device__ __forceinline__ void block_sums(double (&v)[NV], double* partials)
         for (int q = 0; q < NV; ++q) {
             double s = lane < nw ? sh[q][lane] : 0.0;
             s = warp_sum(s);
-            if (lane == 0) partials[(size_t)blockIdx.x * 8 + q] = s;
+            if (lane == 0) partials[(size_t)block * 8 + q] = s;
         }
     }
+}
+
+template <int NV>
+__device__ __forceinline__ void block_sums(double (&v)[NV], double* partials)
+{
+    block_sums<NV>(v, partials, blockIdx.x);
 }
 
 // One multigrid level of one precision.  u[0]/u[1] ping-pong under the red-black sweep.

@@ -16,6 +16,7 @@
 #include "internal.cuh"
 #include "sweep_fused.cuh"
 #include "outer_ff.cuh"
+#include "resid_fused.cuh"
 
 namespace pmeft {
 
@@ -59,10 +60,11 @@ __global__ void __launch_bounds__(256) k_half_sweep(const T* __restrict__ own, c
     if (lamp) lam += *lamp;
     const int hn = n >> 1;
     const size_t total = (size_t)n * n * hn;
+    const int lg = __ffs(n) - 1;
     for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-        const int m = (int)(t % hn);
-        const size_t row = t / hn;
-        const int j = (int)(row % n), k = (int)(row / n);
+        const int m = (int)(t & (size_t)(hn - 1));  // n (hence hn) is a power of two
+        const size_t row = t >> (lg - 1);
+        const int j = (int)(row & (size_t)(n - 1)), k = (int)(row >> lg);
         const int i = 2 * m + ((j + k + colour) & 1);
         const size_t c = row * n + i;
         Stencil<T> s = load_stencil(own, oth, i, j, k, n);
@@ -94,10 +96,11 @@ __global__ void __launch_bounds__(256) k_residual(const T* __restrict__ u, const
     if (lamp) lam += *lamp;
     float fa[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     const size_t total = (size_t)n * n * n;
+    const int lg = __ffs(n) - 1;
     for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(c % n);
-        const size_t row = c / n;
-        const int j = (int)(row % n), k = (int)(row / n);
+        const int i = (int)(c & (size_t)(n - 1));  // n is a power of two
+        const size_t row = c >> lg;
+        const int j = (int)(row & (size_t)(n - 1)), k = (int)(row >> lg);
         Stencil<T> s = load_stencil(u, u, i, j, k, n);
         Stencil<T> b;
         if (BG) b = load_stencil(bg, bg, i, j, k, n);
@@ -153,10 +156,11 @@ __global__ void __launch_bounds__(256) k_restrict_fas(const T* __restrict__ uf, 
     const int nf = 2 * nc;
     const size_t total = (size_t)nc * nc * nc;
     const T gm = gm_ptr ? (T)(*gm_ptr) : T(0);
+    const int lgc = __ffs(nc) - 1;
     for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x) {
-        const int I = (int)(c % nc);
-        const size_t row = c / nc;
-        const int J = (int)(row % nc), K = (int)(row / nc);
+        const int I = (int)(c & (size_t)(nc - 1));  // nc is a power of two
+        const size_t row = c >> lgc;
+        const int J = (int)(row & (size_t)(nc - 1)), K = (int)(row >> lgc);
         T su = T(0), sr = T(0);
         int cnt = 0;
 #pragma unroll
@@ -182,10 +186,11 @@ __global__ void k_restrict(const T* __restrict__ uf, int nc, T* __restrict__ uc)
 {
     const int nf = 2 * nc;
     const size_t total = (size_t)nc * nc * nc;
+    const int lgc = __ffs(nc) - 1;
     for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x) {
-        const int I = (int)(c % nc);
-        const size_t row = c / nc;
-        const int J = (int)(row % nc), K = (int)(row / nc);
+        const int I = (int)(c & (size_t)(nc - 1));  // nc is a power of two
+        const size_t row = c >> lgc;
+        const int J = (int)(row & (size_t)(nc - 1)), K = (int)(row >> lgc);
         T su = T(0);
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -203,10 +208,11 @@ __global__ void __launch_bounds__(256) k_fas_rhs(const T* __restrict__ uc, const
                                                  T ih2, T nu, T kap, T* __restrict__ fc)
 {
     const size_t total = (size_t)n * n * n;
+    const int lg = __ffs(n) - 1;
     for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(c % n);
-        const size_t row = c / n;
-        const int j = (int)(row % n), k = (int)(row / n);
+        const int i = (int)(c & (size_t)(n - 1));  // n is a power of two
+        const size_t row = c >> lg;
+        const int j = (int)(row & (size_t)(n - 1)), k = (int)(row >> lg);
         Stencil<T> s = load_stencil(uc, uc, i, j, k, n);
         Stencil<T> b;
         if (BG) b = load_stencil(bg, bg, i, j, k, n);
@@ -216,30 +222,55 @@ __global__ void __launch_bounds__(256) k_fas_rhs(const T* __restrict__ uc, const
     }
 }
 
-// fine += trilinear cell-centred prolongation of (uc - ur), periodic.
+// fine += trilinear cell-centred prolongation of (uc - ur), periodic.  One thread per
+// coarse cell writes its 8 children: the 3x3x3 coarse neighbourhood is interpolated
+// separably (weights 3/4 and 1/4 per axis, i.e. 27/64, 9/64, 3/64, 1/64 in 3D), and the
+// children are updated as pairs along x (8-byte / 16-byte accesses).
 template <typename T>
 __global__ void __launch_bounds__(256) k_prolong_add(const T* __restrict__ uc, const T* __restrict__ ur, int nc,
                                                      T* __restrict__ uf)
 {
     const int nf = 2 * nc, mc = nc - 1;
-    const size_t total = (size_t)nf * nf * nf;
+    const int lgc = __ffs(nc) - 1;
+    const size_t total = (size_t)nc * nc * nc;
+    const T a = T(0.75), b = T(0.25);
     for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(c % nf);
-        const size_t row = c / nf;
-        const int j = (int)(row % nf), k = (int)(row / nf);
-        const int P0 = i >> 1, P1 = j >> 1, P2 = k >> 1;
-        const int Q0 = (i & 1) ? ((P0 + 1) & mc) : ((P0 - 1) & mc);
-        const int Q1 = (j & 1) ? ((P1 + 1) & mc) : ((P1 - 1) & mc);
-        const int Q2 = (k & 1) ? ((P2 + 1) & mc) : ((P2 - 1) & mc);
-        T s = T(0);
+        const int I = (int)(c & (size_t)mc);  // nc is a power of two
+        const size_t row = c >> lgc;
+        const int J = (int)(row & (size_t)mc), K = (int)(row >> lgc);
+        const int xs[3] = {(I - 1) & mc, I, (I + 1) & mc};
+        const int ys[3] = {(J - 1) & mc, J, (J + 1) & mc};
+        const int zs[3] = {(K - 1) & mc, K, (K + 1) & mc};
+        // along x: px[z][y][child]
+        T px[3][3][2];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int ii = (q & 1) ? Q0 : P0, jj = (q & 2) ? Q1 : P1, kk = (q & 4) ? Q2 : P2;
-            const T w = ((q & 1) ? T(0.25) : T(0.75)) * ((q & 2) ? T(0.25) : T(0.75)) * ((q & 4) ? T(0.25) : T(0.75));
-            const size_t g = ((size_t)kk * nc + jj) * nc + ii;
-            s += w * (ur ? uc[g] - ur[g] : uc[g]);
-        }
-        uf[c] += s;
+        for (int kz = 0; kz < 3; ++kz)
+#pragma unroll
+            for (int jy = 0; jy < 3; ++jy) {
+                const size_t base = ((size_t)zs[kz] * nc + ys[jy]) * nc;
+                T v[3];
+#pragma unroll
+                for (int ix = 0; ix < 3; ++ix) v[ix] = ur ? uc[base + xs[ix]] - ur[base + xs[ix]] : uc[base + xs[ix]];
+                px[kz][jy][0] = a * v[1] + b * v[0];
+                px[kz][jy][1] = a * v[1] + b * v[2];
+            }
+        // along y, then z, then add to the children
+#pragma unroll
+        for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy) {
+                T out[2];
+#pragma unroll
+                for (int dx = 0; dx < 2; ++dx) {
+                    T py[3];
+#pragma unroll
+                    for (int kz = 0; kz < 3; ++kz) py[kz] = a * px[kz][1][dx] + b * px[kz][dy ? 2 : 0][dx];
+                    out[dx] = a * py[1] + b * py[dz ? 2 : 0];
+                }
+                T* f = uf + ((size_t)(2 * K + dz) * nf + (2 * J + dy)) * nf + 2 * I;
+                f[0] += out[0];
+                f[1] += out[1];
+            }
     }
 }
 
@@ -320,10 +351,30 @@ template <typename T>
 __global__ void k_sum(const T* __restrict__ x, size_t total, double* __restrict__ partials)
 {
     double v[2] = {0.0, 0.0};
-    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x) {
-        const double d = (double)x[c];
-        v[0] += d;
-        v[1] += d * d;
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+    if constexpr (sizeof(T) == 4) {
+        // FP32 data: 16-byte loads and FP32 per-thread sums (a few hundred terms each; the
+        // FP64 pipe would otherwise bound the pass), FP64 across threads
+        float a = 0.f, b = 0.f;
+        const size_t n4 = total / 4;
+        const float4* x4 = reinterpret_cast<const float4*>(x);
+        for (size_t c = tid; c < n4; c += stride) {
+            const float4 q = x4[c];
+            a += (q.x + q.y) + (q.z + q.w);
+            b += (q.x * q.x + q.y * q.y) + (q.z * q.z + q.w * q.w);
+        }
+        for (size_t c = 4 * n4 + tid; c < total; c += stride) {
+            a += (float)x[c];
+            b += (float)x[c] * (float)x[c];
+        }
+        v[0] = a;
+        v[1] = b;
+    } else {
+        for (size_t c = tid; c < total; c += stride) {
+            const double d = (double)x[c];
+            v[0] += d;
+            v[1] += d * d;
+        }
     }
     block_sums<2>(v, partials);
 }
@@ -362,6 +413,7 @@ struct Coef {
 };
 
 constexpr int kFusedMinN = 256;
+constexpr int kResidZmMinN = 128;  // FP32 residual: z-marching kernel from this size up
 
 // Tile variants of the single-pass FP32 sweep: (TX, TY) x-y tile, NZ planes per block.
 struct FusedCfg {
@@ -525,6 +577,32 @@ static int residual(Exec* ctx, Level<T>& L, const T* u, const T* F, T fscale, T 
     int grid = grid_for(ctx, L.cells);
     if (grid > kMaxPartials) grid = kMaxPartials;
     const T lsn = c.kap != 0.0 ? (T)(0.75 * c.nu * (1.0 - c.eta) / c.kap) : T(0);  // L_sat
+    if constexpr (sizeof(T) == 4 && WRITE_R && !MIXED) {
+        // large FP32 levels: the z-marching kernel, one block per 64 x 8 x NZ brick
+        if (n >= kResidZmMinN) {
+            int nz = 8;
+            while ((size_t)(n / kRzTX) * (n / kRzTY) * (n / nz) > (size_t)kMaxPartials) nz *= 2;
+            const dim3 g3(n / kRzTX, n / kRzTY, n / nz);
+            const int nb = (int)(g3.x * g3.y * g3.z);
+            ctx->begin(PM_K_RESID32, L.fine, (long long)L.cells);
+            if (L.bg) {
+                constexpr size_t sm = resid_zm_smem_bytes<true>();
+                k_residual_zm<true><<<g3, 256, sm, ctx->stream>>>(u, F, fscale, lam, L.kmask, L.bg, L.gap, n, nz,
+                                                                  h2inv, (T)c.nu, (T)c.kap, (T)(sqDf * sqDf), lsn,
+                                                                  L.fine, L.r, L.sat, ctx->red_partials, L.lamp);
+            } else {
+                constexpr size_t sm = resid_zm_smem_bytes<false>();
+                k_residual_zm<false><<<g3, 256, sm, ctx->stream>>>(u, F, fscale, lam, L.kmask, nullptr, nullptr, n, nz,
+                                                                   h2inv, (T)c.nu, (T)c.kap, (T)(sqDf * sqDf), lsn,
+                                                                   L.fine, L.r, L.sat, ctx->red_partials, L.lamp);
+            }
+            ctx->end();
+            ctx->begin(PM_K_REDUCE, false, 0);
+            k_finalize<<<1, 256, 0, ctx->stream>>>(ctx->red_partials, nb, ctx->red_out);
+            ctx->end();
+            return nb;
+        }
+    }
     if (L.bg) {
         ctx->begin(sizeof(T) == 8 ? PM_K_RESID64 : PM_K_RESID32, L.fine, (long long)L.cells);
         k_residual<T, true, WRITE_R, MIXED><<<grid, kThreads, 0, ctx->stream>>>(
@@ -590,7 +668,7 @@ static void vcycle(Exec* ctx, std::vector<Level<T>>& lv, int l, const T* F0, T f
     }
     vcycle(ctx, lv, l + 1, F0, fs0, lam0, c);
     ctx->begin(PM_K_TRANSFER, false, 0);
-    k_prolong_add<T><<<grid_for(ctx, L.cells), kThreads, 0, ctx->stream>>>(C.u[C.cur], C.ur, C.n, L.u[L.cur]);
+    k_prolong_add<T><<<grid_for(ctx, C.cells), kThreads, 0, ctx->stream>>>(C.u[C.cur], C.ur, C.n, L.u[L.cur]);
     ctx->end();
     for (int s = 0; s < ctx->prm.npost; ++s) sweep(ctx, L, F, fs, lam, c);
 }
@@ -650,8 +728,17 @@ static void residual_ff(Exec* ctx, Workspace* w, const float2* xff, const float2
     int grid = grid_for(ctx, cells);
     if (grid > kMaxPartials) grid = kMaxPartials;
     ctx->begin(PM_K_RESID64, true, (long long)cells);
-    k_residual_ff<<<grid, kThreads, 0, ctx->stream>>>(xff, fff, lam, lamp, n, fk, w->rplain, w->s[0].bg, w->s[0].gap,
-                                                      ctx->red_partials);
+    if (n >= kFzTX) {
+        int nz = 8 < n ? 8 : n;
+        while ((size_t)(n / kFzTX) * (n / kFzTY) * (n / nz) > (size_t)kMaxPartials) nz *= 2;
+        const dim3 g3(n / kFzTX, n / kFzTY, n / nz);
+        grid = (int)(g3.x * g3.y * g3.z);
+        k_residual_ff_zm<<<g3, 256, kFzSmem, ctx->stream>>>(xff, fff, lam, lamp, n, nz, fk, w->rplain, w->s[0].bg,
+                                                            w->s[0].gap, ctx->red_partials);
+    } else {
+        k_residual_ff<<<grid, kThreads, 0, ctx->stream>>>(xff, fff, lam, lamp, n, fk, w->rplain, w->s[0].bg,
+                                                          w->s[0].gap, ctx->red_partials);
+    }
     ctx->end();
     ctx->begin(PM_K_REDUCE, false, 0);
     k_finalize<<<1, 256, 0, ctx->stream>>>(ctx->red_partials, grid, ctx->red_out);
@@ -815,10 +902,13 @@ pm_status mg_solve(pm_ctx* pctx, const double* delta, int n, const pm_coeffs& cf
         }
         ++cyc;
     }
-    if (mixed && st != PM_OK) {
-        ctx->begin(PM_K_REDUCE, false, 0);
-        k_from_ff<<<grid_for(ctx, cells), kThreads, 0, ctx->stream>>>(xff, cells, L0.u[0]);
-        ctx->end();
+    if (mixed) {
+        if (st != PM_OK) {
+            ctx->begin(PM_K_REDUCE, false, 0);
+            k_from_ff<<<grid_for(ctx, cells), kThreads, 0, ctx->stream>>>(xff, cells, L0.u[0]);
+            ctx->end();
+        }
+        recentre<double>(ctx, L0.u[0], cells);  // <chi> = 0 to FP64 rounding
     }
     PM_CUDA(cudaMemcpyAsync(phi, L0.u[L0.cur], cells * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
     cudaEventRecord(e1, ctx->stream);
@@ -877,17 +967,18 @@ extern "C" pm_status pm_mg_sweep(pm_ctx* ctx, double* u, const double* f, double
 }
 
 extern "C" pm_status pm_mg_sweep_f32(pm_ctx* ctx, float* u, const float* f, float lambda, int n, double nu,
-                                     double kappa, double eta, const unsigned char* kmask, int mode)
+                                     double kappa, double eta, const unsigned char* kmask, const float* bg,
+                                     const float* gap, int mode)
 {
     PM_TRY(check_mg_args(ctx, n));
-    if (!u || !f || mode < 0 || mode > kNumFusedCfgs) return PM_ERR_INVALID_ARG;
+    if (!u || !f || mode < 0 || mode > kNumFusedCfgs || (gap && !bg)) return PM_ERR_INVALID_ARG;
     Workspace* w = nullptr;
     PM_TRY(get_workspace(ctx, n, &w));
     PM_TRY(ensure_mg(ctx, w, true));
-    Level<float> L = w->s[0];  // borrow the buffers, with the caller's mask and no background
+    Level<float> L = w->s[0];  // borrow the buffers, with the caller's mask, background and gap
     L.kmask = (uint8_t*)kmask;
-    L.bg = nullptr;
-    L.gap = nullptr;
+    L.bg = (float*)bg;
+    L.gap = (float*)gap;
     L.cur = 0;
     const size_t cells = L.cells;
     PM_CUDA(cudaMemcpyAsync(L.u[0], u, cells * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
@@ -938,7 +1029,7 @@ extern "C" pm_status pm_mg_prolong_add(pm_ctx* ctx, const double* coarse, int n,
     if (!fine || !coarse) return PM_ERR_INVALID_ARG;
     const int nc = n / 2;
     ctx->begin(PM_K_TRANSFER, false, 0);
-    k_prolong_add<double><<<grid_for(ctx, (size_t)n * n * n), kThreads, 0, ctx->stream>>>(coarse, nullptr, nc, fine);
+    k_prolong_add<double><<<grid_for(ctx, (size_t)nc * nc * nc), kThreads, 0, ctx->stream>>>(coarse, nullptr, nc, fine);
     ctx->end();
     PM_CUDA(cudaGetLastError());
     return PM_OK;

@@ -18,6 +18,7 @@
 #pragma once
 
 #include "internal.cuh"
+#include "sweep_fused.cuh"
 
 namespace pmeft {
 
@@ -210,6 +211,177 @@ __global__ void __launch_bounds__(256) k_residual_ff(const float2* __restrict__ 
 #pragma unroll
     for (int q = 0; q < 5; ++q) acc[q] = (double)fa[q];
     block_sums<5>(acc, partials);
+}
+
+
+// ------------------------------------------------------------------ two cells per thread
+//
+// Blackwell issues FADD2 / FMUL2 / FFMA2: one instruction for a float2 of operations, each
+// component rounded exactly as its scalar form.  The z-marching residual below keeps two
+// cells per thread in the two components (hi parts in one float2, lo parts in another), so
+// every error-free transformation costs the instructions of one cell.
+
+struct ff2 {
+    float2 hi, lo;  // components: cell A, cell B
+};
+
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p_splat(float a) { return make_float2(a, a); }
+
+__device__ __forceinline__ ff2 ff2_norm(float2 s, float2 e)
+{
+    ff2 r;
+    r.hi = p_add(s, e);
+    r.lo = p_sub(e, p_sub(r.hi, s));
+    return r;
+}
+
+__device__ __forceinline__ ff2 ff2_add(ff2 a, ff2 b)
+{
+    const float2 s = p_add(a.hi, b.hi);
+    const float2 bb = p_sub(s, a.hi);
+    const float2 e = p_add(p_sub(a.hi, p_sub(s, bb)), p_sub(b.hi, bb));
+    return ff2_norm(s, p_add(e, p_add(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ ff2 ff2_neg(ff2 a) { return ff2{make_float2(-a.hi.x, -a.hi.y), make_float2(-a.lo.x, -a.lo.y)}; }
+__device__ __forceinline__ ff2 ff2_sub(ff2 a, ff2 b) { return ff2_add(a, ff2_neg(b)); }
+
+__device__ __forceinline__ ff2 ff2_mul(ff2 a, ff2 b)
+{
+    const float2 p = p_mul(a.hi, b.hi);
+    float2 e = p_fma(a.hi, b.hi, make_float2(-p.x, -p.y));
+    e = p_fma(a.hi, b.lo, e);
+    e = p_fma(a.lo, b.hi, e);
+    return ff2_norm(p, e);
+}
+
+__device__ __forceinline__ ff2 ff2_scale2(ff2 a, float p2) { return ff2{p_mul(a.hi, p_splat(p2)), p_mul(a.lo, p_splat(p2))}; }
+__device__ __forceinline__ ff2 ff2_splat(ff a) { return ff2{p_splat(a.hi), p_splat(a.lo)}; }
+
+constexpr int kFzTX = 64, kFzTY = 8;
+constexpr int kFzW = kFzTX + 2, kFzP = kFzW * (kFzTY + 2);  // plane region with a 1-cell halo
+constexpr size_t kFzSmem = sizeof(float) * 2 * 4 * kFzP;       // hi and lo, 4 ring slots
+
+// The float-float residual of k_residual_ff, z-marching: a block owns a 64 x 8 (x, y) tile
+// and NZ planes; the hi and lo parts of the iterate's planes (tile + 1 halo) arrive in
+// shared memory by asynchronous copies one plane ahead; each thread evaluates cells
+// (x, y) and (x, y + 4) of its plane together.  Grid (n/64, n/8, n/NZ), at most
+// kMaxPartials blocks.
+__global__ void __launch_bounds__(256) k_residual_ff_zm(const float2* __restrict__ U, const float2* __restrict__ F,
+                                                        double lam_host, const double* __restrict__ lamp, int n,
+                                                        int NZ, FFCoef k, float* __restrict__ rplain,
+                                                        float* __restrict__ chi32, float* __restrict__ gap32,
+                                                        double* __restrict__ partials)
+{
+    const ff lam1 = ff_from_double(lam_host + (lamp ? *lamp : 0.0));
+    const ff2 lam = ff2_splat(lam1);
+    const ff2 nu1 = ff2_splat(ff{k.nu1_hi, k.nu1_lo}), kap1 = ff2_splat(ff{k.kap1_hi, k.kap1_lo});
+    const ff2 lsat = ff2_splat(ff{k.lsat_hi, k.lsat_lo}), nu = ff2_splat(ff{k.nu_hi, k.nu_lo});
+    const bool screened = k.kap_f != 0.f;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* sh = reinterpret_cast<float*>(smem_raw);  // [4][H][W] hi parts
+    float* sl = sh + 4 * kFzP;                        // [4][H][W] lo parts
+    const unsigned sh_s = (unsigned)__cvta_generic_to_shared(sh);
+    const unsigned sl_s = (unsigned)__cvta_generic_to_shared(sl);
+    const int m = n - 1;
+    const int x0 = blockIdx.x * kFzTX, y0 = blockIdx.y * kFzTY, z0 = blockIdx.z * NZ;
+    const int t = threadIdx.x;
+    const size_t plane = (size_t)n * n;
+    auto slot = [&](int p) { return ((p - z0 + 4) & 3) * kFzP; };  // p >= z0 - 1
+    constexpr int K = (kFzP + 255) / 256;
+    int off[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        const int e = t + 256 * q;
+        const int yy = e / kFzW, xx = e - yy * kFzW;
+        off[q] = e < kFzP ? (((y0 - 1 + yy) & m) * n + ((x0 - 1 + xx) & m)) : -1;
+    }
+    auto issue = [&](int p) {
+        const float* Up = reinterpret_cast<const float*>(U + (size_t)(p & m) * plane);
+        const int so = slot(p);
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            if (off[q] < 0) continue;
+            const unsigned d = 4u * (unsigned)(so + t + 256 * q);
+            cp_async4(sh_s + d, Up + 2 * off[q]);
+            cp_async4(sl_s + d, Up + 2 * off[q] + 1);
+        }
+        cp_async_commit_group();
+    };
+    const int x = t & 63, yA = t >> 6;
+    const int cA = (yA + 1) * kFzW + x + 1, cB = cA + 4 * kFzW;
+    const int gA = (y0 + yA) * n + x0 + x, gB = gA + 4 * n;
+    // value of plane slot `b` at offset d from the two centres, as a pair
+    auto ld = [&](int b, int d) {
+        return ff2{make_float2(sh[b + cA + d], sh[b + cB + d]), make_float2(sl[b + cA + d], sl[b + cB + d])};
+    };
+    float fa[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    issue(z0 - 1);
+    issue(z0);
+    issue(z0 + 1);
+    for (int s = z0; s < z0 + NZ; ++s) {
+        const size_t os = (size_t)s * plane;  // s is inside [0, n)
+        const float2 fA = F[os + gA], fB = F[os + gB];
+        cp_async_wait_all();  // planes up to s+1
+        __syncthreads();
+        if (s + 2 <= z0 + NZ) issue(s + 2);  // its slot held plane s-2, no longer read
+        const int bp = slot(s - 1), bc = slot(s), bn = slot(s + 1);
+        constexpr int W = kFzW;
+        const ff2 c0 = ld(bc, 0);
+        const ff2 m2c = ff2_scale2(c0, -2.f);
+        const ff2 X = ff2_add(ff2_add(ld(bc, 1), ld(bc, -1)), m2c);
+        const ff2 Y = ff2_add(ff2_add(ld(bc, W), ld(bc, -W)), m2c);
+        const ff2 Z = ff2_add(ff2_add(ld(bn, 0), ld(bp, 0)), m2c);
+        const ff2 exy = ff2_sub(ff2_sub(ld(bc, 1 + W), ld(bc, 1 - W)), ff2_sub(ld(bc, -1 + W), ld(bc, -1 - W)));
+        const ff2 exz = ff2_sub(ff2_sub(ld(bn, 1), ld(bp, 1)), ff2_sub(ld(bn, -1), ld(bp, -1)));
+        const ff2 eyz = ff2_sub(ff2_sub(ld(bn, W), ld(bp, W)), ff2_sub(ld(bn, -W), ld(bp, -W)));
+        const ff2 L1 = ff2_add(ff2_add(X, Y), Z);
+        const ff2 sq = ff2_add(ff2_add(ff2_mul(exy, exy), ff2_mul(exz, exz)), ff2_mul(eyz, eyz));
+        const ff2 pr = ff2_add(ff2_add(ff2_mul(X, Y), ff2_mul(Y, Z)), ff2_mul(Z, X));
+        const ff2 q2 = ff2_sub(ff2_scale2(pr, 2.f), ff2_scale2(sq, 0.125f));
+        const ff2 N = ff2_sub(ff2_mul(nu1, L1), ff2_mul(kap1, q2));
+        const ff2 rhs = ff2_add(ff2{make_float2(fA.x, fB.x), make_float2(fA.y, fB.y)}, lam);
+        const ff2 G = ff2_sub(N, rhs);
+        const ff2 L = ff2_scale2(L1, k.ih2);
+        const ff2 g = ff2_sub(lsat, L);
+        const float2 Lf = p_add(L.hi, L.lo), Gf = p_add(G.hi, G.lo), gf = p_add(g.hi, g.lo);
+        const float2 Ep = p_mul(p_fma(p_splat(8.f * k.kap_f), Lf, p_splat(-6.f * k.nu_f)), p_splat(k.ih2));
+        const float P4 = -96.f * k.kap_f * k.ih2 * k.ih2;  // 4 P
+        const float2 D = p_fma(p_splat(-P4), Gf, p_mul(Ep, Ep));
+        const bool flA = screened && D.x < k.Df, flB = screened && D.y < k.Df;
+        const ff2 ng = ff2_mul(nu, g);
+        const float rvA = flA ? ng.hi.x + ng.lo.x : -Gf.x;
+        const float rvB = flB ? ng.hi.y + ng.lo.y : -Gf.y;
+        rplain[os + gA] = -Gf.x;
+        rplain[os + gB] = -Gf.y;
+        chi32[os + gA] = c0.hi.x;
+        chi32[os + gB] = c0.hi.y;
+        gap32[os + gA] = screened ? gf.x : 0.f;
+        gap32[os + gB] = screened ? gf.y : 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float d = h ? rvB : rvA;
+            const bool fl = h ? flB : flA;
+            if (!isfinite(d)) {
+                fa[4] += 1.f;
+            } else {
+                fa[0] += d;
+                fa[2] += d * d;
+                if (!fl) {
+                    fa[1] += d;
+                    fa[3] += 1.f;
+                }
+            }
+        }
+    }
+    double acc[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) acc[q] = (double)fa[q];
+    block_sums<5>(acc, partials, (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
 }
 
 }  // namespace pmeft

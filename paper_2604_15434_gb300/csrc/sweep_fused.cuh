@@ -3,14 +3,13 @@
 // Same arithmetic and the same snapshot semantics as two k_half_sweep launches: red cells
 // are updated from the old field; black cells from the old black values (centre and the 12
 // same-colour edge neighbours) and the new red values (the 6 faces).  A thread block owns
-// a TX x TY tile of (x, y) and marches along z through a chunk of NZ planes, keeping in
-// shared memory a ring of 4 old planes and of the background (tile + 2-cell halo) and a
-// ring of 3 planes of new red values (tile + 1-cell halo); the right-hand side and the gap
-// are read at the cell from global memory.  At step s it loads plane s+1, computes the
-// red update of plane s on the
-// tile + 1 halo, then the black update of plane s-1 on the tile, and writes the whole of
-// plane s-1 (red and black) with coalesced paired stores.  Each input is read from DRAM
-// once per sweep; the halo re-reads come from L2.
+// a TX x TY tile of (x, y) and marches along z through a chunk of NZ planes.  Shared
+// memory holds a ring of old planes and of the background (tile + 2-cell halo) and a ring
+// of 3 planes of new red values (tile + 1-cell halo).  At step s it computes the red update
+// of plane s on the tile + 1 halo, then the black update of plane s-1 on the tile, and
+// writes the whole of plane s-1 (red and black) with coalesced paired stores, while plane
+// s+2 is being copied in.  Each input is read from DRAM once per sweep; the halo re-reads
+// come from L2.
 #pragma once
 
 #include "internal.cuh"
@@ -22,15 +21,28 @@ struct FusedGeom {
     static constexpr int WU = TX + 4, HU = TY + 4;  // old-value / background region
     static constexpr int WR = TX + 2, HR = TY + 2;  // red-update region
     static constexpr int PU = WU * HU, PR = WR * HR;
+    static constexpr int NS = 5;                    // ring slots of old planes: s-2 .. s+2
 };
 
 template <typename T, int TX, int TY, bool BG, bool GAP>
 constexpr size_t fused_smem_bytes()
 {
     using G = FusedGeom<TX, TY>;
-    return sizeof(T) * ((size_t)4 * G::PU * (BG ? 2 : 1) + (size_t)3 * G::PR);
+    return sizeof(T) * ((size_t)G::NS * G::PU * (BG ? 2 : 1) + (size_t)3 * G::PR);
 }
 
+__device__ __forceinline__ void cp_async4(unsigned smem_addr, const void* gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Data movement: the old planes (and the background) arrive through a 5-slot ring filled
+// by asynchronous copies one plane ahead, so the copy of plane s+2 overlaps the updates of
+// step s; the right-hand side, gap and mask values of a step's cells are loaded into
+// registers before the step's barrier.  Every per-cell index is an int32 offset computed
+// once per thread (n^3 <= 2^30); a step adds only the plane bases and the colour parity.
 template <typename T, int TX, int TY, bool BG, bool GAP>
 __global__ void __launch_bounds__(256) k_sweep_fused(const T* __restrict__ U, T* __restrict__ V,
                                                      const T* __restrict__ F, T fscale, T lam,
@@ -38,23 +50,27 @@ __global__ void __launch_bounds__(256) k_sweep_fused(const T* __restrict__ U, T*
                                                      const T* __restrict__ gap, int n, int NZ, T ih2, T nu, T kap,
                                                      T sp, T Df, T lsat, const T* __restrict__ lamp)
 {
+    static_assert(sizeof(T) == 4, "the single-pass sweep is the FP32 smoother");
+    static_assert(TX % 32 == 0 && TY % 2 == 0, "tile");
     if (lamp) lam += *lamp;
     using G = FusedGeom<TX, TY>;
-    extern __shared__ unsigned char smem_raw[];
-    T* su = reinterpret_cast<T*>(smem_raw);            // [4][HU][WU] old values
-    T* sb = su + 4 * G::PU;                            // [4][HU][WU] background (BG)
-    T* sr = sb + (BG ? 4 * G::PU : 0);                 // [3][HR][WR] new red values
+    constexpr int NS = G::NS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* su = reinterpret_cast<T*>(smem_raw);            // [NS][HU][WU] old values
+    T* sb = su + NS * G::PU;                           // [NS][HU][WU] background (BG)
+    T* sr = sb + (BG ? NS * G::PU : 0);                // [3][HR][WR] new red values
+    const unsigned su_s = (unsigned)__cvta_generic_to_shared(su);
+    const unsigned sb_s = (unsigned)__cvta_generic_to_shared(sb);
     const int m = n - 1;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * NZ;
-    const int t = threadIdx.x, nt = blockDim.x;
-    const size_t sn = (size_t)n;
-    auto gidx = [&](int x, int y, int z) { return ((size_t)(z & m) * sn + (y & m)) * sn + (x & m); };
-    // ring slots are taken from (plane - z0 + 8), which is never negative here
-    auto uslot = [&](int p) { return ((p - z0 + 8) & 3) * G::PU; };
+    const int t = threadIdx.x;
+    const size_t plane = (size_t)n * n;
+    // ring slots from (plane - z0 + 10) and (plane - z0 + 9), never negative here
+    auto uslot = [&](int p) { return ((p - z0 + 10) % NS) * G::PU; };
     auto rslot = [&](int p) { return ((p - z0 + 9) % 3) * G::PR; };
 
-    // the (x, y) offsets of this thread's share of a plane load are the same on every
-    // plane: compute them once (with the periodic wrap) and add the plane offset later
+    // this thread's share of a plane copy: the same (x, y) offsets (with the periodic
+    // wrap) on every plane
     constexpr int KU = (G::PU + 255) / 256;
     int offu[KU];
 #pragma unroll
@@ -63,30 +79,74 @@ __global__ void __launch_bounds__(256) k_sweep_fused(const T* __restrict__ U, T*
         const int yy = q / G::WU, xx = q - yy * G::WU;
         offu[k] = q < G::PU ? (((y0 - 2 + yy) & m) * n + ((x0 - 2 + xx) & m)) : -1;
     }
-    const size_t plane = (size_t)n * n;
-    auto load_u = [&](int p) {
-        T* du = su + uslot(p);
-        T* db = sb + uslot(p);
+    auto issue = [&](int p) {
         const T* Up = U + (size_t)(p & m) * plane;
         const T* Bp = bg + (size_t)(p & m) * plane;
+        const int so = uslot(p);
 #pragma unroll
         for (int k = 0; k < KU; ++k) {
             if (offu[k] < 0) continue;
-            du[t + k * 256] = Up[offu[k]];
-            if (BG) db[t + k * 256] = Bp[offu[k]];
+            const unsigned d = 4u * (unsigned)(so + t + k * 256);
+            cp_async4(su_s + d, Up + offu[k]);
+            if (BG) cp_async4(sb_s + d, Bp + offu[k]);
         }
+        cp_async_commit_group();
     };
+
+    // Work units.  Same-colour cells of one row sit two words apart, so a warp reading 32
+    // of them from one row would hit every bank twice; each warp instead takes 16 cells
+    // from each of two adjacent rows (opposite colour parity, even widths), which fall on
+    // the even and the odd banks.
+    const int lane = t & 31, warp = t >> 5;
+    const int half = lane >> 4, hl = lane & 15;
+    // red cells of the tile + 1 halo: per_row per row, 16-cell chunks, then the ragged rest
+    constexpr int per_row = G::WR / 2;
+    constexpr int chunks = per_row / 16;
+    constexpr int rest = per_row - 16 * chunks;
+    constexpr int units = ((G::HR + 1) / 2) * chunks;
+    constexpr int rest_units = (rest * G::HR + 31) / 32;
+    constexpr int NRU = (units + rest_units + 7) / 8;
+    int r_row[NRU], r_cu[NRU], r_cr[NRU], r_g0[NRU], r_g1[NRU];
+#pragma unroll
+    for (int it = 0; it < NRU; ++it) {
+        const int wu = warp + 8 * it;
+        int yr = G::HR, k = per_row;
+        if (wu < units) {
+            const int rp2 = wu / chunks, ch = wu - rp2 * chunks;
+            yr = 2 * rp2 + half;
+            k = ch * 16 + hl;
+        } else if (rest > 0 && wu < units + rest_units) {
+            const int q = (wu - units) * 32 + lane;
+            yr = q / (rest > 0 ? rest : 1);
+            k = 16 * chunks + q - yr * rest;
+        }
+        const bool ok = yr < G::HR && k < per_row;
+        r_row[it] = ok ? yr : -1;
+        r_cu[it] = (yr + 1) * G::WU + 2 * k + 1;   // + colour parity
+        r_cr[it] = yr * G::WR + 2 * k;             // + colour parity
+        const int gy = ((y0 - 1 + yr) & m) * n;
+        r_g0[it] = gy + ((x0 - 1 + 2 * k) & m);
+        r_g1[it] = gy + ((x0 + 2 * k) & m);
+    }
+    // black cells of the tile, one per (x, x+1) pair
+    constexpr int pairs = TX / 2;
+    constexpr int bchunks = (pairs + 15) / 16;
+    constexpr int bunits = ((TY + 1) / 2) * bchunks;
+    constexpr int NBU = (bunits + 7) / 8;
+    int b_row[NBU], b_x2[NBU];
+#pragma unroll
+    for (int it = 0; it < NBU; ++it) {
+        const int wu = warp + 8 * it;
+        const int rp2 = wu / bchunks, ch = wu - rp2 * bchunks;
+        const int y = 2 * rp2 + half, kq = ch * 16 + hl;
+        const bool ok = wu < bunits && y < TY && kq < pairs;
+        b_row[it] = ok ? y : -1;
+        b_x2[it] = 2 * kq;
+    }
+
     const T h2over6 = T(1) / (T(6) * ih2), inv2P = kap != T(0) ? T(1) / (T(-48) * kap * ih2 * ih2) : T(0);
-    auto update = [&](const Local<T>& o, T kc) -> T {
-        if constexpr (sizeof(T) == 4)
-            return local_update_fast(o, sp, Df, h2over6, kc != T(0) ? inv2P : T(0));
-        else
-            return local_update(o, sp, Df, ih2);
-    };
-    // 19-point stencil of the U region around (xu, yu) of plane p, faces from `face`
-    auto stencil_u = [&](const T* rp, const T* rc, const T* rn, int xu, int yu) {
+    auto stencil_u = [&](const T* rp, const T* rc, const T* rn, int c) {
         Stencil<T> s;
-        const int c = yu * G::WU + xu;
         s.c0 = rc[c];
         s.ax = rc[c + 1] + rc[c - 1];
         s.ay = rc[c + G::WU] + rc[c - G::WU];
@@ -97,20 +157,46 @@ __global__ void __launch_bounds__(256) k_sweep_fused(const T* __restrict__ U, T*
         return s;
     };
 
-    // Same-colour cells of one row sit two words apart, so a warp reading 32 of them from
-    // one row would hit every bank twice.  Each warp instead takes 16 cells from each of two
-    // adjacent rows: the rows alternate colour parity and have even widths, so the two
-    // halves fall on the even and the odd banks.
-    const int lane = t & 31, warp = t >> 5, nwarps = nt >> 5;
-    const int half = lane >> 4, hl = lane & 15;
-    const T* F_ = F;
-    auto rhs_at = [&](int gx, int gy, int p) { return fscale * F_[gidx(gx, gy, p)] + lam; };
-
-    load_u(z0 - 2);
-    load_u(z0 - 1);
+    issue(z0 - 2);
+    issue(z0 - 1);
+    issue(z0);
     for (int s = z0 - 1; s <= z0 + NZ; ++s) {
-        load_u(s + 1);
+        const int pb = s - 1;
+        const bool black = pb >= z0;
+        // this step's right-hand side, gap and mask values, before the barrier
+        T rF[NRU], rG[NRU], bF[NBU], bG[NBU];
+        bool rK[NRU], bK[NBU];
+        {
+            const size_t os = (size_t)(s & m) * plane, ob = (size_t)(pb & m) * plane;
+#pragma unroll
+            for (int it = 0; it < NRU; ++it) {
+                rF[it] = T(0);
+                rG[it] = T(0);
+                rK[it] = false;
+                if (r_row[it] >= 0) {
+                    const size_t g = os + (size_t)(((r_row[it] + s) & 1) ? r_g1[it] : r_g0[it]);
+                    rF[it] = F[g];
+                    if (GAP) rG[it] = gap[g];
+                    if (kmask) rK[it] = kmask[g] != 0;
+                }
+            }
+#pragma unroll
+            for (int it = 0; it < NBU; ++it) {
+                const int y = b_row[it];
+                bF[it] = T(0);
+                bG[it] = T(0);
+                bK[it] = false;
+                if (black && y >= 0) {
+                    const size_t gb = ob + (size_t)((y0 + y) * n + x0 + b_x2[it] + (((y + pb) & 1) ? 0 : 1));
+                    bF[it] = F[gb];
+                    if (GAP) bG[it] = gap[gb];
+                    if (kmask) bK[it] = kmask[gb] != 0;
+                }
+            }
+        }
+        cp_async_wait_all();  // plane s+1, copied during the previous step
         __syncthreads();
+        if (s + 2 <= z0 + NZ + 1) issue(s + 2);  // its slot held plane s-3, no longer read
         // ---- red update of plane s on the tile + 1 halo (all inputs old) ----
         {
             const T* up = su + uslot(s - 1);
@@ -120,38 +206,22 @@ __global__ void __launch_bounds__(256) k_sweep_fused(const T* __restrict__ U, T*
             const T* bc = sb + uslot(s);
             const T* bn = sb + uslot(s + 1);
             T* rc = sr + rslot(s);
-            constexpr int per_row = G::WR / 2;            // red cells per row of the region
-            constexpr int chunks = per_row / 16;          // full 16-cell chunks per row
-            constexpr int rest = per_row - 16 * chunks;   // cells left at the end of each row
-            constexpr int units = ((G::HR + 1) / 2) * chunks;  // (row pair, chunk) work units
-            constexpr int rest_units = (rest * G::HR + 31) / 32;  // leftover cells, 32 per unit
-            for (int wu = warp; wu < units + rest_units; wu += nwarps) {
-                int yr, k;
-                if (wu < units) {
-                    const int rp2 = wu / chunks, ch = wu - rp2 * chunks;
-                    yr = 2 * rp2 + half;
-                    k = ch * 16 + hl;
-                } else {
-                    const int q = (wu - units) * 32 + lane;  // q-th leftover cell
-                    yr = rest > 0 ? q / rest : G::HR;
-                    k = 16 * chunks + (rest > 0 ? q - yr * rest : 0);
-                }
-                if (yr >= G::HR || k >= per_row) continue;
-                const int xr = 2 * k + ((x0 - 1 + y0 - 1 + yr + s) & 1);
-                const int xu = xr + 1, yu = yr + 1;
-                Stencil<T> a = stencil_u(up, uc, un, xu, yu);
+#pragma unroll
+            for (int it = 0; it < NRU; ++it) {
+                if (r_row[it] < 0) continue;
+                const int par = (r_row[it] + s) & 1;
+                const int cu = r_cu[it] + par;
+                Stencil<T> a = stencil_u(up, uc, un, cu);
                 Stencil<T> b;
-                if (BG) b = stencil_u(bp, bc, bn, xu, yu);
-                const size_t g = gidx(x0 - 1 + xr, y0 - 1 + yr, s);
-                const T kc = (kmask && kmask[g]) ? T(0) : kap;
-                Local<T> o = local_eval<T, BG>(a, b, ih2, nu, kc, fscale * F_[g] + lam, lsat, GAP, GAP ? gap[g] : T(0));
-                rc[yr * G::WR + xr] = a.c0 + update(o, kc);
+                if (BG) b = stencil_u(bp, bc, bn, cu);
+                const T kc = rK[it] ? T(0) : kap;
+                Local<T> o = local_eval<T, BG>(a, b, ih2, nu, kc, fscale * rF[it] + lam, lsat, GAP, rG[it]);
+                rc[r_cr[it] + par] = a.c0 + local_update_fast(o, sp, Df, h2over6, kc != T(0) ? inv2P : T(0));
             }
         }
         __syncthreads();
-        // ---- black update of plane b = s - 1 on the tile, then store the plane ----
-        const int pb = s - 1;
-        if (pb >= z0) {
+        // ---- black update of plane pb = s - 1 on the tile, then store the plane ----
+        if (black) {
             const T* up = su + uslot(pb - 1);
             const T* uc = su + uslot(pb);
             const T* un = su + uslot(pb + 1);
@@ -161,20 +231,16 @@ __global__ void __launch_bounds__(256) k_sweep_fused(const T* __restrict__ U, T*
             const T* rp = sr + rslot(pb - 1);
             const T* rc = sr + rslot(pb);
             const T* rn = sr + rslot(pb + 1);
-            constexpr int pairs = TX / 2;                 // black cells (and pairs) per tile row
-            constexpr int chunks = (pairs + 15) / 16;
-            constexpr int units = ((TY + 1) / 2) * chunks;
-            for (int wu = warp; wu < units; wu += nwarps) {
-                const int rp2 = wu / chunks, ch = wu - rp2 * chunks;
-                const int y = 2 * rp2 + half;
-                const int kq = ch * 16 + hl;
-                if (y >= TY || kq >= pairs) continue;
-                const int x2 = 2 * kq;
-                const int par = (x0 + x2 + y0 + y + pb) & 1;  // 1: the first cell of the pair is black
-                const int xbk = x2 + (par ? 0 : 1), xrd = x2 + (par ? 1 : 0);
+            T* Vp = V + (size_t)pb * plane;  // pb is inside [0, n): no wrap
+#pragma unroll
+            for (int it = 0; it < NBU; ++it) {
+                const int y = b_row[it];
+                if (y < 0) continue;
+                const int x2 = b_x2[it];
+                const int par = (y + pb) & 1;  // 1: the first cell of the pair is black
+                const int xbk = x2 + (par ? 0 : 1), xrd = x2 + par;
                 // black cell: centre and edges from the old values, faces from the new red values
-                const int xu = xbk + 2, yu = y + 2, xr = xbk + 1, yr = y + 1;
-                const int cu = yu * G::WU + xu, cr = yr * G::WR + xr;
+                const int cu = (y + 2) * G::WU + xbk + 2, cr = (y + 1) * G::WR + xbk + 1;
                 Stencil<T> a;
                 a.c0 = uc[cu];
                 a.ax = rc[cr + 1] + rc[cr - 1];
@@ -184,23 +250,15 @@ __global__ void __launch_bounds__(256) k_sweep_fused(const T* __restrict__ U, T*
                 a.exz = un[cu + 1] - up[cu + 1] - un[cu - 1] + up[cu - 1];
                 a.eyz = un[cu + G::WU] - up[cu + G::WU] - un[cu - G::WU] + up[cu - G::WU];
                 Stencil<T> b;
-                if (BG) b = stencil_u(bp, bc, bn, xu, yu);
-                const size_t gb = gidx(x0 + xbk, y0 + y, pb);
-                const T kc = (kmask && kmask[gb]) ? T(0) : kap;
-                Local<T> o = local_eval<T, BG>(a, b, ih2, nu, kc, fscale * F_[gb] + lam, lsat, GAP, GAP ? gap[gb] : T(0));
-                const T vb = a.c0 + update(o, kc);
-                const T vr = rc[yr * G::WR + xrd + 1];
-                const size_t g0 = gidx(x0 + x2, y0 + y, pb);
-                if (sizeof(T) == 4) {
-                    float2 v2 = par ? make_float2((float)vb, (float)vr) : make_float2((float)vr, (float)vb);
-                    *reinterpret_cast<float2*>(V + g0) = v2;
-                } else {
-                    V[g0] = par ? vb : vr;
-                    V[g0 + 1] = par ? vr : vb;
-                }
+                if (BG) b = stencil_u(bp, bc, bn, cu);
+                const T kc = bK[it] ? T(0) : kap;
+                Local<T> o = local_eval<T, BG>(a, b, ih2, nu, kc, fscale * bF[it] + lam, lsat, GAP, bG[it]);
+                const T vb = a.c0 + local_update_fast(o, sp, Df, h2over6, kc != T(0) ? inv2P : T(0));
+                const T vr = rc[(y + 1) * G::WR + xrd + 1];
+                *reinterpret_cast<float2*>(Vp + (y0 + y) * n + x0 + x2) =
+                    par ? make_float2(vb, vr) : make_float2(vr, vb);
             }
         }
-        __syncthreads();
     }
 }
 

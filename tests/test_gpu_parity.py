@@ -264,6 +264,25 @@ def test_fp32_fused_sweep_matches_half_sweeps_and_oracle(gpu_lib, n, masked):
         assert np.abs(b - want).max() <= 1e-4 * np.abs(want).max()
 
 
+@pytest.mark.parametrize("variant", ["plain", "masked", "bg", "bg+gap"])
+@pytest.mark.parametrize("mode", range(1, 9))
+def test_every_fused_tile_variant_equals_half_sweeps(gpu_lib, variant, mode):
+    """Each tile variant the autotuner may pick, with and without the background / gap of
+    the correction form, gives the two half-sweep launches' result (same arithmetic)."""
+    n = 64
+    u, f, c = _sweep_inputs(n, 900 + mode, 0.5)
+    rng = np.random.default_rng(mode)
+    km = cu((rng.random((n, n, n)) < 0.3).astype(np.uint8), torch.uint8) if variant == "masked" else None
+    bg = cu(2.0 * rng.standard_normal((n, n, n)) / n ** 2, torch.float32) if variant.startswith("bg") else None
+    lsat = 0.75 * c["nu"] * (1 - 0.35) / c["kappa"]
+    gap = cu(lsat * (1.0 + 0.5 * rng.standard_normal((n, n, n))), torch.float32) if variant == "bg+gap" else None
+    args = (cu(f, torch.float32), 0.01, c["nu"], c["kappa"], 0.35)
+    a = gpu_lib.pm_mg_sweep_f32(cu(u, torch.float32), *args, kmask=km, mode=0, bg=bg, gap=gap).cpu().numpy()
+    b = gpu_lib.pm_mg_sweep_f32(cu(u, torch.float32), *args, kmask=km, mode=mode, bg=bg, gap=gap).cpu().numpy()
+    assert np.isfinite(b).all()
+    assert np.abs(a - b).max() <= 2e-6 * np.abs(a).max()
+
+
 @pytest.mark.parametrize("inner", [1, 3])
 def test_mixed_precision_solve_256_uses_fused_sweep(gpu_lib, inner):
     """At 256^3 the inner cycle runs the fused sweep on its finest level; the mixed solve
