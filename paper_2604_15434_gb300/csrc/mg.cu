@@ -15,6 +15,7 @@
 
 #include "internal.cuh"
 #include "sweep_fused.cuh"
+#include "sweep_pair.cuh"
 #include "outer_ff.cuh"
 #include "resid_fused.cuh"
 
@@ -418,9 +419,13 @@ constexpr int kResidZmMinN = 128;  // FP32 residual: z-marching kernel from this
 // Tile variants of the single-pass FP32 sweep: (TX, TY) x-y tile, NZ planes per block.
 struct FusedCfg {
     int tx, ty, nz;
+    bool pair;  // k_sweep_pair (two cells per thread) instead of k_sweep_fused
 };
-static const FusedCfg kFusedCfgs[] = {{64, 16, 32}, {64, 8, 32}, {64, 8, 64}, {32, 8, 32}, {32, 8, 64}, {64, 4, 64},
-                                     {64, 16, 16}, {64, 8, 16}};
+static const FusedCfg kFusedCfgs[] = {{64, 16, 32, false}, {64, 8, 32, false}, {64, 8, 64, false},
+                                     {32, 8, 32, false},  {32, 8, 64, false}, {64, 4, 64, false},
+                                     {64, 16, 16, false}, {64, 8, 16, false}, {64, 8, 32, true},
+                                     {64, 8, 64, true},   {64, 16, 32, true}, {64, 16, 64, true},
+                                     {64, 4, 64, true},   {64, 8, 16, true}};
 constexpr int kNumFusedCfgs = sizeof(kFusedCfgs) / sizeof(kFusedCfgs[0]);
 
 template <int TX, int TY, bool BG, bool GAP>
@@ -436,21 +441,43 @@ static void launch_fused(Exec* ctx, const float* A, float* B, const float* F, fl
                                       (float)c.kap, sp, Df, lsn, L.lamp);
 }
 
+template <int TY, bool BG, bool GAP>
+static void launch_pair(Exec* ctx, const float* A, float* B, const float* F, float fscale, float lam,
+                        const Level<float>& L, int nz, float h2inv, const Coef& c, float sp, float Df, float lsn)
+{
+    const int n = L.n;
+    constexpr size_t sm = pair_smem_bytes<TY, BG>();
+    auto k = k_sweep_pair<TY, BG, GAP>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const dim3 grid(n / 64, n / TY, n / nz);
+    k<<<grid, PairGeom<TY>::NT, sm, ctx->stream>>>(A, B, F, fscale, lam, L.kmask, L.bg, L.gap, n, nz, h2inv,
+                                                   (float)c.nu, (float)c.kap, sp, Df, lsn, L.lamp);
+}
+
 template <bool BG, bool GAP>
 static void launch_fused_cfg(Exec* ctx, int cfg, const float* A, float* B, const float* F, float fscale, float lam,
                              const Level<float>& L, float h2inv, const Coef& c, float sp, float Df, float lsn)
 {
     const FusedCfg& g = kFusedCfgs[cfg];
 #define PM_FUSED_CASE(TX_, TY_)                                                                        \
-    if (g.tx == TX_ && g.ty == TY_) {                                                                  \
+    if (!g.pair && g.tx == TX_ && g.ty == TY_) {                                                       \
         launch_fused<TX_, TY_, BG, GAP>(ctx, A, B, F, fscale, lam, L, g.nz, h2inv, c, sp, Df, lsn);    \
+        return;                                                                                        \
+    }
+#define PM_PAIR_CASE(TY_)                                                                              \
+    if (g.pair && g.ty == TY_) {                                                                       \
+        launch_pair<TY_, BG, GAP>(ctx, A, B, F, fscale, lam, L, g.nz, h2inv, c, sp, Df, lsn);          \
         return;                                                                                        \
     }
     PM_FUSED_CASE(64, 16)
     PM_FUSED_CASE(64, 8)
     PM_FUSED_CASE(32, 8)
     PM_FUSED_CASE(64, 4)
+    PM_PAIR_CASE(16)
+    PM_PAIR_CASE(8)
+    PM_PAIR_CASE(4)
 #undef PM_FUSED_CASE
+#undef PM_PAIR_CASE
 }
 
 static bool fused_cfg_fits(int cfg, int n)

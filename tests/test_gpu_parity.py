@@ -265,10 +265,12 @@ def test_fp32_fused_sweep_matches_half_sweeps_and_oracle(gpu_lib, n, masked):
 
 
 @pytest.mark.parametrize("variant", ["plain", "masked", "bg", "bg+gap"])
-@pytest.mark.parametrize("mode", range(1, 9))
+@pytest.mark.parametrize("mode", range(1, 15))
 def test_every_fused_tile_variant_equals_half_sweeps(gpu_lib, variant, mode):
     """Each tile variant the autotuner may pick, with and without the background / gap of
-    the correction form, gives the two half-sweep launches' result (same arithmetic)."""
+    the correction form, gives the two half-sweep launches' result: the same formulas in
+    FP32, up to rounding (the single-pass kernels use the hardware's approximate reciprocal
+    and reciprocal square root, and the paired kernels their own operation order)."""
     n = 64
     u, f, c = _sweep_inputs(n, 900 + mode, 0.5)
     rng = np.random.default_rng(mode)
@@ -280,7 +282,8 @@ def test_every_fused_tile_variant_equals_half_sweeps(gpu_lib, variant, mode):
     a = gpu_lib.pm_mg_sweep_f32(cu(u, torch.float32), *args, kmask=km, mode=0, bg=bg, gap=gap).cpu().numpy()
     b = gpu_lib.pm_mg_sweep_f32(cu(u, torch.float32), *args, kmask=km, mode=mode, bg=bg, gap=gap).cpu().numpy()
     assert np.isfinite(b).all()
-    assert np.abs(a - b).max() <= 2e-6 * np.abs(a).max()
+    assert np.abs(a - b).max() <= 1e-5 * np.abs(a).max()
+    assert np.sqrt(np.mean((a - b) ** 2)) <= 1e-6 * np.sqrt(np.mean(a ** 2))
 
 
 @pytest.mark.parametrize("inner", [1, 3])
