@@ -31,6 +31,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 COMBOS = [(-2.0, 0.0), (-2.0, 0.5), (-0.5, 0.0), (-0.5, 0.5)]
+# DRAM bytes per cell of one finest-level sweep launch, from the ncu capture summarised in
+# profiles/k_sweep_pair_256.md (dram__bytes_read.sum + dram__bytes_write.sum of one launch
+# at 256^3 over its cells; every input is read once, so the traffic scales with the cells)
+SWEEP_DRAM_BYTES_PER_CELL = 19.5
 TOL = 1e-8
 SEED = 1003
 METRIC = "512^3 scalar solve time-to-residual 1e-8 (learned+FP32 vs plain FP64); HBM GB/s %"
@@ -363,7 +367,9 @@ def main():
         roof = {"kernel": "single-pass FP32 red-black sweep of the finest level (k_sweep_pair / k_sweep_fused, "
                           "autotuned: " + (tuned[-1].split(": ", 1)[1] if tuned else "?") + ")", "bound": "hbm",
                 "achieved": ach, "peak": hbm,
-                "unit": "GB/s", "frac": ach / hbm, "traffic": None, "peak_source": src,
+                "unit": "GB/s", "frac": ach / hbm, "traffic": SWEEP_DRAM_BYTES_PER_CELL * cells,
+                "traffic_source": "ncu capture at 256^3 scaled by the cells (profiles/k_sweep_pair_256.md)",
+                "peak_source": src,
                 "bytes_per_launch": bytes_launch, "avg_launch_ms": avg_ms, "launches": fine["fine_launches"]}
     r64 = prof["resid64"]
     resid64 = None
@@ -382,7 +388,9 @@ def main():
                                "two FP32 inner FAS V(2,2) cycles per outer iteration of a float-float defect-"
                                "correction loop, the result confirmed by an FP64 residual; the learned warm start "
                                "is timed separately (warm_start)",
-                   "n": n, "solves_per_step": solves, "tol": TOL, "l2": "inputs larger than L2 (1 GiB per field)"},
+                   "n": n, "solves_per_step": solves, "tol": TOL,
+                   "l2": f"inputs larger than L2 ({n ** 3 * 8 / 2 ** 30:g} GiB per field)" if n ** 3 * 8 > 129e6
+                         else "inputs smaller than L2 (no flush: small-case profiling run)"},
         "e2e": {"value": sum(e2e_ms) / len(e2e_ms), "unit": "ms", "h2d_bytes_per_step": cells * 8,
                 "d2h_bytes_per_step": cells * 8, "per": "one solve (alpha_B0=-2, alpha_M0=0) incl. H2D delta, D2H chi"},
         "roofline": roof,

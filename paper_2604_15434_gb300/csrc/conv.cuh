@@ -237,4 +237,155 @@ __global__ void __launch_bounds__(128) k_conv3d_wgrad(const __nv_bfloat16* __res
     }
 }
 
+
+// ------------------------------------------------------------------ tiled forward conv
+//
+// Persistent implicit-GEMM 3x3x3 convolution for grids of at least 16^3.  A block keeps
+// the layer's BF16 weights resident in shared memory ([tap][ci/16][N][16], each 32-byte
+// row of 16 k with its two 16-byte halves swapped on every other group of four rows, so
+// that ldmatrix rows fall on distinct banks) and walks output tiles of 16 x 8 x 2 voxels.
+// Per tile and 16-channel chunk it stages the 18 x 10 x 4 input patch (the same half
+// swizzle per voxel) by cp.async, then runs all 27 taps without a barrier: each warp owns
+// two 16-voxel rows of the tile (M = 16 each) and all N outputs, its A fragments come from
+// ldmatrix with per-lane patch addresses (the tap shift is an address offset), B from the
+// resident weights.  mma.sync m16n8k16, BF16 inputs, FP32 accumulators.  (A second patch
+// buffer, to copy the next tile during the multiplications, was measured slower: it halves
+// the resident blocks, which already overlap one another's copies.)
+
+constexpr int kTX = 16, kTY = 8, kTZ = 2;                        // output tile
+constexpr int kPX = kTX + 2, kPY = kTY + 2, kPZ = kTZ + 2;       // input patch
+constexpr int kPV = kPX * kPY * kPZ;                             // 720 patch voxels
+
+__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], unsigned addr)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+
+// byte offset of half h (0: k 0-7, 1: k 8-15) of 32-byte row r
+__device__ __forceinline__ unsigned swz_row(int r, int h) { return (unsigned)(r * 32 + ((h ^ ((r >> 2) & 1)) << 4)); }
+
+template <int N>
+constexpr size_t conv_tile_smem(int cin)
+{
+    return (size_t)27 * cin * N * 2 + (size_t)kPV * 32;
+}
+
+template <int N>
+__global__ void __launch_bounds__(256) k_conv3d_tile(const __nv_bfloat16* __restrict__ in, int in_ld, int in_off,
+                                                    int Cin, const __nv_bfloat16* __restrict__ wt,
+                                                    const float* __restrict__ bias, __nv_bfloat16* __restrict__ out,
+                                                    int out_ld, int out_off, int n, int relu,
+                                                    const __nv_bfloat16* __restrict__ mask, int mask_ld, int mask_off)
+{
+    extern __shared__ __align__(128) unsigned char sm[];
+    const int kchunks = Cin / 16;
+    unsigned char* sW = sm;                                   // [27 * kchunks * N] rows of 32 B
+    unsigned char* sP = sm + (size_t)27 * kchunks * N * 32;   // [kPV] rows of 32 B
+    const unsigned sW_s = (unsigned)__cvta_generic_to_shared(sW);
+    const unsigned sP_s = (unsigned)__cvta_generic_to_shared(sP);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int g = lane >> 2, t4 = lane & 3;
+    const int m = n - 1;
+    constexpr int NT = N / 8;
+
+    // resident weights: row q = (tap * kchunks + ch) * N + co, 16 k each
+    const int wrows = 27 * kchunks * N;
+    for (int q = t; q < wrows * 2; q += 256) {
+        const int r = q >> 1, h = q & 1;
+        const unsigned d = sW_s + swz_row(r, h);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(wt + (size_t)r * 16 + h * 8));
+    }
+    cp_async_commit();
+
+    // lane roles in ldmatrix: A rows (voxels) and k halves; B rows (outputs) and k halves
+    const int mi = lane >> 3, rr = lane & 7;
+    const int a_row = rr + 8 * (mi & 1), a_h = mi >> 1;
+    const int b_row = rr + 8 * (mi >> 1), b_h = mi & 1;
+    // this warp's two M rows of the tile: (y, z) = (mt & 7, mt >> 3), x = 0..15
+    const int mt0 = 2 * warp, mt1 = 2 * warp + 1;
+    const int prow0 = ((mt0 >> 3) * kPY + (mt0 & 7)) * kPX;
+    const int prow1 = ((mt1 >> 3) * kPY + (mt1 & 7)) * kPX;
+
+    const int tx = n / kTX, ty = n / kTY, tz = n / kTZ;
+    const long long tiles = (long long)tx * ty * tz;
+    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int bx = (int)(tile % tx), by = (int)((tile / tx) % ty), bz = (int)(tile / ((long long)tx * ty));
+        const int x0 = bx * kTX, y0 = by * kTY, z0 = bz * kTZ;
+        float acc[2][NT][4];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < NT; ++j)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+        for (int ch = 0; ch < kchunks; ++ch) {
+            // the patch of this chunk: voxel p = (pz * kPY + py) * kPX + px, two 16-byte halves
+            for (int q = t; q < kPV * 2; q += 256) {
+                const int p = q >> 1, h = q & 1;
+                const int px = p % kPX, py = (p / kPX) % kPY, pz = p / (kPX * kPY);
+                const int gx = (x0 - 1 + px) & m, gy = (y0 - 1 + py) & m, gz = (z0 - 1 + pz) & m;
+                const __nv_bfloat16* src = in + ((size_t)(gz * n + gy) * n + gx) * in_ld + in_off + ch * 16 + h * 8;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sP_s + swz_row(p, h)), "l"(src));
+            }
+            cp_async_commit();
+            cp_async_wait<0>();
+            __syncthreads();
+#pragma unroll 1
+            for (int tap = 0; tap < 27; ++tap) {
+                const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;  // patch offsets 0..2
+                const int sh = (dz * kPY + dy) * kPX + dx;
+                unsigned a0[4], a1[4];
+                ldsm_x4(a0, sP_s + swz_row(prow0 + sh + a_row, a_h));
+                ldsm_x4(a1, sP_s + swz_row(prow1 + sh + a_row, a_h));
+                const int wbase = (tap * kchunks + ch) * N;
+#pragma unroll
+                for (int j = 0; j < NT; j += 2) {
+                    unsigned b[4];
+                    ldsm_x4(b, sW_s + swz_row(wbase + 8 * j + b_row, b_h));
+                    const unsigned b0[2] = {b[0], b[1]}, b1[2] = {b[2], b[3]};
+                    mma_bf16(acc[0][j], a0, b0);
+                    mma_bf16(acc[1][j], a1, b0);
+                    mma_bf16(acc[0][j + 1], a0, b1);
+                    mma_bf16(acc[1][j + 1], a1, b1);
+                }
+            }
+            __syncthreads();  // the patch is refilled next
+        }
+        // epilogue: bias, activation, optional mask, BF16 pairs
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int mt = 2 * warp + i;
+            const int y = y0 + (mt & 7), z = z0 + (mt >> 3);
+#pragma unroll
+            for (int hr = 0; hr < 2; ++hr) {
+                const int x = x0 + g + 8 * hr;
+                const size_t v = ((size_t)z * n + y) * n + x;
+#pragma unroll
+                for (int j = 0; j < NT; ++j) {
+                    const int c = j * 8 + 2 * t4;
+                    float y0v = acc[i][j][2 * hr], y1v = acc[i][j][2 * hr + 1];
+                    if (bias) {
+                        y0v += bias[c];
+                        y1v += bias[c + 1];
+                    }
+                    if (relu) {
+                        y0v = fmaxf(y0v, 0.f);
+                        y1v = fmaxf(y1v, 0.f);
+                    }
+                    if (mask) {
+                        const __nv_bfloat162 mk =
+                            *reinterpret_cast<const __nv_bfloat162*>(mask + v * mask_ld + mask_off + c);
+                        if (!(__bfloat162float(mk.x) > 0.f)) y0v = 0.f;
+                        if (!(__bfloat162float(mk.y) > 0.f)) y1v = 0.f;
+                    }
+                    *reinterpret_cast<__nv_bfloat162*>(out + v * out_ld + out_off + c) = __floats2bfloat162_rn(y0v, y1v);
+                }
+            }
+        }
+    }
+    cp_async_wait<0>();
+}
+
 }  // namespace pmeft

@@ -14,6 +14,7 @@
 //   up -> [cat1 0:32], c8 48->16, c9 16->16        (n)
 //   head 1x1x1 16->1 (linear) -> T_hat
 // Parameters (FP32 master copy, flat): per conv W[tap][ci][co] then b[co]; head w[16], b.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -43,31 +44,39 @@ static long long total_params()
 __global__ void k_pack_input(const double* __restrict__ delta, int nvox, float p1, float p2, float p3,
                              __nv_bfloat16* __restrict__ out)
 {
+    // the network sees asinh(delta) in BF16: FP32 asinh is far below that rounding
+    const __nv_bfloat16 b1 = __float2bfloat16(p1), b2 = __float2bfloat16(p2), b3 = __float2bfloat16(p3);
+    const __nv_bfloat16 z = __float2bfloat16(0.f);
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += gridDim.x * blockDim.x) {
-        __nv_bfloat16* o = out + (size_t)v * 16;
-        o[0] = __float2bfloat16((float)asinh(delta[v]));
-        o[1] = __float2bfloat16(p1);
-        o[2] = __float2bfloat16(p2);
-        o[3] = __float2bfloat16(p3);
-#pragma unroll
-        for (int c = 4; c < 16; ++c) o[c] = __float2bfloat16(0.f);
+        __align__(16) __nv_bfloat16 o[8] = {__float2bfloat16(asinhf((float)delta[v])), b1, b2, b3, z, z, z, z};
+        uint4* dst = reinterpret_cast<uint4*>(out + (size_t)v * 16);
+        dst[0] = *reinterpret_cast<const uint4*>(o);
+        dst[1] = make_uint4(0u, 0u, 0u, 0u);
     }
 }
 
 // out (n/2 grid, C channels) = average of the 8 children of in (slice ld/off)
 __global__ void k_pool2(const __nv_bfloat16* __restrict__ in, int ld, int off, int C, int n, __nv_bfloat16* __restrict__ out)
 {
-    const int nc = n / 2, total = nc * nc * nc * C;
+    // one thread per (coarse voxel, group of 8 channels); n is a power of two, C, ld and
+    // off multiples of 8 (16-byte accesses)
+    const int nc = n / 2, lgc = __ffs(nc) - 1, G = C / 8, total = nc * nc * nc * G;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
-        const int c = q % C, v = q / C;
-        const int X = v % nc, Y = (v / nc) % nc, Z = v / (nc * nc);
-        float s = 0.f;
+        const int cg = q % G, v = q / G;
+        const int X = v & (nc - 1), Y = (v >> lgc) & (nc - 1), Z = v >> (2 * lgc);
+        float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int f = ((2 * Z + (k >> 2)) * n + (2 * Y + ((k >> 1) & 1))) * n + (2 * X + (k & 1));
-            s += __bfloat162float(in[(size_t)f * ld + off + c]);
+            const uint4 raw = *reinterpret_cast<const uint4*>(in + (size_t)f * ld + off + cg * 8);
+            const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&raw);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) s[c] += __bfloat162float(e[c]);
         }
-        out[(size_t)v * C + c] = __float2bfloat16(0.125f * s);
+        __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) o[c] = __float2bfloat16(0.125f * s[c]);
+        *reinterpret_cast<uint4*>(out + (size_t)v * C + cg * 8) = *reinterpret_cast<const uint4*>(o);
     }
 }
 
@@ -75,9 +84,10 @@ __global__ void k_pool2(const __nv_bfloat16* __restrict__ in, int ld, int off, i
 __global__ void k_pool2_bwd_add(const __nv_bfloat16* __restrict__ dout, int C, int n, __nv_bfloat16* __restrict__ din,
                                 int ld, int off, const __nv_bfloat16* __restrict__ mask)
 {
-    const int total = n * n * n * C, nc = n / 2;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
-        const int c = q % C, v = q / C;
+    const long long total = (long long)n * n * n * C;  // 2^31 at 512^3 x 16 channels
+    const int nc = n / 2;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(q % C), v = (int)(q / C);
         const int x = v % n, y = (v / n) % n, z = v / (n * n);
         const int p = ((z >> 1) * nc + (y >> 1)) * nc + (x >> 1);
         const size_t idx = (size_t)v * ld + off + c;
@@ -90,11 +100,15 @@ __global__ void k_pool2_bwd_add(const __nv_bfloat16* __restrict__ dout, int C, i
 // out[child][off + c] = in[parent][c]  (nearest upsampling into a channel slice)
 __global__ void k_up2(const __nv_bfloat16* __restrict__ in, int C, int nc, __nv_bfloat16* __restrict__ out, int ld, int off)
 {
-    const int n = 2 * nc, total = n * n * n * C;
+    // one thread per (fine voxel, group of 8 channels), 16-byte copies; the count stays
+    // below 2^31 up to 512^3 x 64 channels
+    const int n = 2 * nc, lg = __ffs(n) - 1, G = C / 8, total = n * n * n * G;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
-        const int c = q % C, v = q / C;
-        const int x = v % n, y = (v / n) % n, z = v / (n * n);
-        out[(size_t)v * ld + off + c] = in[(size_t)(((z >> 1) * nc + (y >> 1)) * nc + (x >> 1)) * C + c];
+        const int cg = q % G, v = q / G;
+        const int x = v & (n - 1), y = (v >> lg) & (n - 1), z = v >> (2 * lg);
+        const size_t pv = (size_t)(((z >> 1) * nc + (y >> 1)) * nc + (x >> 1));
+        *reinterpret_cast<uint4*>(out + (size_t)v * ld + off + cg * 8) =
+            *reinterpret_cast<const uint4*>(in + pv * C + cg * 8);
     }
 }
 
@@ -120,9 +134,15 @@ __global__ void k_up2_bwd(const __nv_bfloat16* __restrict__ dout, int ld, int of
 __global__ void k_head(const __nv_bfloat16* __restrict__ y, const float* __restrict__ w, int nvox, double* __restrict__ out)
 {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += gridDim.x * blockDim.x) {
+        const uint4* src = reinterpret_cast<const uint4*>(y + (size_t)v * 16);
+        const uint4 r0 = src[0], r1 = src[1];
+        const __nv_bfloat16* e0 = reinterpret_cast<const __nv_bfloat16*>(&r0);
+        const __nv_bfloat16* e1 = reinterpret_cast<const __nv_bfloat16*>(&r1);
         float s = w[16];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) s += w[c] * __bfloat162float(y[(size_t)v * 16 + c]);
+        for (int c = 0; c < 8; ++c) s += w[c] * __bfloat162float(e0[c]);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) s += w[8 + c] * __bfloat162float(e1[c]);
         out[v] = (double)s;
     }
 }
@@ -350,19 +370,53 @@ static void conv_fwd(pm_ctx* ctx, const __nv_bfloat16* in, int in_ld, int in_off
 {
     const int nvox = n * n * n, grid = (nvox + kConvM - 1) / kConvM;
     ctx->begin(PM_K_PM);
+    // grids of 16^3 and up whose weights fit next to the patch in shared memory take the
+    // persistent tiled kernel, the rest the per-128-voxel kernel
+    bool tiled = false;
+    if (n >= kTX && n % kTX == 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const long long tiles = (long long)(n / kTX) * (n / kTY) * (n / kTZ);
+#define PM_TILE_CASE(N_)                                                                                          \
+    case N_: {                                                                                                    \
+        const size_t smem = conv_tile_smem<N_>(ci);                                                               \
+        if (smem <= 227 * 1024) {                                                                                 \
+            auto k = k_conv3d_tile<N_>;                                                                           \
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                      \
+            int per_sm = 0;                                                                                       \
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem);                                 \
+            const long long g = std::min<long long>(tiles, (long long)sms * std::max(per_sm, 1));                 \
+            k<<<(int)g, 256, smem, ctx->stream>>>(in, in_ld, in_off, ci, w, bias, out, out_ld, out_off, n,        \
+                                                 relu ? 1 : 0, mask, mask_ld, mask_off);                          \
+            tiled = true;                                                                                         \
+        }                                                                                                         \
+        break;                                                                                                    \
+    }
+        switch (co) {
+            PM_TILE_CASE(16)
+            PM_TILE_CASE(32)
+            PM_TILE_CASE(48)
+            PM_TILE_CASE(64)
+            PM_TILE_CASE(96)
+        }
+#undef PM_TILE_CASE
+    }
+    if (!tiled) {
 #define PM_CONV_CASE(N_)                                                                                           \
     case N_:                                                                                                       \
         k_conv3d_fwd<N_><<<grid, 128, 0, ctx->stream>>>(in, in_ld, in_off, ci, w, bias, out, out_ld, out_off, n,    \
                                                         relu ? 1 : 0, mask, mask_ld, mask_off);                    \
         break;
-    switch (co) {
-        PM_CONV_CASE(16)
-        PM_CONV_CASE(32)
-        PM_CONV_CASE(48)
-        PM_CONV_CASE(64)
-        PM_CONV_CASE(96)
-    }
+        switch (co) {
+            PM_CONV_CASE(16)
+            PM_CONV_CASE(32)
+            PM_CONV_CASE(48)
+            PM_CONV_CASE(64)
+            PM_CONV_CASE(96)
+        }
 #undef PM_CONV_CASE
+    }
     ctx->end();
 }
 

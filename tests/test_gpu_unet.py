@@ -37,6 +37,41 @@ def test_forward_matches_reference(gpu_lib, case):
     assert np.linalg.norm(got - want) / np.linalg.norm(want) < 3e-2  # BF16 activations and weights
 
 
+def test_forward_matches_reference_64(gpu_lib):
+    """At 64^3 every level takes the tiled convolution kernel (levels 64, 32, 16)."""
+    n = 64
+    delta = synth.lognormal_delta(n, -2.0, 1.2, 21)
+    p = U.init_params(9)
+    p[-1] = 0.1
+    net = gpu_lib.UNet()
+    net.set_params(p)
+    got = net.forward(cu(delta), -1.2, 0.3, 0.7).cpu().numpy()
+    want, _ = U.forward(p, delta, -1.2, 0.3, 0.7)
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 3e-2
+
+
+@pytest.mark.slow
+def test_forward_at_512_matches_reference_on_a_crop(gpu_lib):
+    """The network applied at 512^3 (the size the warm start runs at; some of its
+    activation tensors hold more than 2^31 values) against the reference evaluated on a
+    64^3 crop: outputs farther from the crop's faces than the receptive field (about 23
+    voxels through the coarsest level) do not see the crop's wrap-around, so the central
+    8^3 must agree."""
+    n, s0, w = 512, 196, 64
+    g = torch.Generator(device="cuda")
+    g.manual_seed(3)
+    delta = (torch.randn((n, n, n), generator=g, device="cuda", dtype=torch.float64) * 0.8).exp() - 1.0
+    p = U.init_params(4)
+    p[-1] = 0.1
+    net = gpu_lib.UNet()
+    net.set_params(p)
+    got = net.forward(delta, -1.0, 0.2, 0.9)[s0 + 28:s0 + 36, s0 + 28:s0 + 36, s0 + 28:s0 + 36].cpu().numpy()
+    crop = delta[s0:s0 + w, s0:s0 + w, s0:s0 + w].cpu().numpy()
+    want, _ = U.forward(p, crop, -1.0, 0.2, 0.9)
+    want = want[28:36, 28:36, 28:36]
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 3e-2
+
+
 def test_gradients_match_reference(gpu_lib, case):
     n, delta, target, p = case
     net = gpu_lib.UNet()
