@@ -32,9 +32,9 @@ if ROOT not in sys.path:
 
 COMBOS = [(-2.0, 0.0), (-2.0, 0.5), (-0.5, 0.0), (-0.5, 0.5)]
 # DRAM bytes per cell of one finest-level sweep launch, from the ncu capture summarised in
-# profiles/k_sweep_pair_256.md (dram__bytes_read.sum + dram__bytes_write.sum of one launch
-# at 256^3 over its cells; every input is read once, so the traffic scales with the cells)
-SWEEP_DRAM_BYTES_PER_CELL = 19.5
+# profiles/k_sweep_pair_256.md (dram__bytes_read.sum + dram__bytes_write.sum of one 512^3
+# launch over its cells; every input is read once, so the traffic scales with the cells)
+SWEEP_DRAM_BYTES_PER_CELL = 20.3
 TOL = 1e-8
 SEED = 1003
 METRIC = "512^3 scalar solve time-to-residual 1e-8 (learned+FP32 vs plain FP64); HBM GB/s %"
@@ -368,7 +368,7 @@ def main():
                           "autotuned: " + (tuned[-1].split(": ", 1)[1] if tuned else "?") + ")", "bound": "hbm",
                 "achieved": ach, "peak": hbm,
                 "unit": "GB/s", "frac": ach / hbm, "traffic": SWEEP_DRAM_BYTES_PER_CELL * cells,
-                "traffic_source": "ncu capture at 256^3 scaled by the cells (profiles/k_sweep_pair_256.md)",
+                "traffic_source": "ncu capture of a 512^3 launch (profiles/k_sweep_pair_256.md)",
                 "peak_source": src,
                 "bytes_per_launch": bytes_launch, "avg_launch_ms": avg_ms, "launches": fine["fine_launches"]}
     r64 = prof["resid64"]
