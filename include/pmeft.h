@@ -257,8 +257,10 @@ int pm_tune_log(const pm_ctx* ctx, char* buf, int len);
 
 /* One red-black sweep (red = (i+j+k) even first; a half-sweep reads same-colour
  * neighbours from the values at its start).  u updated in place; f the right-hand
- * side; lambda added to it; kmask (device n^3 bytes, nullable) switches the screening
- * term off per cell.  h = 1/n. */
+ * side; lambda added to it.  kmask (device n^3 bytes, nullable): per cell, the eighths
+ * of the screening term switched off: 0 keeps kappa, k in 1..7 keeps (8-k)/8 of it, 8 or
+ * more removes it (the coarse levels of the FAS cycle store there the mean unscreened
+ * fraction of a cell's children).  h = 1/n. */
 pm_status pm_mg_sweep(pm_ctx* ctx, double* u, const double* f, double lambda, int n, double nu, double kappa,
                       double eta, const unsigned char* kmask);
 /* The same sweep on an FP32 grid: mode 0 runs the two half-sweep kernels, mode k >= 1

@@ -108,7 +108,9 @@ def apply_N_padded(p, h, nu, kappa):
 
 
 def smooth_sweep(u, f, lam, nu, kappa, eta, kmask=None):
-    """One red-black Newton-Gauss-Seidel sweep on a periodic grid (Sec. 3.2.1, 3.3, 3.4)."""
+    """One red-black Newton-Gauss-Seidel sweep on a periodic grid (Sec. 3.2.1, 3.3, 3.4).
+    kmask (uint8, optional): per cell, the eighths of the screening term switched off
+    (0 keeps kappa, 8 or more removes it)."""
     u = _f64(u).copy()
     f = _f64(f)
     n = u.shape[0]

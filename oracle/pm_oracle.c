@@ -167,6 +167,16 @@ static void local_eval(const double* p, size_t c, int n, double h, double nu, do
     o->D = o->Ep * o->Ep - 4.0 * o->P * o->G;
 }
 
+/* Screening weight of a cell from its mask byte k: the cell keeps (8 - k)/8 of the
+ * screening term, none for k >= 8.  Coarse FAS levels store in k how many of the cell's 8
+ * children were floored or themselves partly unscreened (their mean, in eighths), so the
+ * coarse operator varies continuously across the edge of a floored region. */
+static double screen_w(const unsigned char* kmask, size_t u)
+{
+    if (!kmask) return 1.0;
+    return kmask[u] >= 8 ? 0.0 : (8.0 - (double)kmask[u]) / 8.0;
+}
+
 static double floor_disc(double nu, double h, double eta)
 {
     double s = eta * 6.0 * fabs(nu) / (h * h);
@@ -225,8 +235,8 @@ void orc_apply_N(const double* u, int n, double h, double nu, double kap, double
 
 /* ------------------------------------------------------------------ */
 /* One red-black sweep (red = (i+j+k) even first), R-rb semantics.
- * kmask (nullable) marks cells whose screening term is switched off
- * (coarse levels of the FAS cycle).  lam is added to the rhs of the cells
+ * kmask (nullable): per cell, the eighths of the screening term switched off
+ * (0 keeps it, 8 or more removes it; coarse levels of the FAS cycle).  lam is added to the rhs of the cells
  * that carry the gauge multiplier.  Works on a padded array.            */
 /* ------------------------------------------------------------------ */
 static void sweep_padded(double* p, double* snap, const double* f, double lam, int n, double h,
@@ -243,7 +253,7 @@ static void sweep_padded(double* p, double* snap, const double* f, double lam, i
                 for (int i = 0; i < n; ++i) {
                     if (((i + j + k) & 1) != colour) continue;
                     size_t u = uidx(i, j, k, n);
-                    double kc = (kmask && kmask[u]) ? 0.0 : kap;
+                    double kc = kap * screen_w(kmask, u);
                     orc_local o;
                     int sat;
                     local_eval(snap, pidx(i, j, k, n), n, h, nu, kc, f[u] + lam, &o);
@@ -265,7 +275,7 @@ static long long residual_padded(double* p, const double* f, double lam, int n, 
         for (int j = 0; j < n; ++j)
             for (int i = 0; i < n; ++i) {
                 size_t u = uidx(i, j, k, n);
-                double kc = (kmask && kmask[u]) ? 0.0 : kap;
+                double kc = kap * screen_w(kmask, u);
                 orc_local o;
                 int sat;
                 local_eval(p, pidx(i, j, k, n), n, h, nu, kc, f[u] + lam, &o);
@@ -421,13 +431,13 @@ static void vcycle(level_t* lv, int l, int nlev, double lam, const orc_mg_params
         for (size_t i = 0; i < m; ++i)
             if (!L->sat[i]) L->r[i] -= gm;
     }
-    /* coarse mask: a coarse cell drops its screening term when at least half
-     * of its children used the floored (linear) piece or were masked */
+    /* coarse mask: the unscreened fraction of a coarse cell, in eighths, is the mean of
+     * its children's (1 for a floored child, whose equation is linear) */
     double* tmp = (double*)malloc(m * sizeof(double));
-    for (size_t i = 0; i < m; ++i) tmp[i] = (L->sat[i] || (L->kmask && L->kmask[i])) ? 1.0 : 0.0;
+    for (size_t i = 0; i < m; ++i) tmp[i] = L->sat[i] ? 1.0 : 1.0 - screen_w(L->kmask, i);
     double* tc = (double*)malloc(mc * sizeof(double));
     orc_restrict(tmp, L->n, tc);
-    for (size_t i = 0; i < mc; ++i) C->kmask[i] = tc[i] >= 0.5 ? 1 : 0;
+    for (size_t i = 0; i < mc; ++i) C->kmask[i] = (unsigned char)lround(tc[i] * 8.0);
     /* FAS: restrict the approximation and build f_H = N_H(R u) + R r */
     unpad_to(L->p, L->n, tmp);
     orc_restrict(tmp, L->n, C->ur);
@@ -440,7 +450,7 @@ static void vcycle(level_t* lv, int l, int nlev, double lam, const orc_mg_params
             for (int j = 0; j < C->n; ++j)
                 for (int i = 0; i < C->n; ++i) {
                     size_t u = uidx(i, j, k, C->n);
-                    double kc = C->kmask[u] ? 0.0 : prm->kappa;
+                    double kc = prm->kappa * screen_w(C->kmask, u);
                     local_eval(C->p, pidx(i, j, k, C->n), C->n, C->h, prm->nu, kc, 0.0, &o);
                     nh[u] = o.N;
                 }

@@ -72,6 +72,17 @@ __device__ __forceinline__ void block_sums(double (&v)[NV], double* partials)
     block_sums<NV>(v, partials, blockIdx.x);
 }
 
+// Screening weight of a cell from its mask byte k: the cell keeps (8 - k)/8 of kappa,
+// none for k >= 8.  Coarse FAS levels store in k the mean unscreened fraction of a cell's
+// 8 children in eighths (a floored child counts as unscreened: its equation is linear).
+template <typename T>
+__device__ __forceinline__ T screen_w(const uint8_t* __restrict__ kmask, size_t c)
+{
+    if (!kmask) return T(1);
+    const int k = kmask[c];
+    return k >= 8 ? T(0) : T(8 - k) * T(0.125);
+}
+
 // One multigrid level of one precision.  u[0]/u[1] ping-pong under the red-black sweep.
 template <typename T>
 struct Level {

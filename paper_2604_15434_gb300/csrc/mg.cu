@@ -71,8 +71,9 @@ __global__ void __launch_bounds__(256) k_half_sweep(const T* __restrict__ own, c
         Stencil<T> s = load_stencil(own, oth, i, j, k, n);
         Stencil<T> b;
         if (BG) b = load_stencil(bg, bg, i, j, k, n);
-        const T kc = (kmask && kmask[c]) ? T(0) : kap;
-        const T lsat = kc != T(0) ? lsat_c : T(0);
+        const T w = screen_w<T>(kmask, c);
+        const T kc = kap * w;
+        const T lsat = kc != T(0) ? lsat_c / w : T(0);
         Local<T> o = local_eval<T, BG>(s, b, ih2, nu, kc, fscale * F[c] + lam, lsat, gap != nullptr, gap ? gap[c] : T(0));
         out[c] = s.c0 + local_update(o, sp, Df, ih2);
     }
@@ -105,9 +106,9 @@ __global__ void __launch_bounds__(256) k_residual(const T* __restrict__ u, const
         Stencil<T> s = load_stencil(u, u, i, j, k, n);
         Stencil<T> b;
         if (BG) b = load_stencil(bg, bg, i, j, k, n);
-        const bool masked = kmask && kmask[c];
-        const T kc = masked ? T(0) : kap;
-        const T lsat = kc != T(0) ? lsat_c : T(0);
+        const T w = screen_w<T>(kmask, c);
+        const T kc = kap * w;
+        const T lsat = kc != T(0) ? lsat_c / w : T(0);
         Local<T> o = local_eval<T, BG>(s, b, ih2, nu, kc, fscale * F[c] + lam, lsat, gap != nullptr, gap ? gap[c] : T(0));
         // the floored piece exists on the finest level only; coarse levels take their
         // pieces from the restricted mask (linear where masked, quadratic elsewhere), so
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(256) k_residual(const T* __restrict__ u, const
 
 // Coarse cell = average of its 8 children, for the iterate (-> ur and the coarse start
 // value) and the gauge-projected residual r - gm * [unfloored]; the coarse screening mask
-// is set where at least 4 children were floored or masked.
+// holds the children's mean unscreened fraction in eighths (floored children count 8).
 template <typename T>
 __global__ void __launch_bounds__(256) k_restrict_fas(const T* __restrict__ uf, const T* __restrict__ rf,
                                                       const uint8_t* __restrict__ satf,
@@ -171,13 +172,14 @@ __global__ void __launch_bounds__(256) k_restrict_fas(const T* __restrict__ uf, 
             su += uf[f];
             const bool fl = satf[f] != 0;
             sr += fl ? rf[f] : rf[f] - gm;
-            cnt += (fl || (kmf && kmf[f])) ? 1 : 0;
+            const int kf = kmf ? (kmf[f] < 8 ? kmf[f] : 8) : 0;
+            cnt += fl ? 8 : kf;  // unscreened eighths of the child
         }
         su *= T(0.125);
         ur[c] = su;
         uc[c] = su;
         rc[c] = sr * T(0.125);
-        kmc[c] = cnt >= 4 ? 1 : 0;
+        kmc[c] = (uint8_t)((cnt + 4) >> 3);  // mean of the children, rounded to eighths
     }
 }
 
@@ -217,7 +219,7 @@ __global__ void __launch_bounds__(256) k_fas_rhs(const T* __restrict__ uc, const
         Stencil<T> s = load_stencil(uc, uc, i, j, k, n);
         Stencil<T> b;
         if (BG) b = load_stencil(bg, bg, i, j, k, n);
-        const T kc = kmask[c] ? T(0) : kap;
+        const T kc = kap * screen_w<T>(kmask, c);
         Local<T> o = local_eval<T, BG>(s, b, ih2, nu, kc, T(0), T(0));
         fc[c] = o.G + rc[c];
     }
@@ -311,8 +313,9 @@ __global__ void __launch_bounds__(256) k_coarsest(T* __restrict__ u, const T* __
                 Stencil<double> s = load_stencil<double>(ss, ss, i, j, k, n);
                 Stencil<double> b;
                 if (BG) b = load_stencil<double>(sb, sb, i, j, k, n);
-                const double kc = sk[c] ? 0.0 : kap;
-                Local<double> o = local_eval<double, BG>(s, b, ih2, nu, kc, sf[c] + lam, kc != 0.0 ? lsat_c : 0.0);
+                const double w = sk[c] >= 8 ? 0.0 : (8 - sk[c]) * 0.125;
+                const double kc = kap * w;
+                Local<double> o = local_eval<double, BG>(s, b, ih2, nu, kc, sf[c] + lam, kc != 0.0 ? lsat_c / w : 0.0);
                 su[c] = s.c0 + local_update(o, sp, Df, ih2);
             }
             __syncthreads();
@@ -324,8 +327,9 @@ __global__ void __launch_bounds__(256) k_coarsest(T* __restrict__ u, const T* __
             Stencil<double> s = load_stencil<double>(su, su, i, j, k, n);
             Stencil<double> b;
             if (BG) b = load_stencil<double>(sb, sb, i, j, k, n);
-            const double kc = sk[c] ? 0.0 : kap;
-            Local<double> o = local_eval<double, BG>(s, b, ih2, nu, kc, sf[c] + lam, kc != 0.0 ? lsat_c : 0.0);
+            const double w = sk[c] >= 8 ? 0.0 : (8 - sk[c]) * 0.125;
+            const double kc = kap * w;
+            Local<double> o = local_eval<double, BG>(s, b, ih2, nu, kc, sf[c] + lam, kc != 0.0 ? lsat_c / w : 0.0);
             const bool fl = floor_piece && (o.P != 0.0) && (o.D < Df);
             a0 += fl ? nu * o.g : -o.G;
             a1 += fl ? 0.0 : 1.0;

@@ -86,12 +86,12 @@ __global__ void __launch_bounds__(256) k_residual_zm(const float* __restrict__ u
     for (int s = z0; s < z0 + NZ; ++s) {
         const size_t os = (size_t)s * plane;  // s is inside [0, n)
         float fv[2], gv[2];
-        bool mk[2];
+        float wk[2];  // screening weights
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             fv[h] = F[os + gxy[h]];
             gv[h] = gap ? gap[os + gxy[h]] : 0.f;
-            mk[h] = kmask ? kmask[os + gxy[h]] != 0 : false;
+            wk[h] = screen_w<float>(kmask, os + gxy[h]);
         }
         cp_async_wait_all();  // planes up to s+1
         __syncthreads();
@@ -107,8 +107,8 @@ __global__ void __launch_bounds__(256) k_residual_zm(const float* __restrict__ u
             Stencil<float> a = stencil(up, uc, un, cs[h]);
             Stencil<float> b;
             if (BG) b = stencil(bp, bc, bn, cs[h]);
-            const float kc = mk[h] ? 0.f : kap;
-            const float lsat = kc != 0.f ? lsat_c : 0.f;
+            const float kc = kap * wk[h];
+            const float lsat = kc != 0.f ? lsat_c / wk[h] : 0.f;
             Local<float> o = local_eval<float, BG>(a, b, ih2, nu, kc, fscale * fv[h] + lam, lsat, gap != nullptr, gv[h]);
             // the floored piece exists on the finest level only (see k_residual)
             const bool fl = floor_piece && (o.P != 0.f) && (o.D < Df);

@@ -165,19 +165,19 @@ __global__ void __launch_bounds__(256) k_sweep_fused(const T* __restrict__ U, T*
         const bool black = pb >= z0;
         // this step's right-hand side, gap and mask values, before the barrier
         T rF[NRU], rG[NRU], bF[NBU], bG[NBU];
-        bool rK[NRU], bK[NBU];
+        T rW[NRU], bW[NBU];  // screening weights (1 without a mask)
         {
             const size_t os = (size_t)(s & m) * plane, ob = (size_t)(pb & m) * plane;
 #pragma unroll
             for (int it = 0; it < NRU; ++it) {
                 rF[it] = T(0);
                 rG[it] = T(0);
-                rK[it] = false;
+                rW[it] = T(1);
                 if (r_row[it] >= 0) {
                     const size_t g = os + (size_t)(((r_row[it] + s) & 1) ? r_g1[it] : r_g0[it]);
                     rF[it] = F[g];
                     if (GAP) rG[it] = gap[g];
-                    if (kmask) rK[it] = kmask[g] != 0;
+                    if (kmask) rW[it] = screen_w<T>(kmask, g);
                 }
             }
 #pragma unroll
@@ -185,12 +185,12 @@ __global__ void __launch_bounds__(256) k_sweep_fused(const T* __restrict__ U, T*
                 const int y = b_row[it];
                 bF[it] = T(0);
                 bG[it] = T(0);
-                bK[it] = false;
+                bW[it] = T(1);
                 if (black && y >= 0) {
                     const size_t gb = ob + (size_t)((y0 + y) * n + x0 + b_x2[it] + (((y + pb) & 1) ? 0 : 1));
                     bF[it] = F[gb];
                     if (GAP) bG[it] = gap[gb];
-                    if (kmask) bK[it] = kmask[gb] != 0;
+                    if (kmask) bW[it] = screen_w<T>(kmask, gb);
                 }
             }
         }
@@ -214,9 +214,10 @@ __global__ void __launch_bounds__(256) k_sweep_fused(const T* __restrict__ U, T*
                 Stencil<T> a = stencil_u(up, uc, un, cu);
                 Stencil<T> b;
                 if (BG) b = stencil_u(bp, bc, bn, cu);
-                const T kc = rK[it] ? T(0) : kap;
-                Local<T> o = local_eval<T, BG>(a, b, ih2, nu, kc, fscale * rF[it] + lam, lsat, GAP, rG[it]);
-                rc[r_cr[it] + par] = a.c0 + local_update_fast(o, sp, Df, h2over6, kc != T(0) ? inv2P : T(0));
+                const T kc = kap * rW[it];
+                const T iw = (kmask && kc != T(0)) ? T(1) / rW[it] : T(1);  // L_sat and 1/(2P) scale as 1/kappa
+                Local<T> o = local_eval<T, BG>(a, b, ih2, nu, kc, fscale * rF[it] + lam, lsat * iw, GAP, rG[it]);
+                rc[r_cr[it] + par] = a.c0 + local_update_fast(o, sp, Df, h2over6, kc != T(0) ? inv2P * iw : T(0));
             }
         }
         __syncthreads();
@@ -251,9 +252,10 @@ __global__ void __launch_bounds__(256) k_sweep_fused(const T* __restrict__ U, T*
                 a.eyz = un[cu + G::WU] - up[cu + G::WU] - un[cu - G::WU] + up[cu - G::WU];
                 Stencil<T> b;
                 if (BG) b = stencil_u(bp, bc, bn, cu);
-                const T kc = bK[it] ? T(0) : kap;
-                Local<T> o = local_eval<T, BG>(a, b, ih2, nu, kc, fscale * bF[it] + lam, lsat, GAP, bG[it]);
-                const T vb = a.c0 + local_update_fast(o, sp, Df, h2over6, kc != T(0) ? inv2P : T(0));
+                const T kc = kap * bW[it];
+                const T iw = (kmask && kc != T(0)) ? T(1) / bW[it] : T(1);
+                Local<T> o = local_eval<T, BG>(a, b, ih2, nu, kc, fscale * bF[it] + lam, lsat * iw, GAP, bG[it]);
+                const T vb = a.c0 + local_update_fast(o, sp, Df, h2over6, kc != T(0) ? inv2P * iw : T(0));
                 const T vr = rc[(y + 1) * G::WR + xrd + 1];
                 *reinterpret_cast<float2*>(Vp + (y0 + y) * n + x0 + x2) =
                     par ? make_float2(vb, vr) : make_float2(vr, vb);

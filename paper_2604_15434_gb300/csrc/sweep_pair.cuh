@@ -58,7 +58,7 @@ struct Local2 {
 // local_eval<float, BG> for two cells (h = 1 units; see internal.cuh)
 template <bool BG, bool GAP>
 __device__ __forceinline__ Local2 local_eval2(const Stencil2& s, const Stencil2& b, float ih2, float nu, float2 kap,
-                                              float2 rhs, float lsat_c, float2 gapx)
+                                              float2 rhs, float2 lsat_c, float2 gapx)
 {
     const float2 m2 = f2(-2.f);
     const float2 X = f2fma(m2, s.c0, s.ax);
@@ -88,7 +88,7 @@ __device__ __forceinline__ Local2 local_eval2(const Stencil2& s, const Stencil2&
         if (!GAP) L1tot = f2add(L1, f2add(f2add(Xb, Yb), Zb));
     }
     Local2 o;
-    const float2 lsat = make_float2(kap.x != 0.f ? lsat_c : 0.f, kap.y != 0.f ? lsat_c : 0.f);
+    const float2 lsat = make_float2(kap.x != 0.f ? lsat_c.x : 0.f, kap.y != 0.f ? lsat_c.y : 0.f);
     float2 Ltot;
     if (GAP) {
         o.g = f2fma(f2(-ih2), L1, gapx);  // gap - L1/h^2
@@ -222,10 +222,11 @@ __global__ void __launch_bounds__(16 * TY, TY >= 16 ? 3 : 1) k_sweep_pair(const 
                       f2sub(make_float2(rn[ca - WU], rn[cb - WU]), make_float2(rp[ca - WU], rp[cb - WU])));
         return s;
     };
-    auto update2 = [&](const Local2& o, float2 kc) {
+    // iw: 1/weight of a partly screened cell (L_sat and 1/(2P) scale as 1/kappa)
+    auto update2 = [&](const Local2& o, float2 kc, float2 iw) {
         float2 e;
-        e.x = pick_update(o.G.x, o.Ep.x, o.P.x, o.D.x, o.g.x, sp, Df, h2over6, inv2P);
-        e.y = pick_update(o.G.y, o.Ep.y, o.P.y, o.D.y, o.g.y, sp, Df, h2over6, inv2P);
+        e.x = pick_update(o.G.x, o.Ep.x, o.P.x, o.D.x, o.g.x, sp, Df, h2over6, inv2P * iw.x);
+        e.y = pick_update(o.G.y, o.Ep.y, o.P.y, o.D.y, o.g.y, sp, Df, h2over6, inv2P * iw.y);
         if (kc.x == 0.f || kc.y == 0.f) {  // unscreened cells: the linear (Newton) step
             if (kc.x == 0.f) e.x = __fdividef(-o.G.x, o.Ep.x);
             if (kc.y == 0.f) e.y = __fdividef(-o.G.y, o.Ep.y);
@@ -241,21 +242,20 @@ __global__ void __launch_bounds__(16 * TY, TY >= 16 ? 3 : 1) k_sweep_pair(const 
         const bool black = pb >= z0;
         // this step's right-hand side, gap and mask values, before the barrier
         float2 rF[G::NRU], rG[G::NRU], bF[G::NBU], bG[G::NBU];
-        bool rKa[G::NRU], rKb[G::NRU], bKa[G::NBU], bKb[G::NBU];
+        float2 rW[G::NRU], bW[G::NBU];  // screening weights (1 without a mask)
         {
             const size_t os = (size_t)(s & m) * plane, ob = (size_t)(pb & m) * plane;
 #pragma unroll
             for (int it = 0; it < G::NRU; ++it) {
                 rF[it] = rG[it] = f2(0.f);
-                rKa[it] = rKb[it] = false;
+                rW[it] = f2(1.f);
                 if (r_rowA[it] >= 0) {
                     const size_t ga = os + (size_t)(((r_rowA[it] + s) & 1) ? r_gA1[it] : r_gA0[it]);
                     const size_t gb = os + (size_t)(((r_rowB[it] + s) & 1) ? r_gB1[it] : r_gB0[it]);
                     rF[it] = make_float2(F[ga], F[gb]);
                     if (GAP) rG[it] = make_float2(gap[ga], gap[gb]);
                     if (kmask) {
-                        rKa[it] = kmask[ga] != 0;
-                        rKb[it] = kmask[gb] != 0;
+                        rW[it] = make_float2(screen_w<float>(kmask, ga), screen_w<float>(kmask, gb));
                     }
                 }
             }
@@ -263,14 +263,13 @@ __global__ void __launch_bounds__(16 * TY, TY >= 16 ? 3 : 1) k_sweep_pair(const 
             for (int it = 0; it < G::NBU; ++it) {
                 const int y = b_row[it];
                 bF[it] = bG[it] = f2(0.f);
-                bKa[it] = bKb[it] = false;
+                bW[it] = f2(1.f);
                 if (black && y >= 0) {
                     const size_t ga = ob + (size_t)((y0 + y) * n + x0 + 2 * bkq + (((y + pb) & 1) ? 0 : 1));
                     bF[it] = make_float2(F[ga], F[ga + 32]);
                     if (GAP) bG[it] = make_float2(gap[ga], gap[ga + 32]);
                     if (kmask) {
-                        bKa[it] = kmask[ga] != 0;
-                        bKb[it] = kmask[ga + 32] != 0;
+                        bW[it] = make_float2(screen_w<float>(kmask, ga), screen_w<float>(kmask, ga + 32));
                     }
                 }
             }
@@ -295,10 +294,13 @@ __global__ void __launch_bounds__(16 * TY, TY >= 16 ? 3 : 1) k_sweep_pair(const 
                 const Stencil2 a = stencil2(up, uc, un, ca, cb);
                 Stencil2 b;
                 if (BG) b = stencil2(bp, bc, bn, ca, cb);
-                const float2 kc = make_float2(rKa[it] ? 0.f : kap, rKb[it] ? 0.f : kap);
-                const Local2 o = local_eval2<BG, GAP>(a, b, ih2, nu, kc, f2fma(f2(fscale), rF[it], f2(lam)), lsat,
-                                                      rG[it]);
-                const float2 e = update2(o, kc);
+                const float2 kc = f2mul(f2(kap), rW[it]);
+                const float2 iw = kmask ? make_float2(rW[it].x > 0.f ? 1.f / rW[it].x : 1.f,
+                                                      rW[it].y > 0.f ? 1.f / rW[it].y : 1.f)
+                                        : f2(1.f);
+                const Local2 o = local_eval2<BG, GAP>(a, b, ih2, nu, kc, f2fma(f2(fscale), rF[it], f2(lam)),
+                                                      f2mul(f2(lsat), iw), rG[it]);
+                const float2 e = update2(o, kc, iw);
                 rc[r_crA[it] + pa] = a.c0.x + e.x;
                 rc[r_crB[it] + pbb] = a.c0.y + e.y;
             }
@@ -338,10 +340,13 @@ __global__ void __launch_bounds__(16 * TY, TY >= 16 ? 3 : 1) k_sweep_pair(const 
                               f2sub(make_float2(un[ca - WU], un[cb - WU]), make_float2(up[ca - WU], up[cb - WU])));
                 Stencil2 b;
                 if (BG) b = stencil2(bp, bc, bn, ca, cb);
-                const float2 kc = make_float2(bKa[it] ? 0.f : kap, bKb[it] ? 0.f : kap);
-                const Local2 o = local_eval2<BG, GAP>(a, b, ih2, nu, kc, f2fma(f2(fscale), bF[it], f2(lam)), lsat,
-                                                      bG[it]);
-                const float2 e = update2(o, kc);
+                const float2 kc = f2mul(f2(kap), bW[it]);
+                const float2 iw = kmask ? make_float2(bW[it].x > 0.f ? 1.f / bW[it].x : 1.f,
+                                                      bW[it].y > 0.f ? 1.f / bW[it].y : 1.f)
+                                        : f2(1.f);
+                const Local2 o = local_eval2<BG, GAP>(a, b, ih2, nu, kc, f2fma(f2(fscale), bF[it], f2(lam)),
+                                                      f2mul(f2(lsat), iw), bG[it]);
+                const float2 e = update2(o, kc, iw);
                 const float vba = a.c0.x + e.x, vbb = a.c0.y + e.y;
                 const int rr = (y + 1) * WR + xrd + 1;
                 const float vra = rc[rr], vrb = rc[rr + 32];
