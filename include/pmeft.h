@@ -157,6 +157,18 @@ pm_status pm_step(pm_ctx* ctx, double* pos, double* vel, long long np, int n, do
                   double a, double dt, double tol, double* phi_state, pm_solve_info* info);
 
 /*
+ * nsteps particle-mesh steps (pm_step) at equal steps of supercomoving time t~
+ * (dt~ = H0 dt / a^2, so dt~/da = 1/(a^3 E(a)) on the flat background of Sec. 3.1) from
+ * a_start to a_end, each step's coefficients taken at the scale factor where it starts,
+ * and each chi solve warm-started from the previous step's chi (Sec. 3.5.1): a multi-step
+ * run of the method.  The time integrator is the kick-drift of pm_step (reading: the paper
+ * does not give one).  info (nullable) receives the last step's report; on a solve that
+ * fails, the run stops with that step's status.
+ */
+pm_status pm_run(pm_ctx* ctx, double* pos, double* vel, long long np, int n, double alpha_B0, double alpha_M0,
+                 double a_start, double a_end, int nsteps, double tol, double* phi_state, pm_solve_info* info);
+
+/*
  * Allocation-free CIC deposit.  The paper has no counterpart: this entry point exists
  * for callers that cannot allocate device memory themselves, such as a host
  * application that hands the library a fixed, pre-reserved memory budget, or a

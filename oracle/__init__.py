@@ -280,3 +280,62 @@ def pm_step(pos, vel, n, alpha_B0, alpha_M0, a, dt, tol, chi0=None, omega_m0=OME
     pos2, vel2 = kick_drift(pos, vel, accp, dt)
     return {"acc_fixed": acc_grid_i, "delta": delta, "psiN": psiN, "chi": chi, "info": info, "status": st,
             "acc": accp, "pos": pos2, "vel": vel2}
+
+
+# ---------------------------------------------------------------- several steps and linear growth
+
+def supercomoving_time(a0, a1, omega_m0=OMEGA_M0):
+    """Supercomoving time elapsed from a0 to a1: dt~ = H0 dt / a^2, i.e. dt~/da = 1 / (a^3 E(a)) with
+    E^2 = Omega_m0 a^-3 + 1 - Omega_m0 (the code units of Sec. 3.1, flat background)."""
+    from scipy.integrate import quad
+
+    val, _ = quad(lambda a: 1.0 / (a ** 3 * np.sqrt(omega_m0 / a ** 3 + 1.0 - omega_m0)), a0, a1,
+                  epsabs=0.0, epsrel=1e-13, limit=200)
+    return val
+
+
+def step_schedule(a_start, a_end, nsteps, omega_m0=OMEGA_M0):
+    """(a_n, dt) of nsteps equal supercomoving-time steps from a_start to a_end: a_n is the scale
+    factor at the start of step n, from da/dt~ = a^3 E(a) integrated to 1e-12 (reading R-kd)."""
+    from scipy.integrate import solve_ivp
+
+    T = supercomoving_time(a_start, a_end, omega_m0)
+    dt = T / nsteps
+    ts = dt * np.arange(nsteps)
+    sol = solve_ivp(lambda t, y: [y[0] ** 3 * np.sqrt(omega_m0 / y[0] ** 3 + 1.0 - omega_m0)], (0.0, T),
+                    [a_start], t_eval=ts, rtol=1e-12, atol=0.0, method="DOP853")
+    return sol.y[0], dt
+
+
+def pm_run(pos, vel, n, alpha_B0, alpha_M0, a_start, a_end, nsteps, tol, omega_m0=OMEGA_M0, **kw):
+    """nsteps particle-mesh steps (Sec. 3.5.1) at equal supercomoving-time steps from a_start to
+    a_end, each warm-started from the previous chi (the paper's choice for every step after the
+    first, Sec. 3.5.1).  Returns the final positions, velocities and chi."""
+    a_n, dt = step_schedule(a_start, a_end, nsteps, omega_m0)
+    pos, vel, chi = _f64(pos), _f64(vel), None
+    for a in a_n:
+        out = pm_step(pos, vel, n, alpha_B0, alpha_M0, float(a), dt, tol, chi0=chi, omega_m0=omega_m0, **kw)
+        if out["status"] != 0:
+            raise RuntimeError(f"oracle solve did not converge at a = {a}")
+        pos, vel, chi = out["pos"], out["vel"], out["chi"]
+    return pos, vel, chi
+
+
+def growth_factor(alpha_B0, alpha_M0, a_eval, omega_m0=OMEGA_M0, include_dot=True, a_init=1e-3, y_init=None):
+    """Linear growth D(a) and dD/da of Eq. delta_mod_a:
+        D'' + (3/a + dlnH/da) D' - 3/(2 a^2) Omega_m(a) (G_eff/G) mu_Psi D = 0,
+    mu_Psi = 1 + xi^2/nu (Sec. 2.5), from the matter-era growing mode D = a at a_init (the EFT
+    couplings scale with 1 - Omega_m(a) and vanish there), or from y_init = (D, D') at a_init."""
+    from scipy.integrate import solve_ivp
+
+    def rhs(a, y):
+        c = coefficients(alpha_B0, alpha_M0, a, omega_m0, include_dot)
+        e2 = omega_m0 / a ** 3 + 1.0 - omega_m0
+        dlnh = -1.5 * omega_m0 / a ** 4 / e2
+        mu = c["mu_psi"] if c["xi"] != 0.0 else 1.0
+        return [y[1], -(3.0 / a + dlnh) * y[1] + 1.5 / a ** 2 * c["omega_m_a"] * c["geff"] * mu * y[0]]
+
+    y0 = [a_init, 1.0] if y_init is None else list(y_init)
+    a_eval = np.atleast_1d(np.asarray(a_eval, dtype=np.float64))
+    sol = solve_ivp(rhs, (a_init, float(a_eval.max())), y0, t_eval=a_eval, rtol=1e-11, atol=1e-14, method="DOP853")
+    return sol.y[0], sol.y[1]

@@ -82,6 +82,7 @@ SIGNATURES = {
     "pm_trace_reset": (_I, [_P]),
     "pm_probe_fma": (_I, [_P, _P, _P]),
     "pm_deposit_cic_static": (_I, [_P, _LL, _I, _P, _P]),
+    "pm_run": (_I, [_P, _P, _P, _LL, _I, _D, _D, _D, _D, _I, _D, _P, _P]),
     "pm_mg_sweep_f32": (_I, [_P, _P, _P, ctypes.c_float, _I, _D, _D, _D, _P, _P, _P, _I]),
     "pm_tune_log": (_I, [_P, _P, _I]),
     "scalar_mg_solve_batched": (_I, [_P, _I, _P, _P, _P, _P, _P, _D, _P, _P]),
@@ -311,6 +312,17 @@ def pm_step(pos, vel, n, alpha_B0, alpha_M0, a, dt, tol, phi_state, ctx=None):
     info = SolveInfo()
     ctx._check(load().pm_step(ctx._h, _ptr(pos, name="pos"), _ptr(vel, shape=pos.shape, name="vel"), pos.shape[1], n,
                               alpha_B0, alpha_M0, a, dt, tol, _ptr(phi_state, shape=(n, n, n)), ctypes.byref(info)))
+    return info.as_dict()
+
+
+def pm_run(pos, vel, n, alpha_B0, alpha_M0, a_start, a_end, nsteps, tol, phi_state, ctx=None):
+    """nsteps PM steps in place on pos/vel (3, np) from a_start to a_end (see pm_run in pmeft.h);
+    phi_state (n,n,n): warm start in, last chi out.  Returns the last step's info."""
+    ctx = ctx or default_context()
+    info = SolveInfo()
+    ctx._check(load().pm_run(ctx._h, _ptr(pos, name="pos"), _ptr(vel, shape=pos.shape, name="vel"), pos.shape[1], n,
+                             alpha_B0, alpha_M0, a_start, a_end, nsteps, tol, _ptr(phi_state, shape=(n, n, n)),
+                             ctypes.byref(info)))
     return info.as_dict()
 
 

@@ -321,3 +321,41 @@ extern "C" pm_status pm_step(pm_ctx* ctx, double* pos, double* vel, long long np
     PM_CUDA(cudaStreamSynchronize(ctx->stream));
     return PM_OK;
 }
+
+// ------------------------------------------------------------------ several steps
+
+// supercomoving time per unit scale factor: dt~/da = 1 / (a^3 E(a)), E^2 = Om a^-3 + 1 - Om
+static double dtda(double a, double om) { return 1.0 / (a * a * a * std::sqrt(om / (a * a * a) + 1.0 - om)); }
+static double dadt(double a, double om) { return a * a * a * std::sqrt(om / (a * a * a) + 1.0 - om); }
+
+extern "C" pm_status pm_run(pm_ctx* ctx, double* pos, double* vel, long long np, int n, double alpha_B0,
+                            double alpha_M0, double a_start, double a_end, int nsteps, double tol,
+                            double* phi_state, pm_solve_info* info)
+{
+    PM_TRY(check_common(ctx, n));
+    if (!(a_start > 0.0) || !(a_end >= a_start) || nsteps < 1) {
+        ctx->set_error("pm_run: need 0 < a_start <= a_end and nsteps >= 1");
+        return PM_ERR_INVALID_ARG;
+    }
+    const double om = ctx->prm.omega_m0;
+    // total supercomoving time by composite Simpson in a (4096 intervals), equal steps in it
+    const int K = 4096;
+    const double ha = (a_end - a_start) / K;
+    double T = dtda(a_start, om) + dtda(a_end, om);
+    for (int k = 1; k < K; ++k) T += (k & 1 ? 4.0 : 2.0) * dtda(a_start + k * ha, om);
+    T *= ha / 3.0;
+    const double dt = T / nsteps;
+    double a = a_start;
+    pm_solve_info local{};
+    for (int s = 0; s < nsteps; ++s) {
+        PM_TRY(pm_step(ctx, pos, vel, np, n, alpha_B0, alpha_M0, a, dt, tol, phi_state, info ? info : &local));
+        // advance a over the step: classical Runge-Kutta on da/dt~ = a^3 E(a), 8 substeps
+        const double hs = dt / 8.0;
+        for (int q = 0; q < 8; ++q) {
+            const double k1 = dadt(a, om), k2 = dadt(a + 0.5 * hs * k1, om), k3 = dadt(a + 0.5 * hs * k2, om),
+                         k4 = dadt(a + hs * k3, om);
+            a += hs * (k1 + 2.0 * k2 + 2.0 * k3 + k4) / 6.0;
+        }
+    }
+    return PM_OK;
+}

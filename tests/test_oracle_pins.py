@@ -493,3 +493,55 @@ def test_kick_drift_closed_form_and_wrap():
     p2, v2 = O.kick_drift(pos, vel, acc, 0.01)
     assert np.allclose(v2[:, 0], [1.1, -2.0, -0.04])
     assert np.allclose(p2[:, 0], [(0.95 + 0.011) % 1.0, 0.08, 0.5 - 0.0004])
+
+
+# ---------------------------------------------------------------- several steps and linear growth
+
+
+def test_lcdm_growth_matches_heath_integral():
+    """Eq. delta_mod_a with mu_Psi = G_eff/G = 1 is the LCDM growth equation, whose growing mode
+    is D(a) = (5 Omega_m0 / 2) E(a) int_0^a da' / (a' E(a'))^3 (normalised to D -> a early)."""
+    from scipy.integrate import quad
+
+    om = O.OMEGA_M0
+    E = lambda a: math.sqrt(om / a ** 3 + 1.0 - om)  # noqa: E731
+    a_ev = [0.2, 0.5, 1.0]
+    D, dD = O.growth_factor(0.0, 0.0, a_ev)
+    for a, d in zip(a_ev, D):
+        want = 2.5 * om * E(a) * quad(lambda x: 1.0 / (x * E(x)) ** 3, 0.0, a, epsrel=1e-12)[0]
+        assert d == pytest.approx(want, rel=2e-7)
+
+
+def test_supercomoving_schedule_einstein_de_sitter():
+    """With Omega_m0 = 1, dt~/da = a^(-3/2): the run lasts 2 (a0^-1/2 - a1^-1/2) and the step
+    starts satisfy a_n^-1/2 = a0^-1/2 - n dt / 2."""
+    a_n, dt = O.step_schedule(0.25, 1.0, 8, omega_m0=1.0)
+    assert dt * 8 == pytest.approx(2.0 * (0.25 ** -0.5 - 1.0), rel=1e-12)
+    want = (0.25 ** -0.5 - 0.5 * dt * np.arange(8)) ** -2
+    assert np.allclose(a_n, want, rtol=1e-10)
+
+
+def test_multistep_run_reproduces_linear_growth_ratio():
+    """Several PM steps from Zel'dovich initial conditions at a = 0.1 to a = 1 (16^3, 30 steps):
+    on the largest scales the EFT / LCDM ratio of the density modes follows the ratio of the
+    growth factors of Eq. delta_mod_a (the paper's large-scale check of Sec. 4.2)."""
+    n, a_i, a_f = 16, 0.1, 1.0
+    x0 = synth.zeldovich_particles(n, -1.5, 1.0, 4242)
+    q = (np.indices((n, n, n))[::-1].reshape(3, -1) + 0.5) / n
+    psi = (x0 - q + 0.5) % 1.0 - 0.5
+    D, dD = O.growth_factor(0.0, 0.0, [a_i, a_f])
+    s = 0.1 / D[1]
+    pos = (q + s * D[0] * psi) % 1.0
+    vel = s * a_i ** 3 * math.sqrt(0.3 / a_i ** 3 + 0.7) * dD[0] * psi
+
+    def fundamental(p):
+        F = np.fft.rfftn(O.density(O.deposit_cic(p, n), p.shape[1]))
+        return np.array([F[0, 0, 1], F[0, 1, 0], F[1, 0, 0]])
+
+    m = {}
+    for name, ab in (("lcdm", (0.0, 0.0)), ("eft", (-0.5, 0.0))):
+        p, v, chi = O.pm_run(pos, vel, n, ab[0], ab[1], a_i, a_f, 30, 1e-9)
+        m[name] = fundamental(p)
+    De, _ = O.growth_factor(-0.5, 0.0, [a_f], a_init=a_i, y_init=(D[0], dD[0]))
+    ratio = np.real(m["eft"] / m["lcdm"])
+    assert np.all(np.abs(ratio / (De[0] / D[1]) - 1.0) < 5e-3), ratio
