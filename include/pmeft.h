@@ -50,6 +50,9 @@ typedef struct {
     int include_dot_alphaB;/* 1: keep alpha_B-dot/H = d alpha_B/d ln a in C2 (Sec. 2.2) */
     int inner_cycles;      /* precision 1: FP32 V-cycles on the correction per FP64 outer residual (2) */
     int autotune;          /* 1: time the tile variants of the FP32 sweep on first use of each size (1) */
+    int linear_eft;        /* 1: pm_step / pm_run use the linearised equations (Sec. 2.5, Eq. linearised):
+                              chi = (xi/nu) Psi_N from the one FFT Poisson solve, no screening and no
+                              chi multigrid solve (0) */
 } pm_params;
 
 /* Report of one solve.  rel_res = |r|_2 / |f - <f>|_2 of the FP64 residual. */
@@ -148,9 +151,18 @@ pm_status force_interp(pm_ctx* ctx, const double* psi_N, const double* phi, int 
                        double alpha_M0, double a, const double* pos, long long np, double* acc);
 
 /*
+ * Lensing potential (Eq. phipsi_mod, second line): Phi = Psi_N + alpha_B(a) chi, i.e.
+ * L Phi = (3/2)(G_eff/G) a Omega_m0 delta + alpha_B L chi.  psi_N, chi, Phi: device n^3.
+ * In the linear regime Phi = mu_Phi Psi_N with mu_Phi = 1 + xi alpha_B / nu (Eq. linearised).
+ */
+pm_status lensing_potential(pm_ctx* ctx, const double* psi_N, const double* chi, int n, double alpha_B0,
+                            double alpha_M0, double a, double* Phi);
+
+/*
  * One particle-mesh step (Sec. 3.5.1 order): deposit, Poisson, chi solve (warm
- * started from phi_state, which receives chi), force interpolation, then one kick
- * and one drift: v += g dt; x = frac(x + v dt).  pos, vel: device [3][np], updated
+ * started from phi_state, which receives chi; with params.linear_eft the linearised
+ * chi = (xi/nu) Psi_N instead), force interpolation, then one kick and one drift:
+ * v += g dt; x = frac(x + v dt).  pos, vel: device [3][np], updated
  * in place.  phi_state: device n^3.  info as for scalar_mg_solve.
  */
 pm_status pm_step(pm_ctx* ctx, double* pos, double* vel, long long np, int n, double alpha_B0, double alpha_M0,

@@ -268,13 +268,20 @@ def kick_drift(pos, vel, acc, dt):
     return pos, vel
 
 
-def pm_step(pos, vel, n, alpha_B0, alpha_M0, a, dt, tol, chi0=None, omega_m0=OMEGA_M0, include_dot=True, **kw):
-    """One particle-mesh step: deposit, Poisson, chi solve, force, kick-drift (Sec. 3.5.1 step order)."""
+def pm_step(pos, vel, n, alpha_B0, alpha_M0, a, dt, tol, chi0=None, omega_m0=OMEGA_M0, include_dot=True,
+            linear=False, **kw):
+    """One particle-mesh step: deposit, Poisson, chi solve, force, kick-drift (Sec. 3.5.1 step order).
+    linear: the linearised equations (Sec. 2.5, Eq. linearised): nu L chi = xi S with L Psi_N = S,
+    so chi = (xi / nu) Psi_N, with no screening term and no multigrid solve."""
     c = coefficients(alpha_B0, alpha_M0, a, omega_m0, include_dot)
     acc_grid_i = deposit_cic(pos, n)
     delta = density(acc_grid_i, pos.shape[1])
     psiN = poisson_fft(delta, c, a, omega_m0)
-    chi, info, st = scalar_solve(delta, alpha_B0, alpha_M0, a, tol, omega_m0, include_dot, chi0=chi0, **kw)
+    if linear:
+        chi = (c["xi"] / c["nu"]) * psiN if c["xi"] != 0.0 else np.zeros_like(psiN)
+        info, st = {"cycles": 0}, 0
+    else:
+        chi, info, st = scalar_solve(delta, alpha_B0, alpha_M0, a, tol, omega_m0, include_dot, chi0=chi0, **kw)
     g = accel_grid(psiN, chi, c["xi"], n)
     accp = interp_cic(g, pos)
     pos2, vel2 = kick_drift(pos, vel, accp, dt)
@@ -339,3 +346,9 @@ def growth_factor(alpha_B0, alpha_M0, a_eval, omega_m0=OMEGA_M0, include_dot=Tru
     a_eval = np.atleast_1d(np.asarray(a_eval, dtype=np.float64))
     sol = solve_ivp(rhs, (a_init, float(a_eval.max())), y0, t_eval=a_eval, rtol=1e-11, atol=1e-14, method="DOP853")
     return sol.y[0], sol.y[1]
+
+
+def lensing_potential(psiN, chi, alpha_B0, alpha_M0, a, omega_m0=OMEGA_M0, include_dot=True):
+    """Phi = Psi_N + alpha_B chi (Eq. phipsi_mod, second line: L Phi = S + alpha_B L chi)."""
+    c = coefficients(alpha_B0, alpha_M0, a, omega_m0, include_dot)
+    return _f64(psiN) + c["alpha_B"] * _f64(chi)

@@ -32,7 +32,7 @@ class Params(ctypes.Structure):
     _fields_ = [("omega_m0", ctypes.c_double), ("eta", ctypes.c_double), ("npre", ctypes.c_int),
                 ("npost", ctypes.c_int), ("max_cycles", ctypes.c_int), ("coarsest_n", ctypes.c_int),
                 ("coarse_sweeps", ctypes.c_int), ("precision", ctypes.c_int), ("include_dot_alphaB", ctypes.c_int),
-                ("inner_cycles", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("inner_cycles", ctypes.c_int), ("autotune", ctypes.c_int), ("linear_eft", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -82,6 +82,7 @@ SIGNATURES = {
     "pm_trace_reset": (_I, [_P]),
     "pm_probe_fma": (_I, [_P, _P, _P]),
     "pm_deposit_cic_static": (_I, [_P, _LL, _I, _P, _P]),
+    "lensing_potential": (_I, [_P, _P, _P, _I, _D, _D, _D, _P]),
     "pm_run": (_I, [_P, _P, _P, _LL, _I, _D, _D, _D, _D, _I, _D, _P, _P]),
     "pm_mg_sweep_f32": (_I, [_P, _P, _P, ctypes.c_float, _I, _D, _D, _D, _P, _P, _P, _I]),
     "pm_tune_log": (_I, [_P, _P, _I]),
@@ -304,6 +305,17 @@ def force_interp(psi_N, phi, alpha_B0, alpha_M0, a, pos, acc=None, ctx=None):
     ctx._check(load().force_interp(ctx._h, _ptr(psi_N, shape=(n, n, n)), _ptr(phi, shape=(n, n, n)), n, alpha_B0,
                                    alpha_M0, a, _ptr(pos, name="pos"), pos.shape[1], _ptr(acc, shape=pos.shape)))
     return acc
+
+
+def lensing_potential(psi_N, chi, alpha_B0, alpha_M0, a, Phi=None, ctx=None):
+    """Phi = Psi_N + alpha_B(a) chi on the device (see lensing_potential in pmeft.h)."""
+    ctx = ctx or default_context()
+    n = psi_N.shape[0]
+    if Phi is None:
+        Phi = torch.empty_like(psi_N)
+    ctx._check(load().lensing_potential(ctx._h, _ptr(psi_N, shape=(n, n, n)), _ptr(chi, shape=(n, n, n)), n, alpha_B0,
+                                        alpha_M0, a, _ptr(Phi, shape=(n, n, n))))
+    return Phi
 
 
 def pm_step(pos, vel, n, alpha_B0, alpha_M0, a, dt, tol, phi_state, ctx=None):

@@ -176,6 +176,7 @@ extern "C" void pm_default_params(pm_params* p)
     p->include_dot_alphaB = 1;
     p->inner_cycles = 2;
     p->autotune = 1;
+    p->linear_eft = 0;
 }
 
 static bool params_ok(const pm_params* p)
@@ -184,7 +185,7 @@ static bool params_ok(const pm_params* p)
            p->npost >= 0 && p->npre + p->npost > 0 && p->max_cycles >= 0 && p->coarsest_n >= 2 &&
            p->coarsest_n <= 8 && (p->coarsest_n & (p->coarsest_n - 1)) == 0 && p->coarse_sweeps >= 1 &&
            (p->precision == 0 || p->precision == 1) && p->inner_cycles >= 1 && p->inner_cycles <= 16 &&
-           (p->autotune == 0 || p->autotune == 1);
+           (p->autotune == 0 || p->autotune == 1) && (p->linear_eft == 0 || p->linear_eft == 1);
 }
 
 extern "C" pm_status pm_coefficients(double aB0, double aM0, double a, double om0, int include_dot, pm_coeffs* out)

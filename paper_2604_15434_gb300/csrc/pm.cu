@@ -135,6 +135,23 @@ __global__ void k_kick_drift(double* __restrict__ pos, double* __restrict__ vel,
     }
 }
 
+// out = s * x (+ y), each product and sum rounded as written
+__global__ void k_scale_add(const double* __restrict__ x, double s, const double* __restrict__ y, size_t total,
+                            double* __restrict__ out)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const double v = __dmul_rn(s, x[i]);
+        out[i] = y ? __dadd_rn(y[i], v) : v;
+    }
+}
+
+static void scale_add(pm_ctx* ctx, const double* x, double s, const double* y, size_t total, double* out)
+{
+    ctx->begin(PM_K_PM, false, 0);
+    k_scale_add<<<grid_for(ctx, total), kThreads, 0, ctx->stream>>>(x, s, y, total, out);
+    ctx->end();
+}
+
 pm_status deposit(pm_ctx* ctx, const double* pos, long long np, int n, long long* acc)
 {
     const size_t cells = (size_t)n * n * n;
@@ -305,8 +322,18 @@ extern "C" pm_status pm_step(pm_ctx* ctx, double* pos, double* vel, long long np
     PM_TRY(deposit(ctx, pos, np, n, w->acc));
     PM_TRY(density(ctx, w->acc, n, np, w->delta));
     PM_TRY(poisson(ctx, w->delta, n, cf.poisson_fac, w->psi));
-    pm_status st = mg_solve(ctx, w->delta, n, cf, tol, phi_state, info);
-    if (st != PM_OK) return st;
+    if (ctx->prm.linear_eft) {
+        // linearised equations: nu L chi = xi S and L Psi_N = S, so chi = (xi / nu) Psi_N
+        if (cf.nu == 0.0 && cf.xi != 0.0) {
+            ctx->set_error("pm_step: nu = 0, the linearised chi equation is degenerate");
+            return PM_ERR_INVALID_ARG;
+        }
+        scale_add(ctx, w->psi, cf.xi != 0.0 ? cf.xi / cf.nu : 0.0, nullptr, cells, phi_state);
+        if (info) *info = pm_solve_info{};
+    } else {
+        pm_status st = mg_solve(ctx, w->delta, n, cf, tol, phi_state, info);
+        if (st != PM_OK) return st;
+    }
     // the acceleration goes into the (now free) fixed-point grid's storage when it fits
     double* acc = nullptr;
     const size_t need = (size_t)3 * np * sizeof(double);
@@ -357,5 +384,20 @@ extern "C" pm_status pm_run(pm_ctx* ctx, double* pos, double* vel, long long np,
             a += hs * (k1 + 2.0 * k2 + 2.0 * k3 + k4) / 6.0;
         }
     }
+    return PM_OK;
+}
+
+extern "C" pm_status lensing_potential(pm_ctx* ctx, const double* psi_N, const double* chi, int n, double alpha_B0,
+                                       double alpha_M0, double a, double* Phi)
+{
+    PM_TRY(check_common(ctx, n));
+    if (!psi_N || !chi || !Phi || !(a > 0.0)) {
+        ctx->set_error("lensing_potential: null buffer or a <= 0");
+        return PM_ERR_INVALID_ARG;
+    }
+    pm_coeffs cf;
+    coefficients(alpha_B0, alpha_M0, a, ctx->prm.omega_m0, ctx->prm.include_dot_alphaB, &cf);
+    scale_add(ctx, chi, cf.alpha_B, psi_N, (size_t)n * n * n, Phi);
+    PM_CUDA(cudaGetLastError());
     return PM_OK;
 }

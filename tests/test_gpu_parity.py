@@ -402,7 +402,7 @@ def test_multistep_growth_matches_linear_theory_64(gpu_lib):
     """A 64^3 run of 100 steps on the GPU (mixed-precision solves) from Zel'dovich initial
     conditions at a = 0.1: the largest-scale density modes grow as the LCDM growth factor, and
     the EFT run (alpha_B0 = -0.5) exceeds the LCDM run from the same initial conditions by the
-    ratio of the growth factors of Eq. delta_mod_a."""
+    ratio of the growth factors of Eq. delta_mod_a, as does the linearised-mode run."""
     import math
 
     n, a_i, a_f = 64, 0.1, 1.0
@@ -421,13 +421,37 @@ def test_multistep_growth_matches_linear_theory_64(gpu_lib):
 
     m0 = fundamental(cu(pos))
     m = {}
-    for name, ab in (("lcdm", (0.0, 0.0)), ("eft", (-0.5, 0.0))):
+    for name, ab, lin in (("lcdm", (0.0, 0.0), 0), ("eft", (-0.5, 0.0), 0), ("eft_lin", (-0.5, 0.0), 1)):
         p, v = cu(pos), cu(vel)
         phi = torch.zeros((n, n, n), dtype=torch.float64, device=DEV)
-        gpu_lib.pm_run(p, v, n, ab[0], ab[1], a_i, a_f, 100, 1e-8, phi, ctx=gpu_lib.Context(precision=1, max_cycles=100))
+        ctx = gpu_lib.Context(precision=1, max_cycles=100, linear_eft=lin)
+        gpu_lib.pm_run(p, v, n, ab[0], ab[1], a_i, a_f, 100, 1e-8, phi, ctx=ctx)
         m[name] = fundamental(p)
     De, _ = O.growth_factor(-0.5, 0.0, [a_f], a_init=a_i, y_init=(D[0], dD[0]))
     growth = np.real(m["lcdm"] / m0)
     assert abs(growth.mean() / (D[1] / D[0]) - 1.0) < 0.03, growth
     ratio = np.real(m["eft"] / m["lcdm"])
     assert np.all(np.abs(ratio / (De[0] / D[1]) - 1.0) < 5e-3), ratio
+    # the linearised run (no screening) agrees on these scales, where screening is negligible
+    ratio_lin = np.real(m["eft_lin"] / m["lcdm"])
+    assert np.all(np.abs(ratio_lin / (De[0] / D[1]) - 1.0) < 5e-3), ratio_lin
+    assert np.all(np.abs(ratio / ratio_lin - 1.0) < 3e-3)
+
+
+def test_linearised_pm_step_and_lensing_potential(gpu_lib, c1_particles):
+    """The linearised mode of the PM step (chi = (xi/nu) Psi_N, no chi solve) and the lensing
+    potential Phi = Psi_N + alpha_B chi against the oracle."""
+    n = 32
+    pos = c1_particles
+    vel = 0.01 * np.random.default_rng(4).standard_normal(pos.shape)
+    aB0, aM0, a = -0.5, 0.2, 0.8
+    want = O.pm_step(pos, vel, n, aB0, aM0, a, 1e-3, 1e-12, linear=True)
+    p, v = cu(pos), cu(vel)
+    phi = torch.zeros((n, n, n), dtype=torch.float64, device=DEV)
+    ctx = gpu_lib.Context(precision=0, linear_eft=1)
+    gpu_lib.pm_step(p, v, n, aB0, aM0, a, 1e-3, 1e-12, phi, ctx=ctx)
+    assert rel(phi.cpu().numpy(), want["chi"]) < 1e-12
+    assert rel(v.cpu().numpy(), want["vel"]) < 1e-12
+    psiN = gpu_lib.poisson_solve(cu(want["delta"]), a, aM0, ctx=ctx)
+    Phi = gpu_lib.lensing_potential(psiN, phi, aB0, aM0, a, ctx=ctx).cpu().numpy()
+    assert rel(Phi, O.lensing_potential(want["psiN"], want["chi"], aB0, aM0, a)) < 1e-12

@@ -545,3 +545,28 @@ def test_multistep_run_reproduces_linear_growth_ratio():
     De, _ = O.growth_factor(-0.5, 0.0, [a_f], a_init=a_i, y_init=(D[0], dD[0]))
     ratio = np.real(m["eft"] / m["lcdm"])
     assert np.all(np.abs(ratio / (De[0] / D[1]) - 1.0) < 5e-3), ratio
+
+
+def test_linearised_mode_equals_unscreened_solve_and_mu_factors():
+    """Eq. linearised: with the screening term dropped, nu L chi = xi S, so the linear-mode chi =
+    (xi/nu) Psi_N is the kappa = 0 multigrid solution of the same source; and
+    then Psi = Psi_N + (alpha_B - alpha_M) chi = mu_Psi Psi_N, Phi = mu_Phi Psi_N with
+    mu_Psi = 1 + xi^2/nu and mu_Phi = 1 + xi alpha_B / nu."""
+    n = 16
+    pos = synth.zeldovich_particles(n, -1.5, 0.5, 31)
+    vel = np.zeros_like(pos)
+    aB0, aM0, a = -0.5, 0.2, 0.8
+    c = O.coefficients(aB0, aM0, a)
+    out = O.pm_step(pos, vel, n, aB0, aM0, a, 1e-3, 1e-12, linear=True)
+    psiN, chi = out["psiN"], out["chi"]
+    f = O.source(out["delta"], c)
+    chi_mg, info, st = O.mg_solve(f, c["nu"], 0.0, 1e-13)
+    assert st == 0
+    chi_mg = chi_mg - chi_mg.mean()
+    assert np.linalg.norm(chi - chi_mg) < 1e-9 * np.linalg.norm(chi_mg)
+    psi = psiN + c["xi"] * chi
+    assert np.allclose(psi, (1.0 + c["xi"] ** 2 / c["nu"]) * psiN, rtol=0, atol=1e-14 * np.abs(psiN).max())
+    assert c["mu_psi"] == pytest.approx(1.0 + c["xi"] ** 2 / c["nu"], rel=1e-14)
+    Phi = O.lensing_potential(psiN, chi, aB0, aM0, a)
+    assert np.allclose(Phi, (1.0 + c["xi"] * c["alpha_B"] / c["nu"]) * psiN, rtol=0,
+                       atol=1e-14 * np.abs(psiN).max())
