@@ -79,6 +79,7 @@ static void free_level(Level<T>& L)
     cudaFree(L.kmask);
     cudaFree(L.bg);
     cudaFree(L.gap);
+    cudaFree(L.coef);
     L = Level<T>();
 }
 
@@ -115,6 +116,7 @@ pm_status ensure_mg(pm_ctx* ctx, Workspace* w, bool want_fp32)
         // the inner level 0 keeps its right-hand side in rplain; give it the f slot too
         PM_CUDA(cudaMalloc(&w->rplain, w->s[0].cells * sizeof(float)));
         PM_CUDA(cudaMalloc(&w->s[0].gap, w->s[0].cells * sizeof(float)));
+        if (n >= kCoefMinN) PM_CUDA(cudaMalloc(&w->s[0].coef, 3 * w->s[0].cells * sizeof(uint32_t)));
     }
     return PM_OK;
 }

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include <cufft.h>
 
 #include <cstdint>
@@ -95,6 +96,8 @@ struct Level {
     T* ur = nullptr;        // restriction of the finer iterate (for the FAS correction)
     T* bg = nullptr;        // background field of the correction form (mixed precision), or null
     T* gap = nullptr;       // L_sat - L(background) from the FP64 iterate (finest inner level), or null
+    uint32_t* coef = nullptr;  // the background's bilinear coefficients, 3 planes of BF16 pairs (finest
+                               // inner level of grids >= kCoefMinN), or null
     const T* lamp = nullptr;   // device scalar added to the right-hand side (graph-captured solves), or null
     uint8_t* kmask = nullptr;  // 1: screening term off (coarse levels)
     uint8_t* sat = nullptr;    // 1: floored piece used by the last residual
@@ -362,6 +365,67 @@ __device__ __forceinline__ Local<T> local_eval(const Stencil<T>& s, const Stenci
     o.Ep = (T(-6) * nu + T(8) * kap * o.L) * ih2;
     o.P = T(-24) * kap1;
     o.D = o.Ep * o.Ep - T(4) * o.P * o.G;
+    return o;
+}
+
+// ---------------------------------------------------------------- background coefficients
+//
+// In the correction form the background b enters the operator only through the bilinear
+// part of q2(b + u) - q2(b) - q2(u) = cX X + cY Y + cZ Z + cxy exy + cxz exz + cyz eyz
+// (h = 1 units, X = u_xx h^2 ..., exy the raw 4-point cross difference of u), with
+// cX = 2(Yb + Zb), cY = 2(Xb + Zb), cZ = 2(Xb + Yb), cxy = -bxy/4, cxz = -bxz/4, cyz = -byz/4
+// from b's second and cross differences.  The finest inner level of large grids keeps these
+// six numbers per cell in BF16 (three planes of packed pairs, 12 bytes per cell), written
+// by the outer residual once per outer iteration from the differences of the float-float
+// iterate it has just formed (whose high parts b is), instead of re-reading b's 19-point
+// stencil in every sweep.  BF16 perturbs only this bilinear part of the inner
+// (preconditioning) operator, by 2^-9 relative; the outer float-float residual, which
+// decides convergence, is unaffected.
+constexpr int kCoefMinN = 256;
+
+struct BgCoef {
+    float cX, cY, cZ, cxy, cxz, cyz;
+};
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ BgCoef unpack_bg_coef(uint32_t k0, uint32_t k1, uint32_t k2)
+{
+    return BgCoef{__uint_as_float(k0 << 16), __uint_as_float(k0 & 0xffff0000u), __uint_as_float(k1 << 16),
+                  __uint_as_float(k1 & 0xffff0000u), __uint_as_float(k2 << 16), __uint_as_float(k2 & 0xffff0000u)};
+}
+
+// local_eval<float, BG = true> with the gap of the finest inner level, the background given
+// by its coefficients
+__device__ __forceinline__ Local<float> local_eval_cf(const Stencil<float>& s, const BgCoef& cf, float ih2, float nu,
+                                                      float kap, float rhs, float lsat, float gapx)
+{
+    const float X = s.ax - 2.f * s.c0;
+    const float Y = s.ay - 2.f * s.c0;
+    const float Z = s.az - 2.f * s.c0;
+    Local<float> o;
+    const float L1 = X + Y + Z;
+    float q2 = 2.f * (X * Y + Y * Z + Z * X) - 0.125f * (s.exy * s.exy + s.exz * s.exz + s.eyz * s.eyz);
+    q2 += cf.cX * X + cf.cY * Y + cf.cZ * Z + cf.cxy * s.exy + cf.cxz * s.exz + cf.cyz * s.eyz;
+    float Ltot;
+    if (kap != 0.f) {
+        o.g = gapx - L1 * ih2;
+        Ltot = lsat - o.g;
+    } else {
+        o.g = 0.f;
+        Ltot = L1 * ih2;  // unused: the screening term is off
+    }
+    o.L = Ltot;
+    const float nu1 = nu * ih2, kap1 = kap * ih2 * ih2;
+    const float N = nu1 * L1 - kap1 * q2;
+    o.G = N - rhs;
+    o.Ep = (-6.f * nu + 8.f * kap * o.L) * ih2;
+    o.P = -24.f * kap1;
+    o.D = o.Ep * o.Ep - 4.f * o.P * o.G;
     return o;
 }
 

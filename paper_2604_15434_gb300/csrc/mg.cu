@@ -445,17 +445,18 @@ static void launch_fused(Exec* ctx, const float* A, float* B, const float* F, fl
                                       (float)c.kap, sp, Df, lsn, L.lamp);
 }
 
-template <int TY, bool BG, bool GAP>
+template <int TY, bool BG, bool GAP, bool COEF = false>
 static void launch_pair(Exec* ctx, const float* A, float* B, const float* F, float fscale, float lam,
                         const Level<float>& L, int nz, float h2inv, const Coef& c, float sp, float Df, float lsn)
 {
     const int n = L.n;
-    constexpr size_t sm = pair_smem_bytes<TY, BG>();
-    auto k = k_sweep_pair<TY, BG, GAP>;
+    constexpr size_t sm = pair_smem_bytes<TY, BG, COEF>();
+    auto k = k_sweep_pair<TY, BG, GAP, COEF>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     const dim3 grid(n / 64, n / TY, n / nz);
     k<<<grid, PairGeom<TY>::NT, sm, ctx->stream>>>(A, B, F, fscale, lam, L.kmask, L.bg, L.gap, n, nz, h2inv,
-                                                   (float)c.nu, (float)c.kap, sp, Df, lsn, L.lamp);
+                                                   (float)c.nu, (float)c.kap, sp, Df, lsn, L.lamp,
+                                                   COEF ? L.coef : nullptr);
 }
 
 template <bool BG, bool GAP>
@@ -470,7 +471,10 @@ static void launch_fused_cfg(Exec* ctx, int cfg, const float* A, float* B, const
     }
 #define PM_PAIR_CASE(TY_)                                                                              \
     if (g.pair && g.ty == TY_) {                                                                       \
-        launch_pair<TY_, BG, GAP>(ctx, A, B, F, fscale, lam, L, g.nz, h2inv, c, sp, Df, lsn);          \
+        if (BG && GAP && L.coef)                                                                       \
+            launch_pair<TY_, true, true, true>(ctx, A, B, F, fscale, lam, L, g.nz, h2inv, c, sp, Df, lsn); \
+        else                                                                                           \
+            launch_pair<TY_, BG, GAP>(ctx, A, B, F, fscale, lam, L, g.nz, h2inv, c, sp, Df, lsn);      \
         return;                                                                                        \
     }
     PM_FUSED_CASE(64, 16)
@@ -515,10 +519,13 @@ static void sweep_fused_f32(Exec* ctx, Level<float>& L, const float* F, float fs
 // unchanged whichever runs last) and the fastest is kept for that key.
 static int tuned_cfg(Exec* ctx, Level<float>& L, const float* F, float fscale, float lam, const Coef& c)
 {
-    const int key = L.n * 4 + (L.bg ? 2 : 0) + (L.gap ? 1 : 0);
+    const bool cf = L.coef && L.gap;
+    const int key = L.n * 8 + (cf ? 4 : 0) + (L.bg ? 2 : 0) + (L.gap ? 1 : 0);
     auto it = ctx->tuned.find(key);
     if (it != ctx->tuned.end()) return it->second;
     int best = 0;
+    if (cf)  // only the pair kernel reads coefficients: start from its first variant
+        while (best + 1 < kNumFusedCfgs && !kFusedCfgs[best].pair) ++best;
     if (ctx->prm.autotune) {
         float best_ms = 1e30f;
         cudaEvent_t e0, e1;
@@ -528,6 +535,7 @@ static int tuned_cfg(Exec* ctx, Level<float>& L, const float* F, float fscale, f
         ctx->c->tracing = false;
         for (int cfg = 0; cfg < kNumFusedCfgs; ++cfg) {
             if (!fused_cfg_fits(cfg, L.n)) continue;
+            if (L.coef && L.gap && !kFusedCfgs[cfg].pair) continue;  // only the pair kernel reads coefficients
             // one untimed launch, then three timed back to back
             for (int rep = 0; rep < 2; ++rep) {
                 const int launches = rep == 0 ? 1 : 3;
@@ -551,6 +559,7 @@ static int tuned_cfg(Exec* ctx, Level<float>& L, const float* F, float fscale, f
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         ctx->tune_log += "sweep32 n=" + std::to_string(L.n) + (L.bg ? " bg" : "") + (L.gap ? " gap" : "") +
+                         (cf ? " coef" : "") +
                          ": tile " + std::to_string(kFusedCfgs[best].tx) + "x" + std::to_string(kFusedCfgs[best].ty) +
                          " nz " + std::to_string(kFusedCfgs[best].nz) + (kFusedCfgs[best].pair ? " pair" : " single") +
                          " " + std::to_string(best_ms) + " ms\n";
@@ -622,16 +631,23 @@ static int residual(Exec* ctx, Level<T>& L, const T* u, const T* F, T fscale, T 
             const dim3 g3(n / kRzTX, n / kRzTY, n / nz);
             const int nb = (int)(g3.x * g3.y * g3.z);
             ctx->begin(PM_K_RESID32, L.fine, (long long)L.cells);
-            if (L.bg) {
+            if (L.coef && L.gap) {
+                constexpr size_t sm = resid_zm_smem_bytes<true, true>();
+                k_residual_zm<true, true><<<g3, 256, sm, ctx->stream>>>(
+                    u, F, fscale, lam, L.kmask, L.bg, L.gap, n, nz, h2inv, (T)c.nu, (T)c.kap, (T)(sqDf * sqDf), lsn,
+                    L.fine, L.r, L.sat, ctx->red_partials, L.lamp, L.coef);
+            } else if (L.bg) {
                 constexpr size_t sm = resid_zm_smem_bytes<true>();
                 k_residual_zm<true><<<g3, 256, sm, ctx->stream>>>(u, F, fscale, lam, L.kmask, L.bg, L.gap, n, nz,
                                                                   h2inv, (T)c.nu, (T)c.kap, (T)(sqDf * sqDf), lsn,
-                                                                  L.fine, L.r, L.sat, ctx->red_partials, L.lamp);
+                                                                  L.fine, L.r, L.sat, ctx->red_partials, L.lamp,
+                                                                  nullptr);
             } else {
                 constexpr size_t sm = resid_zm_smem_bytes<false>();
                 k_residual_zm<false><<<g3, 256, sm, ctx->stream>>>(u, F, fscale, lam, L.kmask, nullptr, nullptr, n, nz,
                                                                    h2inv, (T)c.nu, (T)c.kap, (T)(sqDf * sqDf), lsn,
-                                                                   L.fine, L.r, L.sat, ctx->red_partials, L.lamp);
+                                                                   L.fine, L.r, L.sat, ctx->red_partials, L.lamp,
+                                                                   nullptr);
             }
             ctx->end();
             ctx->begin(PM_K_REDUCE, false, 0);
@@ -771,7 +787,7 @@ static void residual_ff(Exec* ctx, Workspace* w, const float2* xff, const float2
         const dim3 g3(n / kFzTX, n / kFzTY, n / nz);
         grid = (int)(g3.x * g3.y * g3.z);
         k_residual_ff_zm<<<g3, 256, kFzSmem, ctx->stream>>>(xff, fff, lam, lamp, n, nz, fk, w->rplain, w->s[0].bg,
-                                                            w->s[0].gap, ctx->red_partials);
+                                                            w->s[0].gap, w->s[0].coef, ctx->red_partials);
     } else {
         k_residual_ff<<<grid, kThreads, 0, ctx->stream>>>(xff, fff, lam, lamp, n, fk, w->rplain, w->s[0].bg,
                                                           w->s[0].gap, ctx->red_partials);
@@ -1016,6 +1032,7 @@ extern "C" pm_status pm_mg_sweep_f32(pm_ctx* ctx, float* u, const float* f, floa
     L.kmask = (uint8_t*)kmask;
     L.bg = (float*)bg;
     L.gap = (float*)gap;
+    L.coef = nullptr;  // the background is the caller's field, not the solve's coefficients
     L.cur = 0;
     const size_t cells = L.cells;
     PM_CUDA(cudaMemcpyAsync(L.u[0], u, cells * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));

@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(256) k_residual_ff_zm(const float2* __restrict
                                                         double lam_host, const double* __restrict__ lamp, int n,
                                                         int NZ, FFCoef k, float* __restrict__ rplain,
                                                         float* __restrict__ chi32, float* __restrict__ gap32,
-                                                        double* __restrict__ partials)
+                                                        uint32_t* __restrict__ coef, double* __restrict__ partials)
 {
     const ff lam1 = ff_from_double(lam_host + (lamp ? *lamp : 0.0));
     const ff2 lam = ff2_splat(lam1);
@@ -356,6 +356,21 @@ __global__ void __launch_bounds__(256) k_residual_ff_zm(const float2* __restrict
         const ff2 ng = ff2_mul(nu, g);
         const float rvA = flA ? ng.hi.x + ng.lo.x : -Gf.x;
         const float rvB = flB ? ng.hi.y + ng.lo.y : -Gf.y;
+        if (coef) {
+            // the background's bilinear coefficients for the inner sweeps, from the second and
+            // cross differences just formed (their high parts: BF16 needs no more)
+            const size_t cells = plane * (size_t)n;
+            const float2 cX = p_mul(p_splat(2.f), p_add(Y.hi, Z.hi)), cY = p_mul(p_splat(2.f), p_add(X.hi, Z.hi));
+            const float2 cZ = p_mul(p_splat(2.f), p_add(X.hi, Y.hi));
+            const float2 cxy = p_mul(p_splat(-0.25f), exy.hi), cxz = p_mul(p_splat(-0.25f), exz.hi),
+                         cyz = p_mul(p_splat(-0.25f), eyz.hi);
+            coef[os + gA] = pack_bf16x2(cX.x, cY.x);
+            coef[os + gB] = pack_bf16x2(cX.y, cY.y);
+            coef[cells + os + gA] = pack_bf16x2(cZ.x, cxy.x);
+            coef[cells + os + gB] = pack_bf16x2(cZ.y, cxy.y);
+            coef[2 * cells + os + gA] = pack_bf16x2(cxz.x, cyz.x);
+            coef[2 * cells + os + gB] = pack_bf16x2(cxz.y, cyz.y);
+        }
         rplain[os + gA] = -Gf.x;
         rplain[os + gB] = -Gf.y;
         chi32[os + gA] = c0.hi.x;

@@ -16,22 +16,24 @@ constexpr int kRzTX = 64, kRzTY = 8;
 constexpr int kRzW = kRzTX + 2, kRzH = kRzTY + 2, kRzP = kRzW * kRzH;  // plane region with halo
 constexpr int kRzSlots = 4;  // planes s-1 .. s+1 in use, s+2 arriving
 
-template <bool BG>
+template <bool BG, bool COEF = false>
 constexpr size_t resid_zm_smem_bytes()
 {
-    return sizeof(float) * (size_t)kRzSlots * kRzP * (BG ? 2 : 1);
+    return sizeof(float) * (size_t)kRzSlots * kRzP * ((BG && !COEF) ? 2 : 1);
 }
 
 // Grid (n/64, n/8, n/NZ), 256 threads; the block count must not exceed kMaxPartials.
-template <bool BG>
+// COEF: the background enters through its per-cell coefficients (BgCoef), not its planes.
+template <bool BG, bool COEF = false>
 __global__ void __launch_bounds__(256) k_residual_zm(const float* __restrict__ u, const float* __restrict__ F,
                                                      float fscale, float lam, const uint8_t* __restrict__ kmask,
                                                      const float* __restrict__ bg, const float* __restrict__ gap, int n,
                                                      int NZ, float ih2, float nu, float kap, float Df, float lsat_c,
                                                      bool floor_piece, float* __restrict__ r,
                                                      uint8_t* __restrict__ sat, double* __restrict__ partials,
-                                                     const float* __restrict__ lamp)
+                                                     const float* __restrict__ lamp, const uint32_t* __restrict__ coef)
 {
+    constexpr bool BGRING = BG && !COEF;
     if (lamp) lam += *lamp;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* su = reinterpret_cast<float*>(smem_raw);  // [slots][H][W]
@@ -60,7 +62,7 @@ __global__ void __launch_bounds__(256) k_residual_zm(const float* __restrict__ u
             if (off[k] < 0) continue;
             const unsigned d = 4u * (unsigned)(so + t + 256 * k);
             cp_async4(su_s + d, Up + off[k]);
-            if (BG) cp_async4(sb_s + d, Bp + off[k]);
+            if (BGRING) cp_async4(sb_s + d, Bp + off[k]);
         }
         cp_async_commit_group();
     };
@@ -86,12 +88,19 @@ __global__ void __launch_bounds__(256) k_residual_zm(const float* __restrict__ u
     for (int s = z0; s < z0 + NZ; ++s) {
         const size_t os = (size_t)s * plane;  // s is inside [0, n)
         float fv[2], gv[2];
+        uint32_t cw[2][3];
         float wk[2];  // screening weights
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             fv[h] = F[os + gxy[h]];
             gv[h] = gap ? gap[os + gxy[h]] : 0.f;
             wk[h] = screen_w<float>(kmask, os + gxy[h]);
+            if (COEF) {
+                const size_t cells = plane * (size_t)n;
+                cw[h][0] = coef[os + gxy[h]];
+                cw[h][1] = coef[cells + os + gxy[h]];
+                cw[h][2] = coef[2 * cells + os + gxy[h]];
+            }
         }
         cp_async_wait_all();  // planes up to s+1
         __syncthreads();
@@ -105,11 +114,17 @@ __global__ void __launch_bounds__(256) k_residual_zm(const float* __restrict__ u
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             Stencil<float> a = stencil(up, uc, un, cs[h]);
-            Stencil<float> b;
-            if (BG) b = stencil(bp, bc, bn, cs[h]);
             const float kc = kap * wk[h];
             const float lsat = kc != 0.f ? lsat_c / wk[h] : 0.f;
-            Local<float> o = local_eval<float, BG>(a, b, ih2, nu, kc, fscale * fv[h] + lam, lsat, gap != nullptr, gv[h]);
+            Local<float> o;
+            if (COEF) {
+                o = local_eval_cf(a, unpack_bg_coef(cw[h][0], cw[h][1], cw[h][2]), ih2, nu, kc, fscale * fv[h] + lam,
+                                  lsat, gv[h]);
+            } else {
+                Stencil<float> b;
+                if (BG) b = stencil(bp, bc, bn, cs[h]);
+                o = local_eval<float, BG>(a, b, ih2, nu, kc, fscale * fv[h] + lam, lsat, gap != nullptr, gv[h]);
+            }
             // the floored piece exists on the finest level only (see k_residual)
             const bool fl = floor_piece && (o.P != 0.f) && (o.D < Df);
             const float rv = fl ? nu * o.g : -o.G;

@@ -34,11 +34,11 @@ struct PairGeom {
     static constexpr int NBU = (BLK_UNITS + NW - 1) / NW;
 };
 
-template <int TY, bool BG>
+template <int TY, bool BG, bool COEF = false>
 constexpr size_t pair_smem_bytes()
 {
     using G = PairGeom<TY>;
-    return sizeof(float) * ((size_t)G::NS * G::PU * (BG ? 2 : 1) + (size_t)3 * G::PR);
+    return sizeof(float) * ((size_t)G::NS * G::PU * ((BG && !COEF) ? 2 : 1) + (size_t)3 * G::PR);
 }
 
 __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -107,6 +107,43 @@ __device__ __forceinline__ Local2 local_eval2(const Stencil2& s, const Stencil2&
     return o;
 }
 
+// local_eval2<BG = true, GAP = true> with the background given by its coefficients (BgCoef
+// of both cells, internal.cuh)
+__device__ __forceinline__ Local2 local_eval2_cf(const Stencil2& s, const BgCoef& ca, const BgCoef& cb, float ih2,
+                                                 float nu, float2 kap, float2 rhs, float2 lsat_c, float2 gapx)
+{
+    const float2 m2 = f2(-2.f);
+    const float2 X = f2fma(m2, s.c0, s.ax);
+    const float2 Y = f2fma(m2, s.c0, s.ay);
+    const float2 Z = f2fma(m2, s.c0, s.az);
+    const float2 L1 = f2add(f2add(X, Y), Z);
+    float2 pr = f2mul(X, Y);
+    pr = f2fma(Y, Z, pr);
+    pr = f2fma(Z, X, pr);
+    float2 sq = f2mul(s.exy, s.exy);
+    sq = f2fma(s.exz, s.exz, sq);
+    sq = f2fma(s.eyz, s.eyz, sq);
+    float2 q2 = f2fma(f2(-0.125f), sq, f2mul(f2(2.f), pr));
+    q2 = f2fma(make_float2(ca.cX, cb.cX), X, q2);
+    q2 = f2fma(make_float2(ca.cY, cb.cY), Y, q2);
+    q2 = f2fma(make_float2(ca.cZ, cb.cZ), Z, q2);
+    q2 = f2fma(make_float2(ca.cxy, cb.cxy), s.exy, q2);
+    q2 = f2fma(make_float2(ca.cxz, cb.cxz), s.exz, q2);
+    q2 = f2fma(make_float2(ca.cyz, cb.cyz), s.eyz, q2);
+    Local2 o;
+    const float2 lsat = make_float2(kap.x != 0.f ? lsat_c.x : 0.f, kap.y != 0.f ? lsat_c.y : 0.f);
+    o.g = f2fma(f2(-ih2), L1, gapx);  // gap - L1/h^2
+    const float2 Ltot = f2sub(lsat, o.g);
+    o.g = make_float2(kap.x != 0.f ? o.g.x : 0.f, kap.y != 0.f ? o.g.y : 0.f);
+    const float2 kap1 = f2mul(kap, f2(ih2 * ih2));
+    const float2 N = f2fma(f2(-1.f), f2mul(kap1, q2), f2mul(f2(nu * ih2), L1));
+    o.G = f2sub(N, rhs);
+    o.Ep = f2mul(f2fma(f2(8.f), f2mul(kap, Ltot), f2(-6.f * nu)), f2(ih2));
+    o.P = f2mul(f2(-24.f), kap1);
+    o.D = f2fma(f2mul(f2(-4.f), o.P), o.G, f2mul(o.Ep, o.Ep));
+    return o;
+}
+
 // local_update_fast for one cell, without branches
 __device__ __forceinline__ float pick_update(float G, float Ep, float P, float D, float g, float sp, float Df,
                                              float h2over6, float inv2P)
@@ -120,21 +157,25 @@ __device__ __forceinline__ float pick_update(float G, float Ep, float P, float D
     return e;
 }
 
-template <int TY, bool BG, bool GAP>
+// COEF (with BG and GAP): the finest inner level, the background entering through its
+// per-cell coefficients (three packed BF16 planes) instead of a ring of its planes.
+template <int TY, bool BG, bool GAP, bool COEF = false>
 __global__ void __launch_bounds__(16 * TY, TY >= 16 ? 3 : 1) k_sweep_pair(const float* __restrict__ U, float* __restrict__ V,
                                                        const float* __restrict__ F, float fscale, float lam,
                                                        const uint8_t* __restrict__ kmask, const float* __restrict__ bg,
                                                        const float* __restrict__ gap, int n, int NZ, float ih2,
                                                        float nu, float kap, float sp, float Df, float lsat,
-                                                       const float* __restrict__ lamp)
+                                                       const float* __restrict__ lamp,
+                                                       const uint32_t* __restrict__ coef)
 {
     using G = PairGeom<TY>;
+    constexpr bool BGRING = BG && !COEF;
     constexpr int NS = G::NS, NT = G::NT, NW = G::NW, WU = G::WU, WR = G::WR;
     if (lamp) lam += *lamp;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* su = reinterpret_cast<float*>(smem_raw);  // [NS][HU][WU] old values
     float* sb = su + NS * G::PU;                      // [NS][HU][WU] background (BG)
-    float* sr = sb + (BG ? NS * G::PU : 0);           // [3][HR][WR] new red values
+    float* sr = sb + (BGRING ? NS * G::PU : 0);       // [3][HR][WR] new red values
     const unsigned su_s = (unsigned)__cvta_generic_to_shared(su);
     const unsigned sb_s = (unsigned)__cvta_generic_to_shared(sb);
     const int m = n - 1;
@@ -161,7 +202,7 @@ __global__ void __launch_bounds__(16 * TY, TY >= 16 ? 3 : 1) k_sweep_pair(const 
             if (offu[k] < 0) continue;
             const unsigned d = 4u * (unsigned)(so + t + k * NT);
             cp_async4(su_s + d, Up + offu[k]);
-            if (BG) cp_async4(sb_s + d, Bp + offu[k]);
+            if (BGRING) cp_async4(sb_s + d, Bp + offu[k]);
         }
         cp_async_commit_group();
     };
@@ -243,7 +284,9 @@ __global__ void __launch_bounds__(16 * TY, TY >= 16 ? 3 : 1) k_sweep_pair(const 
         // this step's right-hand side, gap and mask values, before the barrier
         float2 rF[G::NRU], rG[G::NRU], bF[G::NBU], bG[G::NBU];
         float2 rW[G::NRU], bW[G::NBU];  // screening weights (1 without a mask)
+        uint2 rC[G::NRU][3], bC[G::NBU][3];  // background coefficients (COEF): .x cell A, .y cell B
         {
+            const size_t cells = plane * (size_t)n;
             const size_t os = (size_t)(s & m) * plane, ob = (size_t)(pb & m) * plane;
 #pragma unroll
             for (int it = 0; it < G::NRU; ++it) {
@@ -256,6 +299,10 @@ __global__ void __launch_bounds__(16 * TY, TY >= 16 ? 3 : 1) k_sweep_pair(const 
                     if (GAP) rG[it] = make_float2(gap[ga], gap[gb]);
                     if (kmask) {
                         rW[it] = make_float2(screen_w<float>(kmask, ga), screen_w<float>(kmask, gb));
+                    }
+                    if (COEF) {
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) rC[it][q] = make_uint2(coef[q * cells + ga], coef[q * cells + gb]);
                     }
                 }
             }
@@ -270,6 +317,11 @@ __global__ void __launch_bounds__(16 * TY, TY >= 16 ? 3 : 1) k_sweep_pair(const 
                     if (GAP) bG[it] = make_float2(gap[ga], gap[ga + 32]);
                     if (kmask) {
                         bW[it] = make_float2(screen_w<float>(kmask, ga), screen_w<float>(kmask, ga + 32));
+                    }
+                    if (COEF) {
+#pragma unroll
+                        for (int q = 0; q < 3; ++q)
+                            bC[it][q] = make_uint2(coef[q * cells + ga], coef[q * cells + ga + 32]);
                     }
                 }
             }
@@ -292,14 +344,21 @@ __global__ void __launch_bounds__(16 * TY, TY >= 16 ? 3 : 1) k_sweep_pair(const 
                 const int pa = (r_rowA[it] + s) & 1, pbb = (r_rowB[it] + s) & 1;
                 const int ca = r_cuA[it] + pa, cb = r_cuB[it] + pbb;
                 const Stencil2 a = stencil2(up, uc, un, ca, cb);
-                Stencil2 b;
-                if (BG) b = stencil2(bp, bc, bn, ca, cb);
                 const float2 kc = f2mul(f2(kap), rW[it]);
                 const float2 iw = kmask ? make_float2(rW[it].x > 0.f ? 1.f / rW[it].x : 1.f,
                                                       rW[it].y > 0.f ? 1.f / rW[it].y : 1.f)
                                         : f2(1.f);
-                const Local2 o = local_eval2<BG, GAP>(a, b, ih2, nu, kc, f2fma(f2(fscale), rF[it], f2(lam)),
-                                                      f2mul(f2(lsat), iw), rG[it]);
+                Local2 o;
+                if (COEF) {
+                    o = local_eval2_cf(a, unpack_bg_coef(rC[it][0].x, rC[it][1].x, rC[it][2].x),
+                                       unpack_bg_coef(rC[it][0].y, rC[it][1].y, rC[it][2].y), ih2, nu, kc,
+                                       f2fma(f2(fscale), rF[it], f2(lam)), f2mul(f2(lsat), iw), rG[it]);
+                } else {
+                    Stencil2 b;
+                    if (BG) b = stencil2(bp, bc, bn, ca, cb);
+                    o = local_eval2<BG, GAP>(a, b, ih2, nu, kc, f2fma(f2(fscale), rF[it], f2(lam)),
+                                             f2mul(f2(lsat), iw), rG[it]);
+                }
                 const float2 e = update2(o, kc, iw);
                 rc[r_crA[it] + pa] = a.c0.x + e.x;
                 rc[r_crB[it] + pbb] = a.c0.y + e.y;
@@ -338,14 +397,21 @@ __global__ void __launch_bounds__(16 * TY, TY >= 16 ? 3 : 1) k_sweep_pair(const 
                               f2sub(make_float2(un[ca - 1], un[cb - 1]), make_float2(up[ca - 1], up[cb - 1])));
                 a.eyz = f2sub(f2sub(make_float2(un[ca + WU], un[cb + WU]), make_float2(up[ca + WU], up[cb + WU])),
                               f2sub(make_float2(un[ca - WU], un[cb - WU]), make_float2(up[ca - WU], up[cb - WU])));
-                Stencil2 b;
-                if (BG) b = stencil2(bp, bc, bn, ca, cb);
                 const float2 kc = f2mul(f2(kap), bW[it]);
                 const float2 iw = kmask ? make_float2(bW[it].x > 0.f ? 1.f / bW[it].x : 1.f,
                                                       bW[it].y > 0.f ? 1.f / bW[it].y : 1.f)
                                         : f2(1.f);
-                const Local2 o = local_eval2<BG, GAP>(a, b, ih2, nu, kc, f2fma(f2(fscale), bF[it], f2(lam)),
-                                                      f2mul(f2(lsat), iw), bG[it]);
+                Local2 o;
+                if (COEF) {
+                    o = local_eval2_cf(a, unpack_bg_coef(bC[it][0].x, bC[it][1].x, bC[it][2].x),
+                                       unpack_bg_coef(bC[it][0].y, bC[it][1].y, bC[it][2].y), ih2, nu, kc,
+                                       f2fma(f2(fscale), bF[it], f2(lam)), f2mul(f2(lsat), iw), bG[it]);
+                } else {
+                    Stencil2 b;
+                    if (BG) b = stencil2(bp, bc, bn, ca, cb);
+                    o = local_eval2<BG, GAP>(a, b, ih2, nu, kc, f2fma(f2(fscale), bF[it], f2(lam)),
+                                             f2mul(f2(lsat), iw), bG[it]);
+                }
                 const float2 e = update2(o, kc, iw);
                 const float vba = a.c0.x + e.x, vbb = a.c0.y + e.y;
                 const int rr = (y + 1) * WR + xrd + 1;
