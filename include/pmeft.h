@@ -48,7 +48,7 @@ typedef struct {
     int coarse_sweeps;     /* sweeps of the coarsest-level solve (8) */
     int precision;         /* 0: FP64 FAS cycle; 1: FP32 inner cycle inside an FP64 defect-correction loop */
     int include_dot_alphaB;/* 1: keep alpha_B-dot/H = d alpha_B/d ln a in C2 (Sec. 2.2) */
-    int inner_cycles;      /* precision 1: FP32 V-cycles on the correction per FP64 outer residual (2) */
+    int inner_cycles;      /* precision 1: FP32 V-cycles on the correction per FP64 outer residual (1) */
     int autotune;          /* 1: time the tile variants of the FP32 sweep on first use of each size (1) */
     int linear_eft;        /* 1: pm_step / pm_run use the linearised equations (Sec. 2.5, Eq. linearised):
                               chi = (xi/nu) Psi_N from the one FFT Poisson solve, no screening and no

@@ -176,7 +176,7 @@ extern "C" void pm_default_params(pm_params* p)
     p->coarse_sweeps = 8;
     p->precision = 0;
     p->include_dot_alphaB = 1;
-    p->inner_cycles = 2;
+    p->inner_cycles = 1;
     p->autotune = 1;
     p->linear_eft = 0;
 }

@@ -286,7 +286,7 @@ def test_every_fused_tile_variant_equals_half_sweeps(gpu_lib, variant, mode):
     assert np.sqrt(np.mean((a - b) ** 2)) <= 1e-6 * np.sqrt(np.mean(a ** 2))
 
 
-@pytest.mark.parametrize("inner", [1, 3])
+@pytest.mark.parametrize("inner", [1, 2, 3])
 def test_mixed_precision_solve_256_uses_fused_sweep(gpu_lib, inner):
     """At 256^3 the inner cycle runs the fused sweep on its finest level; the mixed solve
     reaches 1e-8 and agrees with the FP64 GPU solve (itself pinned to the oracle) to 1e-6."""
