@@ -115,6 +115,7 @@ pm_status ensure_mg(pm_ctx* ctx, Workspace* w, bool want_fp32)
         for (int l = 0; l < nlev; ++l) PM_TRY(alloc_level(ctx, w->s[l], n >> l, l > 0, true));
         // the inner level 0 keeps its right-hand side in rplain; give it the f slot too
         PM_CUDA(cudaMalloc(&w->rplain, w->s[0].cells * sizeof(float)));
+        PM_CUDA(cudaMalloc(&w->ff_alt, w->s[0].cells * sizeof(float2)));
         PM_CUDA(cudaMalloc(&w->s[0].gap, w->s[0].cells * sizeof(float)));
         if (n >= kCoefMinN) PM_CUDA(cudaMalloc(&w->s[0].coef, 3 * w->s[0].cells * sizeof(uint32_t)));
     }
@@ -144,6 +145,7 @@ void delete_workspace(Workspace* w)
     for (auto& L : w->d) free_level(L);
     for (auto& L : w->s) free_level(L);
     cudaFree(w->rplain);
+    cudaFree(w->ff_alt);
     cudaFree(w->psi);
     cudaFree(w->delta);
     cudaFree(w->acc);

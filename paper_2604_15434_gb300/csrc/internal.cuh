@@ -110,6 +110,8 @@ struct Workspace {
     std::vector<Level<double>> d;  // FP64 hierarchy
     std::vector<Level<float>> s;   // FP32 hierarchy (mixed precision inner cycle)
     float* rplain = nullptr;       // FP32 inner right-hand side f + lambda - N(chi) at level 0
+    float2* ff_alt = nullptr;      // second float-float iterate buffer (the residual writes the corrected
+                                   // iterate out of place)
     double* psi = nullptr;         // scratch n^3 (Poisson output / total potential)
     double* delta = nullptr;       // scratch n^3 (pm_step)
     long long* acc = nullptr;      // int64 fixed-point deposit grid

@@ -772,9 +772,11 @@ static pm_status source_norm(Exec* ctx, const double* delta, size_t cells, doubl
     return PM_OK;
 }
 
-// float-float outer residual of the mixed path (outer_ff.cuh); sums into red_out[0..8]
+// float-float outer residual of the mixed path (outer_ff.cuh); sums into red_out[0..8].
+// With a pending correction e (n >= kFzTX only; <e> already summed into red_out[16]) the
+// residual is that of xff + e - <e>, and that corrected iterate is written to xout.
 static void residual_ff(Exec* ctx, Workspace* w, const float2* xff, const float2* fff, double lam,
-                        const double* lamp, const FFCoef& fk)
+                        const double* lamp, const FFCoef& fk, const float* e = nullptr, float2* xout = nullptr)
 {
     const int n = w->n;
     const size_t cells = (size_t)n * n * n;
@@ -786,8 +788,14 @@ static void residual_ff(Exec* ctx, Workspace* w, const float2* xff, const float2
         while ((size_t)(n / kFzTX) * (n / kFzTY) * (n / nz) > (size_t)kMaxPartials) nz *= 2;
         const dim3 g3(n / kFzTX, n / kFzTY, n / nz);
         grid = (int)(g3.x * g3.y * g3.z);
-        k_residual_ff_zm<<<g3, 256, kFzSmem, ctx->stream>>>(xff, fff, lam, lamp, n, nz, fk, w->rplain, w->s[0].bg,
-                                                            w->s[0].gap, w->s[0].coef, ctx->red_partials);
+        if (e)
+            k_residual_ff_zm<true><<<g3, 256, kFzSmemCorr, ctx->stream>>>(
+                xff, fff, lam, lamp, n, nz, fk, w->rplain, w->s[0].bg, w->s[0].gap, w->s[0].coef,
+                ctx->red_partials, e, ctx->red_out + 16, xout);
+        else
+            k_residual_ff_zm<false><<<g3, 256, kFzSmem, ctx->stream>>>(
+                xff, fff, lam, lamp, n, nz, fk, w->rplain, w->s[0].bg, w->s[0].gap, w->s[0].coef,
+                ctx->red_partials, nullptr, nullptr, nullptr);
     } else {
         k_residual_ff<<<grid, kThreads, 0, ctx->stream>>>(xff, fff, lam, lamp, n, fk, w->rplain, w->s[0].bg,
                                                           w->s[0].gap, ctx->red_partials);
@@ -798,8 +806,8 @@ static void residual_ff(Exec* ctx, Workspace* w, const float2* xff, const float2
     ctx->end();
 }
 
-// chi += e - <e> on the float-float iterate
-static void add_correction_ff(Exec* ctx, float2* xff, const float* e, size_t cells)
+// sum of the correction e into red_out[16]
+static void correction_sum(Exec* ctx, const float* e, size_t cells)
 {
     int grid = grid_for(ctx, cells);
     if (grid > kMaxPartials) grid = kMaxPartials;
@@ -809,6 +817,12 @@ static void add_correction_ff(Exec* ctx, float2* xff, const float* e, size_t cel
     ctx->begin(PM_K_REDUCE, false, 0);
     k_finalize<<<1, 256, 0, ctx->stream>>>(ctx->red_partials, grid, ctx->red_out + 16);
     ctx->end();
+}
+
+// chi += e - <e> on the float-float iterate
+static void add_correction_ff(Exec* ctx, float2* xff, const float* e, size_t cells)
+{
+    correction_sum(ctx, e, cells);
     ctx->begin(PM_K_REDUCE, false, 0);
     k_add_correction_ff<<<grid_for(ctx, cells), kThreads, 0, ctx->stream>>>(xff, e, cells, ctx->red_out + 16);
     ctx->end();
@@ -878,10 +892,17 @@ pm_status mg_solve(pm_ctx* pctx, const double* delta, int n, const pm_coeffs& cf
     double lam = 0.0, rr = 0.0;
     int cyc = 0, vcyc = 0;
     pm_status st = PM_ERR_NOCONV;
+    // mixed: the iterate lives in xff or w->ff_alt; the correction of an outer iteration is
+    // applied by the next residual launch (pend), which writes the corrected iterate to the
+    // other buffer
+    const float* pend = nullptr;
     for (;;) {
-        if (mixed)
-            residual_ff(ctx, w, xff, fff, lam, nullptr, fk);
-        else
+        if (mixed) {
+            float2* xo = xff == ff_chi(w) ? w->ff_alt : ff_chi(w);
+            residual_ff(ctx, w, xff, fff, lam, nullptr, fk, pend, pend ? xo : nullptr);
+            if (pend) xff = xo;
+            pend = nullptr;
+        } else
             residual<double, false, false>(ctx, L0, L0.u[L0.cur], delta, cf.src, lam, c, nullptr, nullptr);
         PM_TRY(read_sums(ctx, 9));
         const double* h = ctx->host_out;
@@ -947,7 +968,12 @@ pm_status mg_solve(pm_ctx* pctx, const double* delta, int n, const pm_coeffs& cf
                 vcycle<float>(ctx, s, 0, w->rplain, 1.0f, (float)(-gm), c);
                 ++vcyc;
             }
-            add_correction_ff(ctx, xff, s[0].u[s[0].cur], cells);
+            if (n >= kFzTX) {
+                correction_sum(ctx, s[0].u[s[0].cur], cells);
+                pend = s[0].u[s[0].cur];
+            } else {
+                add_correction_ff(ctx, xff, s[0].u[s[0].cur], cells);
+            }
         } else {
             vcycle<double>(ctx, w->d, 0, delta, cf.src, lam, c);
             ++vcyc;

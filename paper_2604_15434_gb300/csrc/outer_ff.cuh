@@ -265,17 +265,26 @@ __device__ __forceinline__ ff2 ff2_splat(ff a) { return ff2{p_splat(a.hi), p_spl
 constexpr int kFzTX = 64, kFzTY = 8;
 constexpr int kFzW = kFzTX + 2, kFzP = kFzW * (kFzTY + 2);  // plane region with a 1-cell halo
 constexpr size_t kFzSmem = sizeof(float) * 2 * 4 * kFzP;       // hi and lo, 4 ring slots
+constexpr size_t kFzSmemCorr = sizeof(float) * 3 * 4 * kFzP;   // + the pending correction e
 
 // The float-float residual of k_residual_ff, z-marching: a block owns a 64 x 8 (x, y) tile
 // and NZ planes; the hi and lo parts of the iterate's planes (tile + 1 halo) arrive in
 // shared memory by asynchronous copies one plane ahead; each thread evaluates cells
 // (x, y) and (x, y + 4) of its plane together.  Grid (n/64, n/8, n/NZ), at most
 // kMaxPartials blocks.
+//
+// CORR: the iterate is U + (E - <E>), the pending correction of the previous outer iteration
+// (esum[0] = sum of E), applied to every plane as it arrives in shared memory; the corrected
+// iterate is written to Uout (never U: other blocks still read U as their halo), which
+// replaces a separate pass chi += e - <e> over the float-float iterate.
+template <bool CORR>
 __global__ void __launch_bounds__(256) k_residual_ff_zm(const float2* __restrict__ U, const float2* __restrict__ F,
                                                         double lam_host, const double* __restrict__ lamp, int n,
                                                         int NZ, FFCoef k, float* __restrict__ rplain,
                                                         float* __restrict__ chi32, float* __restrict__ gap32,
-                                                        uint32_t* __restrict__ coef, double* __restrict__ partials)
+                                                        uint32_t* __restrict__ coef, double* __restrict__ partials,
+                                                        const float* __restrict__ E, const double* __restrict__ esum,
+                                                        float2* __restrict__ Uout)
 {
     const ff lam1 = ff_from_double(lam_host + (lamp ? *lamp : 0.0));
     const ff2 lam = ff2_splat(lam1);
@@ -285,8 +294,16 @@ __global__ void __launch_bounds__(256) k_residual_ff_zm(const float2* __restrict
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* sh = reinterpret_cast<float*>(smem_raw);  // [4][H][W] hi parts
     float* sl = sh + 4 * kFzP;                        // [4][H][W] lo parts
+    float* se = sl + 4 * kFzP;                        // [4][H][W] correction (CORR)
     const unsigned sh_s = (unsigned)__cvta_generic_to_shared(sh);
     const unsigned sl_s = (unsigned)__cvta_generic_to_shared(sl);
+    const unsigned se_s = (unsigned)__cvta_generic_to_shared(se);
+    float mhi = 0.f, mlo = 0.f;  // <E> as a float-float pair
+    if (CORR) {
+        const double mean = esum[0] / ((double)n * n * n);
+        mhi = (float)mean;
+        mlo = (float)(mean - (double)mhi);
+    }
     const int m = n - 1;
     const int x0 = blockIdx.x * kFzTX, y0 = blockIdx.y * kFzTY, z0 = blockIdx.z * NZ;
     const int t = threadIdx.x;
@@ -309,8 +326,24 @@ __global__ void __launch_bounds__(256) k_residual_ff_zm(const float2* __restrict
             const unsigned d = 4u * (unsigned)(so + t + 256 * q);
             cp_async4(sh_s + d, Up + 2 * off[q]);
             cp_async4(sl_s + d, Up + 2 * off[q] + 1);
+            if (CORR) cp_async4(se_s + d, E + (size_t)(p & m) * plane + off[q]);
         }
         cp_async_commit_group();
+    };
+    // CORR: hi + lo += e - <e> on the ring slot of plane p (every element of the region)
+    auto correct = [&](int p) {
+        const int so = slot(p);
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            if (off[q] < 0) continue;
+            const int i = so + t + 256 * q;
+            float err;
+            const float s0 = ff_two_sum(se[i], -mhi, err);
+            const ff d = ff_norm(s0, __fsub_rn(err, mlo));
+            const ff r = ff_add(ff{sh[i], sl[i]}, d);
+            sh[i] = r.hi;
+            sl[i] = r.lo;
+        }
     };
     const int x = t & 63, yA = t >> 6;
     const int cA = (yA + 1) * kFzW + x + 1, cB = cA + 4 * kFzW;
@@ -329,6 +362,15 @@ __global__ void __launch_bounds__(256) k_residual_ff_zm(const float2* __restrict
         cp_async_wait_all();  // planes up to s+1
         __syncthreads();
         if (s + 2 <= z0 + NZ) issue(s + 2);  // its slot held plane s-2, no longer read
+        if (CORR) {
+            // each thread corrects the elements it copied itself, then all see the result
+            if (s == z0) {
+                correct(z0 - 1);
+                correct(z0);
+            }
+            correct(s + 1);
+            __syncthreads();
+        }
         const int bp = slot(s - 1), bc = slot(s), bn = slot(s + 1);
         constexpr int W = kFzW;
         const ff2 c0 = ld(bc, 0);
@@ -370,6 +412,10 @@ __global__ void __launch_bounds__(256) k_residual_ff_zm(const float2* __restrict
             coef[cells + os + gB] = pack_bf16x2(cZ.y, cxy.y);
             coef[2 * cells + os + gA] = pack_bf16x2(cxz.x, cyz.x);
             coef[2 * cells + os + gB] = pack_bf16x2(cxz.y, cyz.y);
+        }
+        if (CORR) {
+            Uout[os + gA] = make_float2(c0.hi.x, c0.lo.x);
+            Uout[os + gB] = make_float2(c0.hi.y, c0.lo.y);
         }
         rplain[os + gA] = -Gf.x;
         rplain[os + gB] = -Gf.y;
