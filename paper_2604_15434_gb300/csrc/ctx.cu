@@ -118,6 +118,12 @@ pm_status ensure_mg(pm_ctx* ctx, Workspace* w, bool want_fp32)
         PM_CUDA(cudaMalloc(&w->ff_alt, w->s[0].cells * sizeof(float2)));
         PM_CUDA(cudaMalloc(&w->s[0].gap, w->s[0].cells * sizeof(float)));
         if (n >= kCoefMinN) PM_CUDA(cudaMalloc(&w->s[0].coef, 3 * w->s[0].cells * sizeof(uint32_t)));
+        // the first coarse inner level, when large enough, also sweeps through coefficients
+        // (written by the FAS right-hand side kernel, with its floored gap)
+        if (nlev > 1 && (n >> 1) >= kCoefMinN) {
+            PM_CUDA(cudaMalloc(&w->s[1].coef, 3 * w->s[1].cells * sizeof(uint32_t)));
+            PM_CUDA(cudaMalloc(&w->s[1].gap, w->s[1].cells * sizeof(float)));
+        }
     }
     return PM_OK;
 }

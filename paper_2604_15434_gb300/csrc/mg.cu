@@ -205,10 +205,14 @@ __global__ void k_restrict(const T* __restrict__ uf, int nc, T* __restrict__ uc)
 }
 
 // FAS right-hand side f_H = N_H(R u) + R r (no gauge term on coarse levels).
+// coefo / gapo (BG, FP32 levels of at least kCoefMinN): also the level's background
+// coefficients (the layout the finest level's float-float residual writes) and its floored
+// gap L_sat/w - L(background), w the cell's screening weight, for the coefficient sweep.
 template <typename T, bool BG>
 __global__ void __launch_bounds__(256) k_fas_rhs(const T* __restrict__ uc, const T* __restrict__ rc,
                                                  const uint8_t* __restrict__ kmask, const T* __restrict__ bg, int n,
-                                                 T ih2, T nu, T kap, T* __restrict__ fc)
+                                                 T ih2, T nu, T kap, T* __restrict__ fc, uint32_t* __restrict__ coefo,
+                                                 float* __restrict__ gapo, float lsat)
 {
     const size_t total = (size_t)n * n * n;
     const int lg = __ffs(n) - 1;
@@ -219,9 +223,18 @@ __global__ void __launch_bounds__(256) k_fas_rhs(const T* __restrict__ uc, const
         Stencil<T> s = load_stencil(uc, uc, i, j, k, n);
         Stencil<T> b;
         if (BG) b = load_stencil(bg, bg, i, j, k, n);
-        const T kc = kap * screen_w<T>(kmask, c);
+        const T w = screen_w<T>(kmask, c);
+        const T kc = kap * w;
         Local<T> o = local_eval<T, BG>(s, b, ih2, nu, kc, T(0), T(0));
         fc[c] = o.G + rc[c];
+        if (BG && coefo) {
+            const float Xb = (float)(b.ax - T(2) * b.c0), Yb = (float)(b.ay - T(2) * b.c0),
+                        Zb = (float)(b.az - T(2) * b.c0);
+            coefo[c] = pack_bf16x2(2.f * (Yb + Zb), 2.f * (Xb + Zb));
+            coefo[total + c] = pack_bf16x2(2.f * (Xb + Yb), -0.25f * (float)b.exy);
+            coefo[2 * total + c] = pack_bf16x2(-0.25f * (float)b.exz, -0.25f * (float)b.eyz);
+            gapo[c] = kc != T(0) ? lsat / (float)w - (float)ih2 * (Xb + Yb + Zb) : 0.f;
+        }
     }
 }
 
@@ -710,13 +723,17 @@ static void vcycle(Exec* ctx, std::vector<Level<T>>& lv, int l, const T* F0, T f
     const T ih2c = (T)((double)C.n * (double)C.n);
     if (C.bg) {
         ctx->begin(PM_K_TRANSFER, false, 0);
+        // FP32 coarse levels with coefficients: the level's coefficients and gap as well
+        uint32_t* co = sizeof(T) == 4 ? C.coef : nullptr;
+        float* go = (sizeof(T) == 4 && co) ? reinterpret_cast<float*>(C.gap) : nullptr;
+        const float lsn = c.kap != 0.0 ? (float)(0.75 * c.nu * (1.0 - c.eta) / c.kap) : 0.f;  // L_sat
         k_fas_rhs<T, true><<<gc, kThreads, 0, ctx->stream>>>(C.u[0], C.r, C.kmask, C.bg, C.n, ih2c, (T)c.nu,
-                                                             (T)c.kap, C.f);
+                                                             (T)c.kap, C.f, co, go, lsn);
         ctx->end();
     } else {
         ctx->begin(PM_K_TRANSFER, false, 0);
         k_fas_rhs<T, false><<<gc, kThreads, 0, ctx->stream>>>(C.u[0], C.r, C.kmask, nullptr, C.n, ih2c, (T)c.nu,
-                                                              (T)c.kap, C.f);
+                                                              (T)c.kap, C.f, nullptr, nullptr, 0.f);
         ctx->end();
     }
     vcycle(ctx, lv, l + 1, F0, fs0, lam0, c);
