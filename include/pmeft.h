@@ -263,6 +263,12 @@ typedef struct {
 
 /* Turn per-launch event tracing on (1) or off (0); resets the counters. */
 pm_status pm_trace_enable(pm_ctx* ctx, int on);
+/* Turn tracing on for a subset of launches only: classes whose bit (1 << PM_K_*) is set in
+ * class_mask, and with fine_only != 0 only the launches on the finest level of their call.
+ * The other launches are still counted in `launches` but get no events, so timing a few
+ * kernels costs the stream almost nothing.  class_mask 0 turns tracing off.  Resets the
+ * counters.  PM_ERR_INVALID_ARG if ctx is null. */
+pm_status pm_trace_select(pm_ctx* ctx, unsigned class_mask, int fine_only);
 /* Synchronise the stream and return the counters accumulated since the last reset. */
 pm_status pm_trace_get(pm_ctx* ctx, pm_profile* out);
 pm_status pm_trace_reset(pm_ctx* ctx);

@@ -78,6 +78,7 @@ SIGNATURES = {
     "pm_mg_restrict": (_I, [_P, _P, _I, _P]),
     "pm_mg_prolong_add": (_I, [_P, _P, _I, _P]),
     "pm_trace_enable": (_I, [_P, _I]),
+    "pm_trace_select": (_I, [_P, ctypes.c_uint, _I]),
     "pm_trace_get": (_I, [_P, _P]),
     "pm_trace_reset": (_I, [_P]),
     "pm_probe_fma": (_I, [_P, _P, _P]),
@@ -177,6 +178,13 @@ class Context:
     def trace(self, on: bool = True):
         """Per-launch CUDA-event tracing of the library's kernels (see pm_trace_enable)."""
         self._check(load().pm_trace_enable(self._h, int(bool(on))))
+
+    def trace_select(self, classes, fine_only: bool = False):
+        """Trace only the launches of the given PM_K_* class indices (see pm_trace_select)."""
+        mask = 0
+        for c in classes:
+            mask |= 1 << int(c)
+        self._check(load().pm_trace_select(self._h, mask, int(bool(fine_only))))
 
     def trace_get(self) -> dict:
         p = Profile()

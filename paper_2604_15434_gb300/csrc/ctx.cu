@@ -290,6 +290,18 @@ extern "C" pm_status pm_trace_enable(pm_ctx* ctx, int on)
     if (!ctx) return PM_ERR_INVALID_ARG;
     pm_trace_reset(ctx);
     ctx->tracing = on != 0;
+    ctx->trace_mask = ~0u;
+    ctx->trace_fine_only = false;
+    return PM_OK;
+}
+
+extern "C" pm_status pm_trace_select(pm_ctx* ctx, unsigned class_mask, int fine_only)
+{
+    if (!ctx) return PM_ERR_INVALID_ARG;
+    pm_trace_reset(ctx);
+    ctx->tracing = class_mask != 0;
+    ctx->trace_mask = class_mask;
+    ctx->trace_fine_only = fine_only != 0;
     return PM_OK;
 }
 

@@ -147,6 +147,12 @@ struct pm_ctx {
     std::string tune_log;
     // tracing (pm_trace_*): event pairs per launch, summed per class on read-out
     bool tracing = false;
+    unsigned trace_mask = ~0u;  // classes traced while tracing is on
+    bool trace_fine_only = false;
+    bool traced(int cls, bool fine) const
+    {
+        return tracing && ((trace_mask >> cls) & 1u) && (fine || !trace_fine_only);
+    }
     pm_profile prof{};
     struct Rec {
         int cls;
@@ -178,7 +184,7 @@ struct pm_ctx {
             prof.fine_launches[cls] += 1;
             prof.cells[cls] += cells;
         }
-        if (!tracing) return;
+        if (!traced(cls, fine)) return;
         open_cls = cls;
         open_fine = fine;
         open_a = ev();
@@ -231,7 +237,7 @@ struct Exec {
             c->prof.fine_launches[cls] += 1;
             c->prof.cells[cls] += cells;
         }
-        if (!tracing()) return;
+        if (!trace_ok || !c->traced(cls, fine)) return;
         open_cls = cls;
         open_fine = fine;
         open_a = c->ev();

@@ -455,3 +455,28 @@ def test_linearised_pm_step_and_lensing_potential(gpu_lib, c1_particles):
     psiN = gpu_lib.poisson_solve(cu(want["delta"]), a, aM0, ctx=ctx)
     Phi = gpu_lib.lensing_potential(psiN, phi, aB0, aM0, a, ctx=ctx).cpu().numpy()
     assert rel(Phi, O.lensing_potential(want["psiN"], want["chi"], aB0, aM0, a)) < 1e-12
+
+
+def test_trace_select_times_only_the_selected_launches(gpu_lib):
+    """pm_trace_select: with the FP32 sweep class and fine_only, only the finest-level sweep
+    launches carry event time; every launch of every class is still counted."""
+    n = 64
+    d = cu(synth.lognormal_delta(n, -2.0, 1.5, 1003))
+    ctx = gpu_lib.Context(precision=1, max_cycles=100)
+    gpu_lib.scalar_mg_solve(d, -0.5, 0.0, 1.0, 1e-8, ctx=ctx)
+    ctx.trace(True)
+    gpu_lib.scalar_mg_solve(d, -0.5, 0.0, 1.0, 1e-8, ctx=ctx)
+    full = ctx.trace_get()
+    ctx.trace_select([gpu_lib.KERNEL_CLASSES.index("sweep32")], fine_only=True)
+    gpu_lib.scalar_mg_solve(d, -0.5, 0.0, 1.0, 1e-8, ctx=ctx)
+    sel = ctx.trace_get()
+    ctx.trace(False)
+    s = sel["sweep32"]
+    assert s["fine_launches"] > 0 and s["fine_ms"] > 0.0
+    assert s["ms"] == pytest.approx(s["fine_ms"])
+    assert s["launches"] > s["fine_launches"]  # the coarse-level sweeps ran, untimed
+    for k, v in sel.items():
+        assert v["launches"] == full[k]["launches"]
+        if k != "sweep32":
+            assert v["ms"] == 0.0 and v["fine_ms"] == 0.0
+    assert full["resid64"]["ms"] > 0.0
