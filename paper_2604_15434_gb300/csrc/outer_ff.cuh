@@ -260,6 +260,60 @@ __device__ __forceinline__ ff2 ff2_mul(ff2 a, ff2 b)
 }
 
 __device__ __forceinline__ ff2 ff2_scale2(ff2 a, float p2) { return ff2{p_mul(a.hi, p_splat(p2)), p_mul(a.lo, p_splat(p2))}; }
+__device__ __forceinline__ float2 p_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+// TwoSum on pairs: s + e == a + b exactly (6 instructions)
+__device__ __forceinline__ float2 two_sum2(float2 a, float2 b, float2& e)
+{
+    const float2 s = p_add(a, b);
+    const float2 bb = p_sub(s, a);
+    e = p_add(p_sub(a, p_sub(s, bb)), p_sub(b, bb));
+    return s;
+}
+
+// a * b = p + e for float-float a, b, unnormalised: TwoProd of the high parts plus the two
+// cross terms (4 instructions; error ~2^-47 of |a b|)
+__device__ __forceinline__ float2 uprod2(const ff2& a, const ff2& b, float2& e)
+{
+    const float2 p = p_mul(a.hi, b.hi);
+    e = p_fma(a.hi, b.hi, p_neg(p));
+    e = p_fma(a.hi, b.lo, e);
+    e = p_fma(a.lo, b.hi, e);
+    return p;
+}
+
+// (a + b) + m2h + m2l for float-float a, b and the pair (m2h, m2l) = -2 c: the second
+// difference, normalised once (19 instructions against 24 for two float-float additions)
+__device__ __forceinline__ ff2 second_diff2(const ff2& a, const ff2& b, float2 m2h, float2 m2l)
+{
+    float2 e1, e2;
+    const float2 s1 = two_sum2(a.hi, b.hi, e1);
+    const float2 t1 = p_add(p_add(a.lo, b.lo), e1);
+    const float2 s2 = two_sum2(s1, m2h, e2);
+    return ff2_norm(s2, p_add(p_add(t1, m2l), e2));
+}
+
+// (a - b) - (c - d), normalised once (27 instructions against 33)
+__device__ __forceinline__ ff2 cross_diff2(const ff2& a, const ff2& b, const ff2& c, const ff2& d)
+{
+    float2 e1, e2, e3;
+    const float2 s1 = two_sum2(a.hi, p_neg(b.hi), e1);
+    const float2 t1 = p_add(p_sub(a.lo, b.lo), e1);
+    const float2 s2 = two_sum2(c.hi, p_neg(d.hi), e2);
+    const float2 t2 = p_add(p_sub(c.lo, d.lo), e2);
+    const float2 s3 = two_sum2(s1, p_neg(s2), e3);
+    return ff2_norm(s3, p_add(p_sub(t1, t2), e3));
+}
+
+// p1 + p2 + p3 with tails e1..e3, unnormalised: the high parts by TwoSum, all tails in t
+__device__ __forceinline__ float2 sum3_2(float2 p1, float2 e1, float2 p2, float2 e2, float2 p3, float2 e3, float2& t)
+{
+    float2 f1, f2;
+    const float2 s1 = two_sum2(p1, p2, f1);
+    const float2 s2 = two_sum2(s1, p3, f2);
+    t = p_add(p_add(p_add(e1, e2), e3), p_add(f1, f2));
+    return s2;
+}
 __device__ __forceinline__ ff2 ff2_splat(ff a) { return ff2{p_splat(a.hi), p_splat(a.lo)}; }
 
 constexpr int kFzTX = 64, kFzTY = 8;
@@ -278,7 +332,7 @@ constexpr size_t kFzSmemCorr = sizeof(float) * 3 * 4 * kFzP;   // + the pending 
 // iterate is written to Uout (never U: other blocks still read U as their halo), which
 // replaces a separate pass chi += e - <e> over the float-float iterate.
 template <bool CORR>
-__global__ void __launch_bounds__(256) k_residual_ff_zm(const float2* __restrict__ U, const float2* __restrict__ F,
+__global__ void __launch_bounds__(256, 3) k_residual_ff_zm(const float2* __restrict__ U, const float2* __restrict__ F,
                                                         double lam_host, const double* __restrict__ lamp, int n,
                                                         int NZ, FFCoef k, float* __restrict__ rplain,
                                                         float* __restrict__ chi32, float* __restrict__ gap32,
@@ -373,31 +427,67 @@ __global__ void __launch_bounds__(256) k_residual_ff_zm(const float2* __restrict
         }
         const int bp = slot(s - 1), bc = slot(s), bn = slot(s + 1);
         constexpr int W = kFzW;
+        // Error-free transformations with the tails summed in FP32 and one normalisation per
+        // quantity; every step's error is ~2^-47 of the largest operand, as in ff2_add.
         const ff2 c0 = ld(bc, 0);
-        const ff2 m2c = ff2_scale2(c0, -2.f);
-        const ff2 X = ff2_add(ff2_add(ld(bc, 1), ld(bc, -1)), m2c);
-        const ff2 Y = ff2_add(ff2_add(ld(bc, W), ld(bc, -W)), m2c);
-        const ff2 Z = ff2_add(ff2_add(ld(bn, 0), ld(bp, 0)), m2c);
-        const ff2 exy = ff2_sub(ff2_sub(ld(bc, 1 + W), ld(bc, 1 - W)), ff2_sub(ld(bc, -1 + W), ld(bc, -1 - W)));
-        const ff2 exz = ff2_sub(ff2_sub(ld(bn, 1), ld(bp, 1)), ff2_sub(ld(bn, -1), ld(bp, -1)));
-        const ff2 eyz = ff2_sub(ff2_sub(ld(bn, W), ld(bp, W)), ff2_sub(ld(bn, -W), ld(bp, -W)));
-        const ff2 L1 = ff2_add(ff2_add(X, Y), Z);
-        const ff2 sq = ff2_add(ff2_add(ff2_mul(exy, exy), ff2_mul(exz, exz)), ff2_mul(eyz, eyz));
-        const ff2 pr = ff2_add(ff2_add(ff2_mul(X, Y), ff2_mul(Y, Z)), ff2_mul(Z, X));
-        const ff2 q2 = ff2_sub(ff2_scale2(pr, 2.f), ff2_scale2(sq, 0.125f));
-        const ff2 N = ff2_sub(ff2_mul(nu1, L1), ff2_mul(kap1, q2));
-        const ff2 rhs = ff2_add(ff2{make_float2(fA.x, fB.x), make_float2(fA.y, fB.y)}, lam);
-        const ff2 G = ff2_sub(N, rhs);
-        const ff2 L = ff2_scale2(L1, k.ih2);
-        const ff2 g = ff2_sub(lsat, L);
-        const float2 Lf = p_add(L.hi, L.lo), Gf = p_add(G.hi, G.lo), gf = p_add(g.hi, g.lo);
+        const float2 m2h = p_mul(p_splat(-2.f), c0.hi), m2l = p_mul(p_splat(-2.f), c0.lo);
+        const ff2 X = second_diff2(ld(bc, 1), ld(bc, -1), m2h, m2l);
+        const ff2 Y = second_diff2(ld(bc, W), ld(bc, -W), m2h, m2l);
+        const ff2 Z = second_diff2(ld(bn, 0), ld(bp, 0), m2h, m2l);
+        const ff2 exy = cross_diff2(ld(bc, 1 + W), ld(bc, 1 - W), ld(bc, -1 + W), ld(bc, -1 - W));
+        const ff2 exz = cross_diff2(ld(bn, 1), ld(bp, 1), ld(bn, -1), ld(bp, -1));
+        const ff2 eyz = cross_diff2(ld(bn, W), ld(bp, W), ld(bn, -W), ld(bp, -W));
+        ff2 L1;
+        {
+            float2 e1, e2;
+            const float2 s1 = two_sum2(X.hi, Y.hi, e1);
+            const float2 s2 = two_sum2(s1, Z.hi, e2);
+            L1 = ff2_norm(s2, p_add(p_add(p_add(X.lo, Y.lo), Z.lo), p_add(e1, e2)));
+        }
+        // q2 = 2 (XY + YZ + ZX) - (exy^2 + exz^2 + eyz^2) / 8
+        ff2 q2;
+        {
+            float2 e1, e2, e3, e4, e5, e6, prt, sqt, f;
+            const float2 p1 = uprod2(X, Y, e1), p2 = uprod2(Y, Z, e2), p3 = uprod2(Z, X, e3);
+            const float2 p4 = uprod2(exy, exy, e4), p5 = uprod2(exz, exz, e5), p6 = uprod2(eyz, eyz, e6);
+            const float2 prs = sum3_2(p1, e1, p2, e2, p3, e3, prt);
+            const float2 sqs = sum3_2(p4, e4, p5, e5, p6, e6, sqt);
+            const float2 qs = two_sum2(p_mul(p_splat(2.f), prs), p_mul(p_splat(-0.125f), sqs), f);
+            q2 = ff2_norm(qs, p_add(p_fma(p_splat(2.f), prt, p_mul(p_splat(-0.125f), sqt)), f));
+        }
+        // G = nu1 L1 - kap1 q2 - (f + lambda), one TwoSum chain; only its rounded value is used
+        float2 Gf;
+        {
+            float2 e1, e2, f1, f2, f3;
+            const float2 a1 = uprod2(nu1, L1, e1), a2 = uprod2(kap1, q2, e2);
+            const float2 fh = make_float2(fA.x, fB.x), fl = make_float2(fA.y, fB.y);
+            const float2 s1 = two_sum2(a1, p_neg(a2), f1);
+            const float2 s2 = two_sum2(s1, p_neg(fh), f2);
+            const float2 s3 = two_sum2(s2, p_neg(lam.hi), f3);
+            const float2 t = p_add(p_add(p_sub(p_sub(e1, e2), p_add(fl, lam.lo)), p_add(f1, f2)), f3);
+            Gf = p_add(s3, t);
+        }
+        // g = L_sat - L1/h^2 (1/h^2 a power of two) and nu g, the floored cells' residual
+        float2 gf, ngf;
+        {
+            float2 f;
+            const float2 ih2 = p_splat(k.ih2);
+            const float2 gs = two_sum2(lsat.hi, p_neg(p_mul(ih2, L1.hi)), f);
+            const float2 gt = p_add(p_sub(lsat.lo, p_mul(ih2, L1.lo)), f);
+            gf = p_add(gs, gt);
+            const float2 p = p_mul(nu.hi, gs);
+            float2 e = p_fma(nu.hi, gs, p_neg(p));
+            e = p_fma(nu.hi, gt, e);
+            e = p_fma(nu.lo, gs, e);
+            ngf = p_add(p, e);
+        }
+        const float2 Lf = p_mul(p_add(L1.hi, L1.lo), p_splat(k.ih2));
         const float2 Ep = p_mul(p_fma(p_splat(8.f * k.kap_f), Lf, p_splat(-6.f * k.nu_f)), p_splat(k.ih2));
         const float P4 = -96.f * k.kap_f * k.ih2 * k.ih2;  // 4 P
         const float2 D = p_fma(p_splat(-P4), Gf, p_mul(Ep, Ep));
         const bool flA = screened && D.x < k.Df, flB = screened && D.y < k.Df;
-        const ff2 ng = ff2_mul(nu, g);
-        const float rvA = flA ? ng.hi.x + ng.lo.x : -Gf.x;
-        const float rvB = flB ? ng.hi.y + ng.lo.y : -Gf.y;
+        const float rvA = flA ? ngf.x : -Gf.x;
+        const float rvB = flB ? ngf.y : -Gf.y;
         if (coef) {
             // the background's bilinear coefficients for the inner sweeps, from the second and
             // cross differences just formed (their high parts: BF16 needs no more)
