@@ -384,17 +384,29 @@ __global__ void __launch_bounds__(256, 3) k_residual_ff_zm(const float2* __restr
         }
         cp_async_commit_group();
     };
-    // CORR: hi + lo += e - <e> on the ring slot of plane p (every element of the region)
+    // CORR: hi + lo += e - <e> on the ring slot of plane p (every element of the region).
+    // (hi + e) - <e>_hi by two TwoSums, the tails in one sum, one normalisation; elements
+    // t and t + 256 of the region go through the paired instructions together.
+    static_assert(K == 3 && kFzP > 512 && kFzP <= 768, "three region elements per thread");
     auto correct = [&](int p) {
         const int so = slot(p);
-#pragma unroll
-        for (int q = 0; q < K; ++q) {
-            if (off[q] < 0) continue;
-            const int i = so + t + 256 * q;
-            float err;
-            const float s0 = ff_two_sum(se[i], -mhi, err);
-            const ff d = ff_norm(s0, __fsub_rn(err, mlo));
-            const ff r = ff_add(ff{sh[i], sl[i]}, d);
+        {
+            const int i0 = so + t, i1 = i0 + 256;
+            float2 t1, t2;
+            const float2 s1 = two_sum2(make_float2(sh[i0], sh[i1]), make_float2(se[i0], se[i1]), t1);
+            const float2 s2 = two_sum2(s1, p_splat(-mhi), t2);
+            const ff2 r = ff2_norm(s2, p_add(p_add(make_float2(sl[i0], sl[i1]), t1), p_sub(t2, p_splat(mlo))));
+            sh[i0] = r.hi.x;
+            sh[i1] = r.hi.y;
+            sl[i0] = r.lo.x;
+            sl[i1] = r.lo.y;
+        }
+        if (off[2] >= 0) {
+            const int i = so + t + 512;
+            float t1, t2;
+            const float s1 = ff_two_sum(sh[i], se[i], t1);
+            const float s2 = ff_two_sum(s1, -mhi, t2);
+            const ff r = ff_norm(s2, __fadd_rn(__fadd_rn(sl[i], t1), __fsub_rn(t2, mlo)));
             sh[i] = r.hi;
             sl[i] = r.lo;
         }
