@@ -372,7 +372,7 @@ def main():
         ach = bytes_launch / (avg_ms * 1e-3) / 1e9
         tuned = [l for l in ctx.tune_log().splitlines() if f"n={n} bg gap" in l]
         roof = {"kernel": "single-pass FP32 red-black sweep of the finest level (k_sweep_pair / k_sweep_fused, "
-                          "autotuned: " + (tuned[-1].split(": ", 1)[1] if tuned else "?") + ")", "bound": "hbm",
+                          "autotuned: " + (tuned[-1].split(": ", 1)[1].split(" (variants")[0] if tuned else "?") + ")", "bound": "hbm",
                 "achieved": ach, "peak": hbm,
                 "unit": "GB/s", "frac": ach / hbm, "traffic": SWEEP_DRAM_BYTES_PER_CELL * cells,
                 "traffic_source": "ncu capture of a 512^3 launch (profiles/k_sweep_pair_256.md)",

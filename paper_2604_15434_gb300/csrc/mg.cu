@@ -541,6 +541,7 @@ static int tuned_cfg(Exec* ctx, Level<float>& L, const float* F, float fscale, f
         while (best + 1 < kNumFusedCfgs && !kFusedCfgs[best].pair) ++best;
     if (ctx->prm.autotune) {
         float best_ms = 1e30f;
+        std::string trials;  // "variant:ms" of every candidate
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
@@ -562,9 +563,12 @@ static int tuned_cfg(Exec* ctx, Level<float>& L, const float* F, float fscale, f
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, e0, e1);
                 ms /= (float)launches;
-                if (rep == 1 && ms < best_ms) {
-                    best_ms = ms;
-                    best = cfg;
+                if (rep == 1) {
+                    trials += " " + std::to_string(cfg) + ":" + std::to_string(ms).substr(0, 6);
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best = cfg;
+                    }
                 }
             }
         }
@@ -575,7 +579,7 @@ static int tuned_cfg(Exec* ctx, Level<float>& L, const float* F, float fscale, f
                          (cf ? " coef" : "") +
                          ": tile " + std::to_string(kFusedCfgs[best].tx) + "x" + std::to_string(kFusedCfgs[best].ty) +
                          " nz " + std::to_string(kFusedCfgs[best].nz) + (kFusedCfgs[best].pair ? " pair" : " single") +
-                         " " + std::to_string(best_ms) + " ms\n";
+                         " " + std::to_string(best_ms) + " ms (variants tried, ms:" + trials + ")\n";
     }
     ctx->tuned[key] = best;
     return best;
