@@ -195,8 +195,9 @@ class Context:
         self._check(load().pm_trace_reset(self._h))
 
     def tune_log(self) -> str:
-        buf = ctypes.create_string_buffer(8192)
-        load().pm_tune_log(self._h, buf, 8192)
+        full = load().pm_tune_log(self._h, None, 0)
+        buf = ctypes.create_string_buffer(full + 1)
+        load().pm_tune_log(self._h, buf, full + 1)
         return buf.value.decode()
 
     def probe_fma(self):
