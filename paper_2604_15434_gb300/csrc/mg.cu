@@ -208,12 +208,16 @@ __global__ void k_restrict(const T* __restrict__ uf, int nc, T* __restrict__ uc)
 // coefo / gapo (BG, FP32 levels of at least kCoefMinN): also the level's background
 // coefficients (the layout the finest level's float-float residual writes) and its floored
 // gap L_sat/w - L(background), w the cell's screening weight, for the coefficient sweep.
+// gm_ptr (non-null after the restricting residual k_residual_zm<.., RESTRICT>): rc holds the
+// children's raw mean residual and the mask byte carries the unfloored children in its high
+// nibble; the gauge term -gm * (unfloored children)/8 is applied here and the nibble cleared.
 template <typename T, bool BG>
 __global__ void __launch_bounds__(256) k_fas_rhs(const T* __restrict__ uc, const T* __restrict__ rc,
-                                                 const uint8_t* __restrict__ kmask, const T* __restrict__ bg, int n,
+                                                 uint8_t* __restrict__ kmask, const T* __restrict__ bg, int n,
                                                  T ih2, T nu, T kap, T* __restrict__ fc, uint32_t* __restrict__ coefo,
-                                                 float* __restrict__ gapo, float lsat)
+                                                 float* __restrict__ gapo, float lsat, const double* __restrict__ gm_ptr)
 {
+    const T gm = gm_ptr ? (T)(*gm_ptr) : T(0);
     const size_t total = (size_t)n * n * n;
     const int lg = __ffs(n) - 1;
     for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x) {
@@ -223,10 +227,16 @@ __global__ void __launch_bounds__(256) k_fas_rhs(const T* __restrict__ uc, const
         Stencil<T> s = load_stencil(uc, uc, i, j, k, n);
         Stencil<T> b;
         if (BG) b = load_stencil(bg, bg, i, j, k, n);
+        T rcv = rc[c];
+        if (gm_ptr) {
+            const uint8_t kb = kmask[c];
+            rcv -= gm * (T)(kb >> 4) * T(0.125);
+            kmask[c] = kb & 15;
+        }
         const T w = screen_w<T>(kmask, c);
         const T kc = kap * w;
         Local<T> o = local_eval<T, BG>(s, b, ih2, nu, kc, T(0), T(0));
-        fc[c] = o.G + rc[c];
+        fc[c] = o.G + rcv;
         if (BG && coefo) {
             const float Xb = (float)(b.ax - T(2) * b.c0), Yb = (float)(b.ay - T(2) * b.c0),
                         Zb = (float)(b.az - T(2) * b.c0);
@@ -692,6 +702,47 @@ static int residual(Exec* ctx, Level<T>& L, const T* u, const T* F, T fscale, T 
     return grid;
 }
 
+// The residual of a large FP32 level with the FAS restriction to C folded in
+// (k_residual_zm<.., RESTRICT>): C.ur, C.u[0], C.r (raw) and C.kmask (packed) are written,
+// L.r and L.sat are not.  Returns false (nothing launched) where the z-marching kernel does
+// not apply.
+static bool residual_restrict_f32(Exec* ctx, Level<float>& L, Level<float>& C, const float* u, const float* F,
+                                  float fscale, float lam, const Coef& c)
+{
+    const int n = L.n;
+    if (n < kResidZmMinN || !C.kmask) return false;
+    int nz = 8;
+    while ((size_t)(n / kRzTX) * (n / kRzTY) * (n / nz) > (size_t)kMaxPartials) nz *= 2;
+    const dim3 g3(n / kRzTX, n / kRzTY, n / nz);
+    const int nb = (int)(g3.x * g3.y * g3.z);
+    const float h2inv = (float)((double)n * (double)n);
+    const double sqDf = c.eta * 6.0 * std::fabs(c.nu) * (double)n * (double)n;
+    const float lsn = c.kap != 0.0 ? (float)(0.75 * c.nu * (1.0 - c.eta) / c.kap) : 0.f;  // L_sat
+    ctx->begin(PM_K_RESID32, L.fine, (long long)L.cells);
+    if (L.coef && L.gap) {
+        constexpr size_t sm = resid_zm_smem_bytes<true, true>();
+        k_residual_zm<true, true, true><<<g3, 256, sm, ctx->stream>>>(
+            u, F, fscale, lam, L.kmask, L.bg, L.gap, n, nz, h2inv, (float)c.nu, (float)c.kap, (float)(sqDf * sqDf),
+            lsn, L.fine, nullptr, nullptr, ctx->red_partials, L.lamp, L.coef, C.ur, C.u[0], C.r, C.kmask);
+    } else if (L.bg) {
+        constexpr size_t sm = resid_zm_smem_bytes<true>();
+        k_residual_zm<true, false, true><<<g3, 256, sm, ctx->stream>>>(
+            u, F, fscale, lam, L.kmask, L.bg, L.gap, n, nz, h2inv, (float)c.nu, (float)c.kap, (float)(sqDf * sqDf),
+            lsn, L.fine, nullptr, nullptr, ctx->red_partials, L.lamp, nullptr, C.ur, C.u[0], C.r, C.kmask);
+    } else {
+        constexpr size_t sm = resid_zm_smem_bytes<false>();
+        k_residual_zm<false, false, true><<<g3, 256, sm, ctx->stream>>>(
+            u, F, fscale, lam, L.kmask, nullptr, nullptr, n, nz, h2inv, (float)c.nu, (float)c.kap,
+            (float)(sqDf * sqDf), lsn, L.fine, nullptr, nullptr, ctx->red_partials, L.lamp, nullptr, C.ur, C.u[0],
+            C.r, C.kmask);
+    }
+    ctx->end();
+    ctx->begin(PM_K_REDUCE, false, 0);
+    k_finalize<<<1, 256, 0, ctx->stream>>>(ctx->red_partials, nb, ctx->red_out);
+    ctx->end();
+    return true;
+}
+
 template <typename T>
 static void vcycle(Exec* ctx, std::vector<Level<T>>& lv, int l, const T* F0, T fs0, T lam0, const Coef& c)
 {
@@ -716,14 +767,20 @@ static void vcycle(Exec* ctx, std::vector<Level<T>>& lv, int l, const T* F0, T f
         return;
     }
     for (int s = 0; s < ctx->prm.npre; ++s) sweep(ctx, L, F, fs, lam, c);
-    residual<T, true, false>(ctx, L, L.u[L.cur], F, fs, lam, c, nullptr, nullptr);
     Level<T>& C = lv[l + 1];
     C.cur = 0;
     const int gc = grid_for(ctx, C.cells);
-    ctx->begin(PM_K_TRANSFER, false, 0);
-    k_restrict_fas<T><<<gc, kThreads, 0, ctx->stream>>>(L.u[L.cur], L.r, L.sat, L.kmask, ctx->red_out + 8, C.n, C.ur,
-                                                        C.u[0], C.r, C.kmask);
-    ctx->end();
+    // large FP32 levels: the residual kernel restricts as well (gauge term left to k_fas_rhs)
+    bool fused = false;
+    if constexpr (sizeof(T) == 4) fused = residual_restrict_f32(ctx, L, C, L.u[L.cur], F, fs, lam, c);
+    if (!fused) {
+        residual<T, true, false>(ctx, L, L.u[L.cur], F, fs, lam, c, nullptr, nullptr);
+        ctx->begin(PM_K_TRANSFER, false, 0);
+        k_restrict_fas<T><<<gc, kThreads, 0, ctx->stream>>>(L.u[L.cur], L.r, L.sat, L.kmask, ctx->red_out + 8, C.n,
+                                                            C.ur, C.u[0], C.r, C.kmask);
+        ctx->end();
+    }
+    const double* gmp = fused ? ctx->red_out + 8 : nullptr;
     const T ih2c = (T)((double)C.n * (double)C.n);
     if (C.bg) {
         ctx->begin(PM_K_TRANSFER, false, 0);
@@ -732,12 +789,12 @@ static void vcycle(Exec* ctx, std::vector<Level<T>>& lv, int l, const T* F0, T f
         float* go = (sizeof(T) == 4 && co) ? reinterpret_cast<float*>(C.gap) : nullptr;
         const float lsn = c.kap != 0.0 ? (float)(0.75 * c.nu * (1.0 - c.eta) / c.kap) : 0.f;  // L_sat
         k_fas_rhs<T, true><<<gc, kThreads, 0, ctx->stream>>>(C.u[0], C.r, C.kmask, C.bg, C.n, ih2c, (T)c.nu,
-                                                             (T)c.kap, C.f, co, go, lsn);
+                                                             (T)c.kap, C.f, co, go, lsn, gmp);
         ctx->end();
     } else {
         ctx->begin(PM_K_TRANSFER, false, 0);
         k_fas_rhs<T, false><<<gc, kThreads, 0, ctx->stream>>>(C.u[0], C.r, C.kmask, nullptr, C.n, ih2c, (T)c.nu,
-                                                              (T)c.kap, C.f, nullptr, nullptr, 0.f);
+                                                              (T)c.kap, C.f, nullptr, nullptr, 0.f, gmp);
         ctx->end();
     }
     vcycle(ctx, lv, l + 1, F0, fs0, lam0, c);

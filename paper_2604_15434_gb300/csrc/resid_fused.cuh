@@ -24,14 +24,23 @@ constexpr size_t resid_zm_smem_bytes()
 
 // Grid (n/64, n/8, n/NZ), 256 threads; the block count must not exceed kMaxPartials.
 // COEF: the background enters through its per-cell coefficients (BgCoef), not its planes.
-template <bool BG, bool COEF = false>
+// RESTRICT: the FAS restriction is done here instead of writing r and sat for k_restrict_fas:
+// for every coarse cell (2x2x2 children; NZ even) it writes the children's mean iterate to
+// ur and uc, the children's mean raw residual to rc, and the byte kmc = (mean unscreened
+// eighths, as k_restrict_fas) | (unfloored children << 4).  The gauge term -gm * [unfloored]
+// needs the finished residual sums, so k_fas_rhs applies it from the high nibble and clears
+// it.  Children pair up across lanes x, x^1 (shuffle), rows y, y+1 (threads t, t+64: shared
+// memory) and planes s, s+1 (registers).
+template <bool BG, bool COEF = false, bool RESTRICT = false>
 __global__ void __launch_bounds__(256) k_residual_zm(const float* __restrict__ u, const float* __restrict__ F,
                                                      float fscale, float lam, const uint8_t* __restrict__ kmask,
                                                      const float* __restrict__ bg, const float* __restrict__ gap, int n,
                                                      int NZ, float ih2, float nu, float kap, float Df, float lsat_c,
                                                      bool floor_piece, float* __restrict__ r,
                                                      uint8_t* __restrict__ sat, double* __restrict__ partials,
-                                                     const float* __restrict__ lamp, const uint32_t* __restrict__ coef)
+                                                     const float* __restrict__ lamp, const uint32_t* __restrict__ coef,
+                                                     float* __restrict__ urc = nullptr, float* __restrict__ ucc = nullptr,
+                                                     float* __restrict__ rcc = nullptr, uint8_t* __restrict__ kmc = nullptr)
 {
     constexpr bool BGRING = BG && !COEF;
     if (lamp) lam += *lamp;
@@ -82,6 +91,10 @@ __global__ void __launch_bounds__(256) k_residual_zm(const float* __restrict__ u
         return s;
     };
     float fa[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    // RESTRICT: per cell h the running sums over the plane pair of iterate, residual,
+    // unscreened eighths and unfloored children; xch carries rows y+1 to rows y
+    float au[2] = {0.f, 0.f}, ar[2] = {0.f, 0.f}, ac[2] = {0.f, 0.f}, an[2] = {0.f, 0.f};
+    __shared__ float xch[RESTRICT ? 8 : 1][64];
     issue(z0 - 1);
     issue(z0);
     issue(z0 + 1);
@@ -128,8 +141,16 @@ __global__ void __launch_bounds__(256) k_residual_zm(const float* __restrict__ u
             // the floored piece exists on the finest level only (see k_residual)
             const bool fl = floor_piece && (o.P != 0.f) && (o.D < Df);
             const float rv = fl ? nu * o.g : -o.G;
-            r[os + gxy[h]] = rv;
-            if (sat) sat[os + gxy[h]] = fl ? 1 : 0;
+            if (RESTRICT) {
+                const int kf = kmask ? (kmask[os + gxy[h]] < 8 ? kmask[os + gxy[h]] : 8) : 0;
+                au[h] += a.c0;
+                ar[h] += rv;
+                ac[h] += fl ? 8.f : (float)kf;
+                an[h] += fl ? 0.f : 1.f;
+            } else {
+                r[os + gxy[h]] = rv;
+                if (sat) sat[os + gxy[h]] = fl ? 1 : 0;
+            }
             if (!isfinite(rv)) {
                 fa[4] += 1.f;
             } else {
@@ -140,6 +161,44 @@ __global__ void __launch_bounds__(256) k_residual_zm(const float* __restrict__ u
                     fa[3] += 1.f;
                 }
             }
+        }
+        if (RESTRICT && ((s - z0) & 1)) {
+            // the plane pair (s - 1, s) is complete: combine x pairs, then row pairs
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                au[h] += __shfl_xor_sync(0xffffffffu, au[h], 1);
+                ar[h] += __shfl_xor_sync(0xffffffffu, ar[h], 1);
+                ac[h] += __shfl_xor_sync(0xffffffffu, ac[h], 1);
+                an[h] += __shfl_xor_sync(0xffffffffu, an[h], 1);
+            }
+            const int q = (yA >> 1) * 32 + (x >> 1);
+            if ((yA & 1) && !(x & 1)) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    xch[4 * h + 0][q] = au[h];
+                    xch[4 * h + 1][q] = ar[h];
+                    xch[4 * h + 2][q] = ac[h];
+                    xch[4 * h + 3][q] = an[h];
+                }
+            }
+            __syncthreads();
+            if (!(yA & 1) && !(x & 1)) {
+                const int nc = n >> 1;
+                const size_t K = (size_t)(s >> 1), I = (size_t)((x0 + x) >> 1);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float su = au[h] + xch[4 * h + 0][q], sr = ar[h] + xch[4 * h + 1][q];
+                    const int cnt = (int)(ac[h] + xch[4 * h + 2][q]), nun = (int)(an[h] + xch[4 * h + 3][q]);
+                    const size_t J = (size_t)((y0 + yA + 4 * h) >> 1);
+                    const size_t c = (K * nc + J) * nc + I;
+                    urc[c] = 0.125f * su;
+                    ucc[c] = 0.125f * su;
+                    rcc[c] = 0.125f * sr;
+                    kmc[c] = (uint8_t)(((cnt + 4) >> 3) | (nun << 4));
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) au[h] = ar[h] = ac[h] = an[h] = 0.f;
         }
     }
     double acc[5];
