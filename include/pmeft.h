@@ -53,6 +53,11 @@ typedef struct {
     int linear_eft;        /* 1: pm_step / pm_run use the linearised equations (Sec. 2.5, Eq. linearised):
                               chi = (xi/nu) Psi_N from the one FFT Poisson solve, no screening and no
                               chi multigrid solve (0) */
+    int smoother;          /* local solve of the FP64 sweeps (pm_mg_sweep and the precision-0 cycle):
+                              0 Method I, the quadratic in the cell value (Sec. 3.2.1); 1 Method II,
+                              operator splitting, the quadratic in the cell's Laplacian with the
+                              traceless Hessian from the neighbours (Sec. 3.2.2, Eq. opsplit).  The two
+                              give the same update in exact arithmetic; FP32 levels use Method I (0) */
 } pm_params;
 
 /* Report of one solve.  rel_res = |r|_2 / |f - <f>|_2 of the FP64 residual. */
@@ -290,7 +295,8 @@ int pm_tune_log(const pm_ctx* ctx, char* buf, int len);
  * side; lambda added to it.  kmask (device n^3 bytes, nullable): per cell, the eighths
  * of the screening term switched off: 0 keeps kappa, k in 1..7 keeps (8-k)/8 of it, 8 or
  * more removes it (the coarse levels of the FAS cycle store there the mean unscreened
- * fraction of a cell's children).  h = 1/n. */
+ * fraction of a cell's children).  h = 1/n.  The local solve is the one the context's
+ * pm_params.smoother selects (Method I or Method II). */
 pm_status pm_mg_sweep(pm_ctx* ctx, double* u, const double* f, double lambda, int n, double nu, double kappa,
                       double eta, const unsigned char* kmask);
 /* The same sweep on an FP32 grid: mode 0 runs the two half-sweep kernels, mode k >= 1

@@ -52,6 +52,7 @@ def _lib():
             h.orc_apply_N.argtypes = [P, I, D, D, D, P]
             h.orc_apply_N_padded.argtypes = [P, I, D, D, D, P]
             h.orc_smooth_sweep.argtypes = [P, P, D, I, D, D, D, D, P]
+            h.orc_smooth_sweep_opsplit.argtypes = [P, P, D, I, D, D, D, D, P]
             h.orc_residual.argtypes = [P, P, D, I, D, D, D, D, P, P, P]
             h.orc_residual.restype = LL
             h.orc_restrict.argtypes = [P, I, P]
@@ -119,6 +120,19 @@ def smooth_sweep(u, f, lam, nu, kappa, eta, kmask=None):
     return u
 
 
+def smooth_sweep_opsplit(u, f, lam, nu, kappa, eta, kmask=None):
+    """One red-black sweep of Method II, operator splitting (Sec. 3.2.2, Eq. opsplit): each
+    cell solves its equation as a quadratic in its Laplacian, with the squared traceless
+    Hessian taken from the neighbours, then moves its value so its discrete Laplacian equals
+    that root.  Same arguments and snapshot semantics as smooth_sweep."""
+    u = _f64(u).copy()
+    f = _f64(f)
+    n = u.shape[0]
+    km = None if kmask is None else np.ascontiguousarray(kmask, dtype=np.uint8)
+    _lib().orc_smooth_sweep_opsplit(_p(u), _p(f), lam, n, 1.0 / n, nu, kappa, eta, _p(km))
+    return u
+
+
 def residual(u, f, lam, nu, kappa, eta, kmask=None):
     """Residual (unsaturated: f + lam - N(u); floored: nu (L_sat - L)) and the floored-cell mask."""
     u = _f64(u)
@@ -152,7 +166,7 @@ class _MGParams(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_double), ("kappa", ctypes.c_double), ("eta", ctypes.c_double),
                 ("npre", ctypes.c_int), ("npost", ctypes.c_int), ("max_cycles", ctypes.c_int),
                 ("coarsest_n", ctypes.c_int), ("coarse_sweeps", ctypes.c_int),
-                ("dirichlet", ctypes.c_int), ("ghosts", ctypes.c_void_p)]
+                ("dirichlet", ctypes.c_int), ("ghosts", ctypes.c_void_p), ("smoother", ctypes.c_int)]
 
 
 class _MGInfo(ctypes.Structure):
@@ -164,11 +178,12 @@ ETA_DEFAULT = 0.35
 
 
 def mg_solve(f, nu, kappa, tol, chi0=None, eta=ETA_DEFAULT, npre=2, npost=2, max_cycles=200,
-             coarsest_n=4, coarse_sweeps=100, ghosts=None):
+             coarsest_n=4, coarse_sweeps=100, ghosts=None, smoother=0):
     """FAS multigrid solve of nu L(chi) - kappa q2(chi) = f (+ lambda) (Sec. 3.4).
 
     Periodic by default (with the gauge multiplier and <chi> = 0); with ``ghosts`` (a
-    list of padded ghost arrays, finest level first) the faces are Dirichlet.
+    list of padded ghost arrays, finest level first) the faces are Dirichlet.  smoother 0
+    is Method I (Sec. 3.2.1), 1 Method II (Sec. 3.2.2).
     Returns (chi, info dict, status) with status 0 = converged, 2 = not converged.
     """
     f = _f64(f)
@@ -178,7 +193,7 @@ def mg_solve(f, nu, kappa, tol, chi0=None, eta=ETA_DEFAULT, npre=2, npost=2, max
     if ghosts is not None:
         gbuf = np.concatenate([_f64(g).ravel() for g in ghosts])
     prm = _MGParams(nu, kappa, eta, npre, npost, max_cycles, coarsest_n, coarse_sweeps,
-                    int(ghosts is not None), _p(gbuf) if gbuf is not None else None)
+                    int(ghosts is not None), _p(gbuf) if gbuf is not None else None, int(smoother))
     info = _MGInfo()
     st = _lib().orc_mg_solve(_p(f), n, ctypes.byref(prm), tol, _p(chi), ctypes.byref(info))
     d = {"cycles": info.cycles, "rel_res": info.rel_res, "lambda": info.lam, "sat_cells": info.sat_cells,

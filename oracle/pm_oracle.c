@@ -19,6 +19,10 @@
  *   - the local quadratic (Eq. chi_discrete) solved in correction form on
  *     the root that continues the linear solution (Eq. quadratic), with the
  *     discriminant floored in voids                      [Sec. 3.3]
+ *   - the same local equation solved as a quadratic in the cell's Laplacian,
+ *     with the squared traceless Hessian from the neighbours, and a Newton
+ *     update of the cell value (operator splitting)      [Sec. 3.2.2, Method II,
+ *                                                          Eq. opsplit]
  *   - red-black Gauss-Seidel sweeps and an FAS multigrid V-cycle
  *                                                        [Sec. 3.4]
  *   - CIC density assignment in 2^40 fixed point, the 5-point gradient of
@@ -34,6 +38,9 @@
  *   R-sat   "set the discriminant to a very low value close to zero" is read
  *           as D_eff = max(D, D_floor) with sqrt(D_floor) = eta * 6|nu|/h^2.
  *   R-gauge periodic solvability: N(chi) = f + lambda with <chi> = 0.
+ *   R-ops   Method II: the traceless Hessian from Method I's stencils; its discriminant
+ *           floored at (eta nu)^2 (Method I's floor in this variable); the paper's
+ *           mean subtraction of the target Laplacian is the gauge multiplier lambda.
  *   R-rb    red-black: the 12 edge neighbours share the centre's colour; a
  *           half-sweep reads them from the values at the start of the half-sweep.
  *   R-res   residual: f + lambda - N(chi) in cells with a real root, and
@@ -263,6 +270,83 @@ static void sweep_padded(double* p, double* snap, const double* f, double lam, i
     fill_ghosts(p, n, ghost);
 }
 
+/* ------------------------------------------------------------------ */
+/* Method II, operator splitting (Sec. 3.2.2, Eq. opsplit; w = 1/3).
+ * With Method I's second differences X, Y, Z and cross differences, the squared traceless
+ * Hessian
+ *     T2 = (X - L/3)^2 + (Y - L/3)^2 + (Z - L/3)^2 + 2 (chi_xy^2 + chi_xz^2 + chi_yz^2)
+ * needs only the neighbours: X - L/3 = (2 a_x - a_y - a_z) / (3 h^2), a_x the sum of the
+ * two x neighbours (the centre cancels), and the cross differences never hold the centre.
+ * Since q2 = (2/3) L^2 - T2, the cell's equation nu L - kappa q2 = f + lambda is a
+ * quadratic in its Laplacian L:
+ *     a L^2 + b L + c = 0,   a = -(2/3) kappa,   b = nu,   c = kappa T2 - (f + lambda).
+ * The root continuing the linear solution L = (f + lambda)/nu is taken.  Readings:
+ *   - the discriminant floor of R-sat, carried to this variable: the chi-quadratic's
+ *     discriminant is (6/h^2)^2 times this one, so D_L is floored at (eta nu)^2, and the
+ *     floored root is the vertex-shifted one, L = L_sat;
+ *   - the paper's subtraction of the mean of the target Laplacians (periodic solvability)
+ *     is the gauge multiplier lambda of R-gauge, as for Method I.
+ * The Newton update then moves the centre value so that its discrete Laplacian, linear in
+ * the centre with slope -6/h^2, equals the root:  chi += (L_now - L_root) h^2 / 6.       */
+/* ------------------------------------------------------------------ */
+static double opsplit_update(const double* p, size_t c, int n, double h, double nu, double kap, double rhs,
+                             double eta, int* sat)
+{
+    size_t sx = 1, sy = (size_t)n + 2, sz = sy * sy;
+    double h2 = h * h;
+    double c0 = p[c];
+    double ax = p[c + sx] + p[c - sx];
+    double ay = p[c + sy] + p[c - sy];
+    double az = p[c + sz] + p[c - sz];
+    double Lnow = (ax + ay + az - 6.0 * c0) / h2;
+    double Lroot;
+    *sat = 0;
+    if (kap == 0.0) {
+        Lroot = rhs / nu;
+    } else {
+        double tx = (2.0 * ax - ay - az) / (3.0 * h2);
+        double ty = (2.0 * ay - ax - az) / (3.0 * h2);
+        double tz = (2.0 * az - ax - ay) / (3.0 * h2);
+        double cxy = (p[c + sx + sy] - p[c + sx - sy] - p[c - sx + sy] + p[c - sx - sy]) / (4.0 * h2);
+        double cxz = (p[c + sx + sz] - p[c + sx - sz] - p[c - sx + sz] + p[c - sx - sz]) / (4.0 * h2);
+        double cyz = (p[c + sy + sz] - p[c + sy - sz] - p[c - sy + sz] + p[c - sy - sz]) / (4.0 * h2);
+        double T2 = tx * tx + ty * ty + tz * tz + 2.0 * (cxy * cxy + cxz * cxz + cyz * cyz);
+        double a = -2.0 * kap / 3.0, b = nu, cc = kap * T2 - rhs;
+        double D = b * b - 4.0 * a * cc;
+        double Dfl = eta * nu * eta * nu;
+        double sb = nu >= 0.0 ? 1.0 : -1.0;
+        if (D < Dfl) {
+            *sat = 1;
+            Lroot = (-b + sb * sqrt(Dfl)) / (2.0 * a);
+        } else {
+            Lroot = -2.0 * cc / (b + sb * sqrt(D));
+        }
+    }
+    return c0 + (Lnow - Lroot) * h2 / 6.0;
+}
+
+/* One red-black sweep of Method II, with the snapshot semantics of sweep_padded. */
+static void sweep_padded_opsplit(double* p, double* snap, const double* f, double lam, int n, double h,
+                                 double nu, double kap, double eta, const unsigned char* kmask,
+                                 const double* ghost)
+{
+    size_t m = (size_t)n + 2, tot = m * m * m;
+    for (int colour = 0; colour < 2; ++colour) {
+        fill_ghosts(p, n, ghost);
+        memcpy(snap, p, tot * sizeof(double));
+        for (int k = 0; k < n; ++k)
+            for (int j = 0; j < n; ++j)
+                for (int i = 0; i < n; ++i) {
+                    if (((i + j + k) & 1) != colour) continue;
+                    size_t u = uidx(i, j, k, n);
+                    int sat;
+                    p[pidx(i, j, k, n)] = opsplit_update(snap, pidx(i, j, k, n), n, h, nu, kap * screen_w(kmask, u),
+                                                         f[u] + lam, eta, &sat);
+                }
+    }
+    fill_ghosts(p, n, ghost);
+}
+
 /* Residual on a padded array; returns the count of floored cells. */
 static long long residual_padded(double* p, const double* f, double lam, int n, double h, double nu,
                                  double kap, double eta, const unsigned char* kmask, const double* ghost,
@@ -287,6 +371,19 @@ static long long residual_padded(double* p, const double* f, double lam, int n, 
 }
 
 /* Public single-operation entry points on periodic unpadded grids. */
+void orc_smooth_sweep_opsplit(double* u, const double* f, double lam, int n, double h, double nu, double kap,
+                              double eta, const unsigned char* kmask)
+{
+    size_t m = (size_t)n + 2;
+    double* p = (double*)malloc(m * m * m * sizeof(double));
+    double* s = (double*)malloc(m * m * m * sizeof(double));
+    pad_from(u, n, p);
+    sweep_padded_opsplit(p, s, f, lam, n, h, nu, kap, eta, kmask, NULL);
+    unpad_to(p, n, u);
+    free(p);
+    free(s);
+}
+
 void orc_smooth_sweep(double* u, const double* f, double lam, int n, double h, double nu, double kap,
                       double eta, const unsigned char* kmask)
 {
@@ -369,7 +466,9 @@ typedef struct {
     int npre, npost, max_cycles, coarsest_n, coarse_sweeps;
     int dirichlet;              /* 0: periodic with gauge multiplier; 1: fixed ghosts */
     const double* ghosts;       /* Dirichlet: padded ghost arrays of every level, finest first */
+    int smoother;               /* 0: Method I (quadratic in the cell value); 1: Method II */
 } orc_mg_params;
+
 
 typedef struct {
     int cycles;
@@ -387,6 +486,16 @@ typedef struct {
     const double* ghost;
 } level_t;
 
+/* One smoothing sweep of a level with the method the parameters select. */
+static void smooth_level(level_t* L, double lam, const orc_mg_params* prm)
+{
+    if (prm->smoother == 1)
+        sweep_padded_opsplit(L->p, L->snap, L->f, lam, L->n, L->h, prm->nu, prm->kappa, prm->eta, L->kmask,
+                             L->ghost);
+    else
+        sweep_padded(L->p, L->snap, L->f, lam, L->n, L->h, prm->nu, prm->kappa, prm->eta, L->kmask, L->ghost);
+}
+
 static double sum_arr(const double* a, size_t m)
 {
     double s = 0.0;
@@ -400,7 +509,7 @@ static void coarse_solve(level_t* L, const orc_mg_params* prm, int periodic)
     size_t m = (size_t)L->n * L->n * L->n;
     double lam = 0.0;
     for (int it = 0; it < prm->coarse_sweeps; ++it) {
-        sweep_padded(L->p, L->snap, L->f, lam, L->n, L->h, prm->nu, prm->kappa, prm->eta, L->kmask, L->ghost);
+        smooth_level(L, lam, prm);
         if (periodic) {
             residual_padded(L->p, L->f, lam, L->n, L->h, prm->nu, prm->kappa, prm->eta, L->kmask, L->ghost,
                             L->r, L->sat);
@@ -421,7 +530,7 @@ static void vcycle(level_t* lv, int l, int nlev, double lam, const orc_mg_params
     level_t* C = &lv[l + 1];
     size_t m = (size_t)L->n * L->n * L->n, mc = (size_t)C->n * C->n * C->n;
     for (int s = 0; s < prm->npre; ++s)
-        sweep_padded(L->p, L->snap, L->f, lam, L->n, L->h, prm->nu, prm->kappa, prm->eta, L->kmask, L->ghost);
+        smooth_level(L, lam, prm);
     residual_padded(L->p, L->f, lam, L->n, L->h, prm->nu, prm->kappa, prm->eta, L->kmask, L->ghost, L->r, L->sat);
     /* project out the part of the residual the gauge multiplier absorbs */
     if (periodic) {
@@ -469,7 +578,7 @@ static void vcycle(level_t* lv, int l, int nlev, double lam, const orc_mg_params
     free(tc);
     free(nh);
     for (int s = 0; s < prm->npost; ++s)
-        sweep_padded(L->p, L->snap, L->f, lam, L->n, L->h, prm->nu, prm->kappa, prm->eta, L->kmask, L->ghost);
+        smooth_level(L, lam, prm);
 }
 
 /*

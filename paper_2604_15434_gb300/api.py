@@ -32,7 +32,8 @@ class Params(ctypes.Structure):
     _fields_ = [("omega_m0", ctypes.c_double), ("eta", ctypes.c_double), ("npre", ctypes.c_int),
                 ("npost", ctypes.c_int), ("max_cycles", ctypes.c_int), ("coarsest_n", ctypes.c_int),
                 ("coarse_sweeps", ctypes.c_int), ("precision", ctypes.c_int), ("include_dot_alphaB", ctypes.c_int),
-                ("inner_cycles", ctypes.c_int), ("autotune", ctypes.c_int), ("linear_eft", ctypes.c_int)]
+                ("inner_cycles", ctypes.c_int), ("autotune", ctypes.c_int), ("linear_eft", ctypes.c_int),
+                ("smoother", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):

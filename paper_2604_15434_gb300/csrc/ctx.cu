@@ -187,6 +187,7 @@ extern "C" void pm_default_params(pm_params* p)
     p->inner_cycles = 1;
     p->autotune = 1;
     p->linear_eft = 0;
+    p->smoother = 0;
 }
 
 static bool params_ok(const pm_params* p)
@@ -195,7 +196,8 @@ static bool params_ok(const pm_params* p)
            p->npost >= 0 && p->npre + p->npost > 0 && p->max_cycles >= 0 && p->coarsest_n >= 2 &&
            p->coarsest_n <= 8 && (p->coarsest_n & (p->coarsest_n - 1)) == 0 && p->coarse_sweeps >= 1 &&
            (p->precision == 0 || p->precision == 1) && p->inner_cycles >= 1 && p->inner_cycles <= 16 &&
-           (p->autotune == 0 || p->autotune == 1) && (p->linear_eft == 0 || p->linear_eft == 1);
+           (p->autotune == 0 || p->autotune == 1) && (p->linear_eft == 0 || p->linear_eft == 1) &&
+           (p->smoother == 0 || p->smoother == 1);
 }
 
 extern "C" pm_status pm_coefficients(double aB0, double aM0, double a, double om0, int include_dot, pm_coeffs* out)

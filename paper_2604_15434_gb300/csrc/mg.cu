@@ -48,15 +48,49 @@ __global__ void k_finalize(const double* __restrict__ partials, int nblocks, dou
 
 // ------------------------------------------------------------------ smoother
 
+// Method II, operator splitting (Sec. 3.2.2, Eq. opsplit): the cell's equation
+// nu L - kap [(2/3) L^2 - T2] = rhs as a quadratic in its Laplacian L, T2 the squared
+// traceless Hessian, which holds no centre value (X - L/3 = (2 a_x - a_y - a_z)/(3 h^2));
+// the root continuing the linear solution, the discriminant floored at (eta nu)^2 (the
+// floor of Method I carried to this variable, whose floored root is L_sat), then the
+// Newton update that gives the centre that Laplacian.  In exact arithmetic this is
+// Method I's update; it is a second, independent form of the same local solve.
+template <typename T>
+__device__ __forceinline__ T opsplit_update(const Stencil<T>& s, T ih2, T nu, T kap, T rhs, T etanu)
+{
+    const T Lnow = (s.ax + s.ay + s.az - T(6) * s.c0) * ih2;
+    T Lroot;
+    if (kap == T(0)) {
+        Lroot = rhs / nu;
+    } else {
+        const T third = T(1) / T(3);
+        const T tx = (T(2) * s.ax - s.ay - s.az) * ih2 * third;
+        const T ty = (T(2) * s.ay - s.ax - s.az) * ih2 * third;
+        const T tz = (T(2) * s.az - s.ax - s.ay) * ih2 * third;
+        const T q = T(0.25) * ih2;
+        const T cxy = s.exy * q, cxz = s.exz * q, cyz = s.eyz * q;
+        const T T2 = tx * tx + ty * ty + tz * tz + T(2) * (cxy * cxy + cxz * cxz + cyz * cyz);
+        const T a = T(-2) * kap * third, cc = kap * T2 - rhs;
+        const T D = nu * nu - T(4) * a * cc;
+        const T sb = nu >= T(0) ? T(1) : T(-1);
+        if (D < etanu * etanu)
+            Lroot = (-nu + sb * etanu) / (T(2) * a);
+        else
+            Lroot = T(-2) * cc / (nu + sb * sqrt(D));
+    }
+    return s.c0 + (Lnow - Lroot) / (T(6) * ih2);
+}
+
 // One colour half-sweep over the n^3/2 cells of `colour` ((i+j+k) & 1 == colour).
 // own: array holding this colour's current values; oth: the other colour's; out:
-// receives the new values of this colour.  rhs = fscale * F + lam.
-template <typename T, bool BG>
+// receives the new values of this colour.  rhs = fscale * F + lam.  OPS: the local solve
+// of Method II (opsplit_update; etanu = eta |nu|) instead of Method I's.
+template <typename T, bool BG, bool OPS = false>
 __global__ void __launch_bounds__(256) k_half_sweep(const T* __restrict__ own, const T* __restrict__ oth,
                                                     T* __restrict__ out, const T* __restrict__ F, T fscale, T lam,
                                                     const uint8_t* __restrict__ kmask, const T* __restrict__ bg,
                                                     const T* __restrict__ gap, int n, int colour, T ih2, T nu, T kap,
-                                                    T sp, T Df, T lsat_c, const T* __restrict__ lamp)
+                                                    T sp, T Df, T lsat_c, const T* __restrict__ lamp, T etanu)
 {
     if (lamp) lam += *lamp;
     const int hn = n >> 1;
@@ -73,6 +107,10 @@ __global__ void __launch_bounds__(256) k_half_sweep(const T* __restrict__ own, c
         if (BG) b = load_stencil(bg, bg, i, j, k, n);
         const T w = screen_w<T>(kmask, c);
         const T kc = kap * w;
+        if (OPS) {
+            out[c] = opsplit_update<T>(s, ih2, nu, kc, fscale * F[c] + lam, etanu);
+            continue;
+        }
         const T lsat = kc != T(0) ? lsat_c / w : T(0);
         Local<T> o = local_eval<T, BG>(s, b, ih2, nu, kc, fscale * F[c] + lam, lsat, gap != nullptr, gap ? gap[c] : T(0));
         out[c] = s.c0 + local_update(o, sp, Df, ih2);
@@ -627,13 +665,21 @@ static void sweep(Exec* ctx, Level<T>& L, const T* F, T fscale, T lam, const Coe
             ctx->begin(sizeof(T) == 8 ? PM_K_SWEEP64 : PM_K_SWEEP32, L.fine, (long long)(L.cells / 2));
             k_half_sweep<T, true><<<grid, kThreads, 0, ctx->stream>>>(own, oth, B, F, fscale, lam, L.kmask, L.bg,
                                                                       L.gap, n, colour, h2inv, (T)c.nu, (T)c.kap, sp,
-                                                                      (T)(sqDf * sqDf), lsn, L.lamp);
+                                                                      (T)(sqDf * sqDf), lsn, L.lamp, T(0));
             ctx->end();
         } else {
             ctx->begin(sizeof(T) == 8 ? PM_K_SWEEP64 : PM_K_SWEEP32, L.fine, (long long)(L.cells / 2));
-            k_half_sweep<T, false><<<grid, kThreads, 0, ctx->stream>>>(own, oth, B, F, fscale, lam, L.kmask, nullptr,
-                                                                       nullptr, n, colour, h2inv, (T)c.nu, (T)c.kap,
-                                                                       sp, (T)(sqDf * sqDf), lsn, L.lamp);
+            // Method II where the parameters ask for it (the FP64 cycle; FP32 levels keep Method I)
+            const bool ops = sizeof(T) == 8 && ctx->prm.smoother == 1;
+            const T etanu = (T)(c.eta * std::fabs(c.nu));
+            if (ops)
+                k_half_sweep<T, false, true><<<grid, kThreads, 0, ctx->stream>>>(
+                    own, oth, B, F, fscale, lam, L.kmask, nullptr, nullptr, n, colour, h2inv, (T)c.nu, (T)c.kap, sp,
+                    (T)(sqDf * sqDf), lsn, L.lamp, etanu);
+            else
+                k_half_sweep<T, false><<<grid, kThreads, 0, ctx->stream>>>(
+                    own, oth, B, F, fscale, lam, L.kmask, nullptr, nullptr, n, colour, h2inv, (T)c.nu, (T)c.kap, sp,
+                    (T)(sqDf * sqDf), lsn, L.lamp, etanu);
             ctx->end();
         }
     }

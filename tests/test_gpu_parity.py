@@ -95,6 +95,34 @@ def test_one_sweep_with_mask_and_nu_negative(gpu_lib):
     assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
 
 
+@pytest.mark.parametrize("aB0,aM0,masked", [(-0.5, 0.0, False), (-2.0, 0.5, True)])
+def test_method_ii_sweep_matches_oracle(gpu_lib, aB0, aM0, masked):
+    """pm_mg_sweep with smoother = 1 (Method II, Sec. 3.2.2) against the oracle's Method II sweep."""
+    n = 32
+    u, f, _ = _sweep_inputs(n, 21, 0.5)
+    c = O.coefficients(aB0, aM0, 1.0)
+    km = np.random.default_rng(8).integers(0, 10, (n, n, n)).astype(np.uint8) if masked else None
+    want = O.smooth_sweep_opsplit(u, f, 0.01, c["nu"], c["kappa"], 0.35, kmask=km)
+    ctx = gpu_lib.Context(smoother=1)
+    got = gpu_lib.pm_mg_sweep(cu(u), cu(f), 0.01, c["nu"], c["kappa"], 0.35,
+                              kmask=None if km is None else cu(km, torch.uint8), ctx=ctx).cpu().numpy()
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_method_ii_fp64_solve_matches_method_i_and_oracle(gpu_lib):
+    """The FP64 FAS solve with Method II sweeps converges to the Method I solution and the oracle's."""
+    n = 32
+    d = synth.lognormal_delta(n, -2.0, 1.5, 1003)
+    chi1, i1 = gpu_lib.scalar_mg_solve(cu(d), -2.0, 0.0, 1.0, 1e-11, ctx=gpu_lib.Context(precision=0))
+    chi2, i2 = gpu_lib.scalar_mg_solve(cu(d), -2.0, 0.0, 1.0, 1e-11, ctx=gpu_lib.Context(precision=0, smoother=1))
+    a, b = chi1.cpu().numpy(), chi2.cpu().numpy()
+    assert i2["rel_res"] <= 1e-11
+    assert np.abs(a - b).max() <= 1e-9 * np.abs(a).max()
+    want, _, st = O.scalar_solve(d, -2.0, 0.0, 1.0, 1e-11)
+    assert st == 0
+    assert np.abs(b - want).max() <= 1e-9 * np.abs(want).max()
+
+
 def test_residual_matches_oracle(gpu_lib):
     n = 16
     u, f, c = _sweep_inputs(n, 11, 1.0)

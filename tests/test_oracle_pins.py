@@ -161,6 +161,61 @@ def test_local_update_solves_the_cell_equation():
     assert checked == n ** 3 // 2
 
 
+@pytest.mark.parametrize("nu,kap", [(0.475, 0.5), (-1.1, 2.0)])
+def test_method_ii_update_solves_the_cell_equation(nu, kap):
+    """Method II (Sec. 3.2.2, Eq. opsplit): after its red half-sweep each red cell, with only
+    its own value changed, zeroes the residual of the operator of Sec. 3.2.1 (real root), or
+    of the floored piece of R-res (floored cells, exercised by the nu < 0 case)."""
+    rng = np.random.default_rng(6)
+    n = 8
+    u = 0.002 * rng.standard_normal((n, n, n))
+    f = rng.standard_normal((n, n, n))
+    eta = 0.35
+    u1 = O.smooth_sweep_opsplit(u, f, 0.0, nu, kap, eta)
+    red = (np.indices(u.shape).sum(0) % 2) == 0
+    floored = 0
+    for cell in zip(*np.nonzero(red)):
+        uc = u.copy()
+        uc[cell] = u1[cell]
+        r, sat = O.residual(uc, f, 0.0, nu, kap, eta)
+        scale = 6 * abs(nu) * n * n * max(abs(uc[cell]), 1e-3)
+        assert abs(r[cell]) < 1e-10 * scale, (cell, r[cell], sat[cell])
+        floored += int(sat[cell])
+    if nu < 0:
+        assert floored > 0
+
+
+@pytest.mark.parametrize("aB0,aM0,masked", [(-0.5, 0.0, False), (-2.0, 0.0, False), (-2.0, 0.5, True)])
+def test_method_ii_sweep_equals_method_i(aB0, aM0, masked):
+    """The squared traceless Hessian holds no centre value and q2 = (2/3) L^2 - T2, so Method II's
+    local solve in the Laplacian and Method I's in the cell value (Eq. quadratic) are one
+    equation: a whole sweep agrees to rounding, floored and partly screened cells included."""
+    n = 16
+    d = synth.lognormal_delta(n, -2.0, 1.5, 1003)
+    c = O.coefficients(aB0, aM0, 1.0)
+    f = O.source(d, c)
+    u = 1e-3 * np.random.default_rng(2).standard_normal((n, n, n))
+    km = np.random.default_rng(4).integers(0, 10, (n, n, n)).astype(np.uint8) if masked else None
+    a = O.smooth_sweep(u, f, 0.013, c["nu"], c["kappa"], 0.35, kmask=km)
+    b = O.smooth_sweep_opsplit(u, f, 0.013, c["nu"], c["kappa"], 0.35, kmask=km)
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
+    _, fl = O.residual(a, f, 0.013, c["nu"], c["kappa"], 0.35)
+    if c["nu"] < 0:
+        assert fl.sum() > 0
+
+
+def test_method_ii_fas_solve_matches_method_i():
+    """The FAS cycle with Method II sweeps reaches the solution of the Method I cycle."""
+    n = 16
+    d = synth.lognormal_delta(n, -2.0, 1.5, 1003)
+    c = O.coefficients(-2.0, 0.0, 1.0)
+    f = O.source(d, c)
+    chi1, i1, s1 = O.mg_solve(f, c["nu"], c["kappa"], 1e-11)
+    chi2, i2, s2 = O.mg_solve(f, c["nu"], c["kappa"], 1e-11, smoother=1)
+    assert s1 == 0 and s2 == 0
+    assert np.abs(chi1 - chi2).max() <= 1e-10 * np.abs(chi1).max()
+
+
 @pytest.mark.parametrize("k", [0, 3, 8, 11])
 def test_partial_screening_mask_scales_kappa(k):
     """The mask byte k of a cell keeps (8 - k)/8 of the screening term (none for k >= 8):
