@@ -222,6 +222,73 @@ def warm_start_leg(api, delta, stream, ctx):
             "note": "total_ms = initial guess + solve; guess_rel_res = relative residual of the guess"}
 
 
+def next_rows_leg(api, dev, stream):
+    """The full PM step of the 256^3-mesh / 256^3-particle configuration (Zel'dovich ICs,
+    P ~ k^-1.5, sigma 2, alpha = (-1, 0.2), a = 1, dt = 1e-3: deposit, FFT Poisson, chi solve to
+    1e-8, gradient, force interpolation, kick-drift) and the rows built beyond the solve: a
+    4-step run a = 0.5 -> 1, the linearised mode, the lensing potential and the Method II
+    smoother.  Each is timed on the device through the public API after one warm-up call."""
+    import torch
+    from paper_2604_15434_gb300 import synth
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, r
+
+    n = 256
+    pos0 = torch.from_numpy(synth.zeldovich_particles(n, -1.5, 2.0, 1002)).to(dev)
+    pos, vel = pos0.clone(), torch.zeros_like(pos0)
+    phi = torch.zeros((n, n, n), dtype=torch.float64, device=dev)
+    out = {"particles": n ** 3, "mesh": n}
+
+    def step(c, tol=TOL):
+        pos.copy_(pos0)
+        vel.zero_()
+        phi.zero_()
+        return api.pm_step(pos, vel, n, -1.0, 0.2, 1.0, 1e-3, tol, phi, ctx=c)
+
+    for name, c in (("pm_step_mixed", api.Context(dev.index, stream, precision=1, max_cycles=100)),
+                    ("pm_step_fp64", api.Context(dev.index, stream, precision=0, max_cycles=100)),
+                    ("pm_step_linearised", api.Context(dev.index, stream, precision=1, linear_eft=1))):
+        ms, info = timed(lambda: step(c), 2)
+        out[name] = {"ms": ms, "cycles": info["cycles"], "rel_res": info["rel_res"],
+                     "particles_per_s": n ** 3 / (ms * 1e-3)}
+    cr = api.Context(dev.index, stream, precision=1, max_cycles=100)
+
+    def run():
+        pos.copy_(pos0)
+        vel.zero_()
+        phi.zero_()
+        return api.pm_run(pos, vel, n, -1.0, 0.2, 0.5, 1.0, 4, TOL, phi, ctx=cr)
+
+    ms, info = timed(run, 1)
+    out["pm_run_4_steps"] = {"ms": ms, "ms_per_step": ms / 4, "last_cycles": info["cycles"]}
+    psi = api.poisson_solve(torch.from_numpy(synth.lognormal_delta(n, -2.0, 1.5, SEED)).to(dev), 1.0, 0.2, ctx=cr)
+    ms, _ = timed(lambda: api.lensing_potential(psi, phi, -1.0, 0.2, 1.0, ctx=cr), 5)
+    out["lensing_potential"] = {"ms": ms, "gbs": 3 * 8 * n ** 3 / (ms * 1e-3) / 1e9}
+    m2 = {}
+    d128 = torch.from_numpy(synth.lognormal_delta(128, -2.0, 1.5, SEED)).to(dev)
+    p128 = torch.zeros_like(d128)
+    for sm in (0, 1):
+        c = api.Context(dev.index, stream, precision=0, max_cycles=100, smoother=sm)
+
+        def solve():
+            p128.zero_()
+            return api.scalar_mg_solve(d128, -2.0, 0.0, 1.0, TOL, phi=p128, ctx=c)[1]
+
+        ms, info = timed(solve, 2)
+        m2["method_" + ("II" if sm else "I")] = {"ms": ms, "cycles": info["cycles"], "rel_res": info["rel_res"]}
+    out["fp64_solve_128_by_smoother"] = m2
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -257,6 +324,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the 24-box batched-solve leg")
     ap.add_argument("--no-warm", action="store_true", help="skip the cold / linear / learned warm-start leg")
+    ap.add_argument("--no-next", action="store_true", help="skip the PM-step / run / linearised / lensing / "
+                                                            "Method II leg")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -425,6 +494,8 @@ def main():
                 line["speedup_learned_vs_fp64"] = line["fp64_ms_per_solve"] / ws_leg["mean_total_ms"]["learned"]
     if not args.no_batch:
         line["batched"] = batched_leg(api, dev, stream)
+    if not args.no_next:
+        line["next_rows"] = next_rows_leg(api, dev, stream)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.sample_n)
     if rank == 0:
