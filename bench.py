@@ -445,7 +445,7 @@ def main():
                 "achieved": ach, "peak": hbm,
                 "unit": "GB/s", "frac": ach / hbm, "traffic": SWEEP_DRAM_BYTES_PER_CELL * cells,
                 "traffic_source": "ncu capture of a 512^3 launch (profiles/k_sweep_pair_256.md)",
-                "peak_source": src,
+                "peak_source": src, "frac_of_nominal_8000": ach / 8000.0,
                 "bytes_per_launch": bytes_launch, "avg_launch_ms": avg_ms, "launches": fine["fine_launches"]}
     r64 = prof_all["resid64"]
     resid64 = None
@@ -477,6 +477,11 @@ def main():
         "speedup_vs_fp64": ((sum(v["ms"] for v in fp64.values()) / len(fp64)) / value) if fp64 else None,
         "solves": {f"{k[0]},{k[1]}": {"cycles": v["cycles"], "rel_res": v["rel_res"], "floored": v["floored_cells"],
                                        "ms": v["ms_total"]} for k, v in infos.items()},
+        # fine-equivalent smoother throughput: every level's cells x sweeps of the inner V-cycles
+        # (one per outer iteration), per second of solve time; and n^3 per time to tolerance
+        "cell_updates_per_s": sum(v["vcycles"] * 4 * sum((n >> l) ** 3 for l in range(int(math.log2(n)) - 1))
+                                  for v in infos.values()) / (sum(v["ms_total"] for v in infos.values()) * 1e-3),
+        "cells_per_s_to_tol": cells * len(infos) / (sum(v["ms_total"] for v in infos.values()) * 1e-3),
         "kernel_ms_per_step": {k: v["ms"] for k, v in prof_all.items()},
         "dominant_class": dominant,
         "resid64": resid64,
