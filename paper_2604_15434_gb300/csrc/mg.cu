@@ -286,6 +286,72 @@ __global__ void __launch_bounds__(256) k_fas_rhs(const T* __restrict__ uc, const
     }
 }
 
+// k_fas_rhs for levels of at least 32^3, tiled: a block stages the iterate (and the
+// background) of a 32 x 4 x 4 brick with its one-cell halo in shared memory, and each
+// thread evaluates two cells' stencils from there, with the arithmetic of load_stencil and
+// k_fas_rhs.  Grid (n/32, n/4, n/4), 256 threads.
+template <typename T, bool BG>
+__global__ void __launch_bounds__(256) k_fas_rhs_tile(const T* __restrict__ uc, const T* __restrict__ rc,
+                                                      uint8_t* __restrict__ kmask, const T* __restrict__ bg, int n,
+                                                      T ih2, T nu, T kap, T* __restrict__ fc,
+                                                      uint32_t* __restrict__ coefo, float* __restrict__ gapo,
+                                                      float lsat, const double* __restrict__ gm_ptr)
+{
+    constexpr int BX = 32, BY = 4, BZ = 4, WX = BX + 2, WY = BY + 2, WZ = BZ + 2, WXY = WX * WY, P = WXY * WZ;
+    __shared__ T su[P];
+    __shared__ T sb[BG ? P : 1];
+    const int m = n - 1;
+    const int X0 = blockIdx.x * BX, Y0 = blockIdx.y * BY, Z0 = blockIdx.z * BZ;
+    for (int e = threadIdx.x; e < P; e += 256) {
+        const int xx = e % WX, yy = (e / WX) % WY, zz = e / WXY;
+        const size_t g = ((size_t)((Z0 - 1 + zz) & m) * n + ((Y0 - 1 + yy) & m)) * n + ((X0 - 1 + xx) & m);
+        su[e] = uc[g];
+        if (BG) sb[e] = bg[g];
+    }
+    __syncthreads();
+    auto stencil = [&](const T* p, int c) {
+        Stencil<T> s;
+        s.c0 = p[c];
+        s.ax = p[c + 1] + p[c - 1];
+        s.ay = p[c + WX] + p[c - WX];
+        s.az = p[c + WXY] + p[c - WXY];
+        s.exy = p[c + 1 + WX] - p[c + 1 - WX] - p[c - 1 + WX] + p[c - 1 - WX];
+        s.exz = p[c + 1 + WXY] - p[c + 1 - WXY] - p[c - 1 + WXY] + p[c - 1 - WXY];
+        s.eyz = p[c + WX + WXY] - p[c + WX - WXY] - p[c - WX + WXY] + p[c - WX - WXY];
+        return s;
+    };
+    const T gm = gm_ptr ? (T)(*gm_ptr) : T(0);
+    const size_t total = (size_t)n * n * n;
+    const int x = threadIdx.x & 31, y = (threadIdx.x >> 5) & 3;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int z = (threadIdx.x >> 7) + 2 * h;
+        const int cl = ((z + 1) * WY + (y + 1)) * WX + x + 1;
+        const size_t c = ((size_t)(Z0 + z) * n + (Y0 + y)) * n + (X0 + x);
+        Stencil<T> s = stencil(su, cl);
+        Stencil<T> b;
+        if (BG) b = stencil(sb, cl);
+        T rcv = rc[c];
+        if (gm_ptr) {
+            const uint8_t kb = kmask[c];
+            rcv -= gm * (T)(kb >> 4) * T(0.125);
+            kmask[c] = kb & 15;
+        }
+        const T w = screen_w<T>(kmask, c);
+        const T kc = kap * w;
+        Local<T> o = local_eval<T, BG>(s, b, ih2, nu, kc, T(0), T(0));
+        fc[c] = o.G + rcv;
+        if (BG && coefo) {
+            const float Xb = (float)(b.ax - T(2) * b.c0), Yb = (float)(b.ay - T(2) * b.c0),
+                        Zb = (float)(b.az - T(2) * b.c0);
+            coefo[c] = pack_bf16x2(2.f * (Yb + Zb), 2.f * (Xb + Zb));
+            coefo[total + c] = pack_bf16x2(2.f * (Xb + Yb), -0.25f * (float)b.exy);
+            coefo[2 * total + c] = pack_bf16x2(-0.25f * (float)b.exz, -0.25f * (float)b.eyz);
+            gapo[c] = kc != T(0) ? lsat / (float)w - (float)ih2 * (Xb + Yb + Zb) : 0.f;
+        }
+    }
+}
+
 // fine += trilinear cell-centred prolongation of (uc - ur), periodic.  One thread per
 // coarse cell writes its 8 children: the 3x3x3 coarse neighbourhood is interpolated
 // separably (weights 3/4 and 1/4 per axis, i.e. 27/64, 9/64, 3/64, 1/64 in 3D), and the
@@ -319,6 +385,59 @@ __global__ void __launch_bounds__(256) k_prolong_add(const T* __restrict__ uc, c
                 px[kz][jy][1] = a * v[1] + b * v[2];
             }
         // along y, then z, then add to the children
+#pragma unroll
+        for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy) {
+                T out[2];
+#pragma unroll
+                for (int dx = 0; dx < 2; ++dx) {
+                    T py[3];
+#pragma unroll
+                    for (int kz = 0; kz < 3; ++kz) py[kz] = a * px[kz][1][dx] + b * px[kz][dy ? 2 : 0][dx];
+                    out[dx] = a * py[1] + b * py[dz ? 2 : 0];
+                }
+                T* f = uf + ((size_t)(2 * K + dz) * nf + (2 * J + dy)) * nf + 2 * I;
+                f[0] += out[0];
+                f[1] += out[1];
+            }
+    }
+}
+
+// The same prolongation for coarse grids of at least 32^3, tiled: a block stages the
+// differences uc - ur of a 32 x 4 x 4 coarse brick and its one-cell halo (34 x 6 x 6) in
+// shared memory once, then each thread interpolates the children of two coarse cells from
+// there (the interpolation and its order as in k_prolong_add) and updates them as x pairs.
+// Grid (nc/32, nc/4, nc/4), 256 threads.
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong_add_tile(const T* __restrict__ uc, const T* __restrict__ ur,
+                                                          int nc, T* __restrict__ uf)
+{
+    constexpr int BX = 32, BY = 4, BZ = 4, WX = BX + 2, WY = BY + 2, WZ = BZ + 2, P = WX * WY * WZ;
+    __shared__ T sd[P];
+    const int mc = nc - 1, nf = 2 * nc;
+    const int X0 = blockIdx.x * BX, Y0 = blockIdx.y * BY, Z0 = blockIdx.z * BZ;
+    for (int e = threadIdx.x; e < P; e += 256) {
+        const int xx = e % WX, yy = (e / WX) % WY, zz = e / (WX * WY);
+        const size_t g = ((size_t)((Z0 - 1 + zz) & mc) * nc + ((Y0 - 1 + yy) & mc)) * nc + ((X0 - 1 + xx) & mc);
+        sd[e] = ur ? uc[g] - ur[g] : uc[g];
+    }
+    __syncthreads();
+    const T a = T(0.75), b = T(0.25);
+    const int x = threadIdx.x & 31, y = (threadIdx.x >> 5) & 3;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int z = (threadIdx.x >> 7) + 2 * h;
+        T px[3][3][2];
+#pragma unroll
+        for (int kz = 0; kz < 3; ++kz)
+#pragma unroll
+            for (int jy = 0; jy < 3; ++jy) {
+                const T* v = sd + ((z + kz) * WY + (y + jy)) * WX + x;
+                px[kz][jy][0] = a * v[1] + b * v[0];
+                px[kz][jy][1] = a * v[1] + b * v[2];
+            }
+        const int I = X0 + x, J = Y0 + y, K = Z0 + z;
 #pragma unroll
         for (int dz = 0; dz < 2; ++dz)
 #pragma unroll
@@ -834,18 +953,30 @@ static void vcycle(Exec* ctx, std::vector<Level<T>>& lv, int l, const T* F0, T f
         uint32_t* co = sizeof(T) == 4 ? C.coef : nullptr;
         float* go = (sizeof(T) == 4 && co) ? reinterpret_cast<float*>(C.gap) : nullptr;
         const float lsn = c.kap != 0.0 ? (float)(0.75 * c.nu * (1.0 - c.eta) / c.kap) : 0.f;  // L_sat
-        k_fas_rhs<T, true><<<gc, kThreads, 0, ctx->stream>>>(C.u[0], C.r, C.kmask, C.bg, C.n, ih2c, (T)c.nu,
-                                                             (T)c.kap, C.f, co, go, lsn, gmp);
+        if (C.n >= 32)
+            k_fas_rhs_tile<T, true><<<dim3(C.n / 32, C.n / 4, C.n / 4), 256, 0, ctx->stream>>>(
+                C.u[0], C.r, C.kmask, C.bg, C.n, ih2c, (T)c.nu, (T)c.kap, C.f, co, go, lsn, gmp);
+        else
+            k_fas_rhs<T, true><<<gc, kThreads, 0, ctx->stream>>>(C.u[0], C.r, C.kmask, C.bg, C.n, ih2c, (T)c.nu,
+                                                                 (T)c.kap, C.f, co, go, lsn, gmp);
         ctx->end();
     } else {
         ctx->begin(PM_K_TRANSFER, false, 0);
-        k_fas_rhs<T, false><<<gc, kThreads, 0, ctx->stream>>>(C.u[0], C.r, C.kmask, nullptr, C.n, ih2c, (T)c.nu,
-                                                              (T)c.kap, C.f, nullptr, nullptr, 0.f, gmp);
+        if (C.n >= 32)
+            k_fas_rhs_tile<T, false><<<dim3(C.n / 32, C.n / 4, C.n / 4), 256, 0, ctx->stream>>>(
+                C.u[0], C.r, C.kmask, nullptr, C.n, ih2c, (T)c.nu, (T)c.kap, C.f, nullptr, nullptr, 0.f, gmp);
+        else
+            k_fas_rhs<T, false><<<gc, kThreads, 0, ctx->stream>>>(C.u[0], C.r, C.kmask, nullptr, C.n, ih2c, (T)c.nu,
+                                                                  (T)c.kap, C.f, nullptr, nullptr, 0.f, gmp);
         ctx->end();
     }
     vcycle(ctx, lv, l + 1, F0, fs0, lam0, c);
     ctx->begin(PM_K_TRANSFER, false, 0);
-    k_prolong_add<T><<<grid_for(ctx, C.cells), kThreads, 0, ctx->stream>>>(C.u[C.cur], C.ur, C.n, L.u[L.cur]);
+    if (C.n >= 32)
+        k_prolong_add_tile<T><<<dim3(C.n / 32, C.n / 4, C.n / 4), 256, 0, ctx->stream>>>(C.u[C.cur], C.ur, C.n,
+                                                                                          L.u[L.cur]);
+    else
+        k_prolong_add<T><<<grid_for(ctx, C.cells), kThreads, 0, ctx->stream>>>(C.u[C.cur], C.ur, C.n, L.u[L.cur]);
     ctx->end();
     for (int s = 0; s < ctx->prm.npost; ++s) sweep(ctx, L, F, fs, lam, c);
 }
@@ -1233,7 +1364,11 @@ extern "C" pm_status pm_mg_prolong_add(pm_ctx* ctx, const double* coarse, int n,
     if (!fine || !coarse) return PM_ERR_INVALID_ARG;
     const int nc = n / 2;
     ctx->begin(PM_K_TRANSFER, false, 0);
-    k_prolong_add<double><<<grid_for(ctx, (size_t)nc * nc * nc), kThreads, 0, ctx->stream>>>(coarse, nullptr, nc, fine);
+    if (nc >= 32)  // the tiled kernel of the V-cycle from 32^3 coarse cells up
+        k_prolong_add_tile<double><<<dim3(nc / 32, nc / 4, nc / 4), 256, 0, ctx->stream>>>(coarse, nullptr, nc, fine);
+    else
+        k_prolong_add<double><<<grid_for(ctx, (size_t)nc * nc * nc), kThreads, 0, ctx->stream>>>(coarse, nullptr, nc,
+                                                                                                fine);
     ctx->end();
     PM_CUDA(cudaGetLastError());
     return PM_OK;

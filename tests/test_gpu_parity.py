@@ -136,10 +136,12 @@ def test_residual_matches_oracle(gpu_lib):
     assert np.abs(r_g - r_o)[same].max() <= 1e-10 * np.abs(r_o).max()
 
 
-def test_transfers_match_oracle(gpu_lib):
+@pytest.mark.parametrize("n", [32, 64, 128])
+def test_transfers_match_oracle(gpu_lib, n):
+    """Restriction and prolongation (the tiled prolongation from 32^3 coarse cells up)."""
     rng = np.random.default_rng(4)
-    fine = rng.standard_normal((32, 32, 32))
-    coarse = rng.standard_normal((16, 16, 16))
+    fine = rng.standard_normal((n, n, n))
+    coarse = rng.standard_normal((n // 2, n // 2, n // 2))
     assert np.abs(gpu_lib.pm_mg_restrict(cu(fine)).cpu().numpy() - O.restrict(fine)).max() < 1e-15
     got = gpu_lib.pm_mg_prolong_add(cu(coarse), cu(fine)).cpu().numpy()
     assert np.abs(got - O.prolong_add(coarse, fine)).max() < 1e-14
