@@ -459,30 +459,33 @@ __global__ void __launch_bounds__(256) k_prolong_add_tile(const T* __restrict__ 
 
 // ------------------------------------------------------------------ coarsest level
 
-// Exact-enough solve of the coarsest level (at most 8^3 cells) in one thread block, in
-// FP64 whatever the storage type: `sweeps` red-black sweeps, each followed by the gauge
-// update lambda -= sum r / #unfloored.
+// Exact-enough solve of the coarsest level (at most 8^3 cells) in one thread block, in the
+// storage type's arithmetic (FP64 for the FP64 cycle, FP32 inside the FP32 inner cycle):
+// `sweeps` red-black sweeps, each followed by the gauge update lambda -= sum r / #unfloored.
+// The block sums go through warp shuffles and one exchange between the warps.
 template <typename T, bool BG>
 __global__ void __launch_bounds__(256) k_coarsest(T* __restrict__ u, const T* __restrict__ F, T fscale,
                                                   const uint8_t* __restrict__ kmask, const T* __restrict__ bg, int n,
-                                                  double ih2, double nu, double kap, double eta, int sweeps,
+                                                  double ih2_d, double nu_d, double kap_d, double eta, int sweeps,
                                                   bool floor_piece)
 {
-    __shared__ double su[512], ss[512], sf[512], sb[512];
+    __shared__ T su[512], ss[512], sf[512], sb[512];
     __shared__ uint8_t sk[512];
-    __shared__ double red[2][256];
-    const int cells = n * n * n, t = threadIdx.x;
+    __shared__ T red[2][8];
+    const int cells = n * n * n, t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const T ih2 = (T)ih2_d, nu = (T)nu_d, kap = (T)kap_d;
     for (int c = t; c < cells; c += blockDim.x) {
-        su[c] = (double)u[c];
-        sf[c] = (double)fscale * (double)F[c];
+        su[c] = u[c];
+        sf[c] = fscale * F[c];
         sk[c] = kmask ? kmask[c] : 0;
-        sb[c] = BG ? (double)bg[c] : 0.0;
+        sb[c] = BG ? bg[c] : T(0);
     }
     __syncthreads();
-    const double sp = nu >= 0.0 ? -1.0 : 1.0;
-    const double sqDf = eta * 6.0 * fabs(nu) * ih2, Df = sqDf * sqDf;
-    const double lsat_c = kap != 0.0 ? 0.75 * nu * (1.0 - eta) / kap : 0.0;  // L_sat
-    double lam = 0.0;
+    const T sp = nu >= T(0) ? T(-1) : T(1);
+    const double sqDf = eta * 6.0 * fabs(nu_d) * ih2_d;
+    const T Df = (T)(sqDf * sqDf);
+    const T lsat_c = kap != T(0) ? (T)(0.75 * nu_d * (1.0 - eta) / kap_d) : T(0);  // L_sat
+    T lam = T(0);
     for (int it = 0; it < sweeps; ++it) {
         for (int colour = 0; colour < 2; ++colour) {
             for (int c = t; c < cells; c += blockDim.x) ss[c] = su[c];
@@ -490,44 +493,48 @@ __global__ void __launch_bounds__(256) k_coarsest(T* __restrict__ u, const T* __
             for (int c = t; c < cells; c += blockDim.x) {
                 const int i = c % n, j = (c / n) % n, k = c / (n * n);
                 if (((i + j + k) & 1) != colour) continue;
-                Stencil<double> s = load_stencil<double>(ss, ss, i, j, k, n);
-                Stencil<double> b;
-                if (BG) b = load_stencil<double>(sb, sb, i, j, k, n);
-                const double w = sk[c] >= 8 ? 0.0 : (8 - sk[c]) * 0.125;
-                const double kc = kap * w;
-                Local<double> o = local_eval<double, BG>(s, b, ih2, nu, kc, sf[c] + lam, kc != 0.0 ? lsat_c / w : 0.0);
+                Stencil<T> s = load_stencil<T>(ss, ss, i, j, k, n);
+                Stencil<T> b;
+                if (BG) b = load_stencil<T>(sb, sb, i, j, k, n);
+                const T w = sk[c] >= 8 ? T(0) : (T)(8 - sk[c]) * T(0.125);
+                const T kc = kap * w;
+                Local<T> o = local_eval<T, BG>(s, b, ih2, nu, kc, sf[c] + lam, kc != T(0) ? lsat_c / w : T(0));
                 su[c] = s.c0 + local_update(o, sp, Df, ih2);
             }
             __syncthreads();
         }
         // gauge update from the residual
-        double a0 = 0.0, a1 = 0.0;
+        T a0 = T(0), a1 = T(0);
         for (int c = t; c < cells; c += blockDim.x) {
             const int i = c % n, j = (c / n) % n, k = c / (n * n);
-            Stencil<double> s = load_stencil<double>(su, su, i, j, k, n);
-            Stencil<double> b;
-            if (BG) b = load_stencil<double>(sb, sb, i, j, k, n);
-            const double w = sk[c] >= 8 ? 0.0 : (8 - sk[c]) * 0.125;
-            const double kc = kap * w;
-            Local<double> o = local_eval<double, BG>(s, b, ih2, nu, kc, sf[c] + lam, kc != 0.0 ? lsat_c / w : 0.0);
-            const bool fl = floor_piece && (o.P != 0.0) && (o.D < Df);
+            Stencil<T> s = load_stencil<T>(su, su, i, j, k, n);
+            Stencil<T> b;
+            if (BG) b = load_stencil<T>(sb, sb, i, j, k, n);
+            const T w = sk[c] >= 8 ? T(0) : (T)(8 - sk[c]) * T(0.125);
+            const T kc = kap * w;
+            Local<T> o = local_eval<T, BG>(s, b, ih2, nu, kc, sf[c] + lam, kc != T(0) ? lsat_c / w : T(0));
+            const bool fl = floor_piece && (o.P != T(0)) && (o.D < Df);
             a0 += fl ? nu * o.g : -o.G;
-            a1 += fl ? 0.0 : 1.0;
+            a1 += fl ? T(0) : T(1);
         }
-        red[0][t] = a0;
-        red[1][t] = a1;
+        for (int o = 16; o > 0; o >>= 1) {
+            a0 += __shfl_down_sync(0xffffffffu, a0, o);
+            a1 += __shfl_down_sync(0xffffffffu, a1, o);
+        }
+        if (lane == 0) {
+            red[0][wid] = a0;
+            red[1][wid] = a1;
+        }
         __syncthreads();
-        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-            if (t < w) {
-                red[0][t] += red[0][t + w];
-                red[1][t] += red[1][t + w];
-            }
-            __syncthreads();
+        T s0 = T(0), s1 = T(0);
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {  // every thread, the same order
+            s0 += red[0][q];
+            s1 += red[1][q];
         }
-        if (red[1][0] > 0.0) lam -= red[0][0] / red[1][0];
+        if (s1 > T(0)) lam -= s0 / s1;
         __syncthreads();
     }
-    for (int c = t; c < cells; c += blockDim.x) u[c] = (T)su[c];
+    for (int c = t; c < cells; c += blockDim.x) u[c] = su[c];
 }
 
 // ------------------------------------------------------------------ misc
