@@ -42,7 +42,10 @@ struct BoxRun {
 static pm_status box_prepare(pm_ctx* ctx, Workspace* w)
 {
     if (!w->stream) PM_CUDA(cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking));
-    if (!w->partials) PM_CUDA(cudaMalloc(&w->partials, sizeof(double) * kMaxPartials * 8));
+    if (!w->partials) {
+        PM_CUDA(cudaMalloc(&w->partials, sizeof(double) * (kMaxPartials * 8 + 8)));
+        PM_CUDA(cudaMemset(w->partials, 0, sizeof(double) * (kMaxPartials * 8 + 8)));  // with the launch counter
+    }
     if (!w->out) PM_CUDA(cudaMalloc(&w->out, sizeof(double) * 64));
     if (!w->host) PM_CUDA(cudaMallocHost(&w->host, sizeof(double) * 64));
     if (!w->lam) PM_CUDA(cudaMalloc(&w->lam, sizeof(double)));

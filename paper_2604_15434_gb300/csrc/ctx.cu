@@ -229,7 +229,7 @@ extern "C" pm_status pm_create(pm_ctx** out, int device, void* stream, const pm_
         return PM_ERR_CUDA;
     }
     cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
-    if (cudaMalloc(&ctx->red_partials, sizeof(double) * kMaxPartials * 8) != cudaSuccess ||
+    if (cudaMalloc(&ctx->red_partials, sizeof(double) * (kMaxPartials * 8 + 8)) != cudaSuccess ||
         cudaMalloc(&ctx->red_out, sizeof(double) * 64) != cudaSuccess ||
         cudaMalloc(&ctx->flag, sizeof(int) * 4) != cudaSuccess ||
         cudaMallocHost(&ctx->host_out, sizeof(double) * 64) != cudaSuccess) {
@@ -237,7 +237,7 @@ extern "C" pm_status pm_create(pm_ctx** out, int device, void* stream, const pm_
         return PM_ERR_OOM;
     }
     cudaMemset(ctx->flag, 0, sizeof(int) * 4);
-    cudaMemset(ctx->red_partials, 0, sizeof(double) * kMaxPartials * 8);
+    cudaMemset(ctx->red_partials, 0, sizeof(double) * (kMaxPartials * 8 + 8));  // partials and their counter
     cudaMemset(ctx->red_out, 0, sizeof(double) * 64);
     *out = ctx;
     return PM_OK;

@@ -46,10 +46,23 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// The launch counter of a partials buffer: one unsigned after its kMaxPartials * 8 doubles
+// (allocated with them, zero between launches).
+__device__ __forceinline__ unsigned* partials_counter(double* partials)
+{
+    return reinterpret_cast<unsigned*>(partials + (size_t)kMaxPartials * 8);
+}
+
+// The block's NV sums into partials[block * 8 + q].  fin_out (nullable): the block that
+// finishes last (ticket from the partials counter, after a fence on every block's writes)
+// also sums all blocks' partials, in a fixed order, into fin_out[0..7] and the gauge shift
+// fin_out[8] = sum r / count unfloored, and resets the counter, with no second launch.
 template <int NV>
-__device__ __forceinline__ void block_sums(double (&v)[NV], double* partials, unsigned block)
+__device__ __forceinline__ void block_sums(double (&v)[NV], double* partials, unsigned block,
+                                           double* fin_out = nullptr)
 {
     __shared__ double sh[NV][32];
+    __shared__ bool last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
@@ -65,12 +78,44 @@ __device__ __forceinline__ void block_sums(double (&v)[NV], double* partials, un
             if (lane == 0) partials[(size_t)block * 8 + q] = s;
         }
     }
+    if (!fin_out) return;
+    const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(partials_counter(partials), 1u) == nblocks - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    __shared__ double fs[8][32];
+    double acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+    for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] += __ldcg(partials + (size_t)b * 8 + q);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const double s = warp_sum(acc[q]);
+        if (lane == 0) fs[q][wid] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot[8];
+        for (int q = 0; q < 8; ++q) {
+            tot[q] = 0.0;
+            for (int w = 0; w < nw; ++w) tot[q] += fs[q][w];
+            fin_out[q] = tot[q];
+        }
+        fin_out[8] = tot[3] > 0.0 ? tot[0] / tot[3] : 0.0;
+        *partials_counter(partials) = 0u;
+    }
 }
 
 template <int NV>
-__device__ __forceinline__ void block_sums(double (&v)[NV], double* partials)
+__device__ __forceinline__ void block_sums(double (&v)[NV], double* partials, double* fin_out = nullptr)
 {
-    block_sums<NV>(v, partials, blockIdx.x);
+    block_sums<NV>(v, partials, blockIdx.x, fin_out);
 }
 
 // Screening weight of a cell from its mask byte k: the cell keeps (8 - k)/8 of kappa,

@@ -23,29 +23,6 @@ namespace pmeft {
 
 // ------------------------------------------------------------------ reductions
 
-// Sum the per-block partials in a fixed order (deterministic), and derive the gauge
-// shift gm = sum r / count unfloored.  out[0..7] sums, out[8] gm.
-__global__ void k_finalize(const double* __restrict__ partials, int nblocks, double* __restrict__ out)
-{
-    __shared__ double sh[8][256];
-    const int t = threadIdx.x;
-    for (int q = 0; q < 8; ++q) {
-        double s = 0.0;
-        for (int b = t; b < nblocks; b += blockDim.x) s += partials[(size_t)b * 8 + q];
-        sh[q][t] = s;
-    }
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (t < w)
-            for (int q = 0; q < 8; ++q) sh[q][t] += sh[q][t + w];
-        __syncthreads();
-    }
-    if (t == 0) {
-        for (int q = 0; q < 8; ++q) out[q] = sh[q][0];
-        out[8] = sh[3][0] > 0.0 ? sh[0][0] / sh[3][0] : 0.0;
-    }
-}
-
 // ------------------------------------------------------------------ smoother
 
 // Method II, operator splitting (Sec. 3.2.2, Eq. opsplit): the cell's equation
@@ -131,7 +108,7 @@ __global__ void __launch_bounds__(256) k_residual(const T* __restrict__ u, const
                                                   uint8_t* __restrict__ sat,
                                                   double* __restrict__ partials, float* __restrict__ rplain,
                                                   float* __restrict__ chi32, float* __restrict__ gap32,
-                                                  const T* __restrict__ lamp)
+                                                  const T* __restrict__ lamp, double* __restrict__ fin_out = nullptr)
 {
     if (lamp) lam += *lamp;
     float fa[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
@@ -178,7 +155,7 @@ __global__ void __launch_bounds__(256) k_residual(const T* __restrict__ u, const
     double acc[5];
 #pragma unroll
     for (int q = 0; q < 5; ++q) acc[q] = (double)fa[q];
-    block_sums<5>(acc, partials);
+    block_sums<5>(acc, partials, fin_out);
 }
 
 // ------------------------------------------------------------------ transfers
@@ -540,7 +517,8 @@ __global__ void __launch_bounds__(256) k_coarsest(T* __restrict__ u, const T* __
 // ------------------------------------------------------------------ misc
 
 template <typename T>
-__global__ void k_sum(const T* __restrict__ x, size_t total, double* __restrict__ partials)
+__global__ void k_sum(const T* __restrict__ x, size_t total, double* __restrict__ partials,
+                      double* __restrict__ fin_out = nullptr)
 {
     double v[2] = {0.0, 0.0};
     const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
@@ -568,12 +546,12 @@ __global__ void k_sum(const T* __restrict__ x, size_t total, double* __restrict_
             v[1] += d * d;
         }
     }
-    block_sums<2>(v, partials);
+    block_sums<2>(v, partials, fin_out);
 }
 
 // sum of (x - mean)^2 with the mean read from the device
 __global__ void k_sum_centred(const double* __restrict__ x, size_t total, const double* __restrict__ sums,
-                              double* __restrict__ partials)
+                              double* __restrict__ partials, double* __restrict__ fin_out = nullptr)
 {
     const double mean = sums[0] / (double)total;
     double v[1] = {0.0};
@@ -581,7 +559,7 @@ __global__ void k_sum_centred(const double* __restrict__ x, size_t total, const 
         const double d = x[c] - mean;
         v[0] += d * d;
     }
-    block_sums<1>(v, partials);
+    block_sums<1>(v, partials, fin_out);
 }
 
 template <typename T>
@@ -834,23 +812,23 @@ static int residual(Exec* ctx, Level<T>& L, const T* u, const T* F, T fscale, T 
                 constexpr size_t sm = resid_zm_smem_bytes<true, true>();
                 k_residual_zm<true, true><<<g3, 256, sm, ctx->stream>>>(
                     u, F, fscale, lam, L.kmask, L.bg, L.gap, n, nz, h2inv, (T)c.nu, (T)c.kap, (T)(sqDf * sqDf), lsn,
-                    L.fine, L.r, L.sat, ctx->red_partials, L.lamp, L.coef);
+                    L.fine, L.r, L.sat, ctx->red_partials, L.lamp, L.coef, nullptr, nullptr, nullptr, nullptr,
+                    ctx->red_out);
             } else if (L.bg) {
                 constexpr size_t sm = resid_zm_smem_bytes<true>();
                 k_residual_zm<true><<<g3, 256, sm, ctx->stream>>>(u, F, fscale, lam, L.kmask, L.bg, L.gap, n, nz,
                                                                   h2inv, (T)c.nu, (T)c.kap, (T)(sqDf * sqDf), lsn,
                                                                   L.fine, L.r, L.sat, ctx->red_partials, L.lamp,
-                                                                  nullptr);
+                                                                  nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                                  ctx->red_out);
             } else {
                 constexpr size_t sm = resid_zm_smem_bytes<false>();
                 k_residual_zm<false><<<g3, 256, sm, ctx->stream>>>(u, F, fscale, lam, L.kmask, nullptr, nullptr, n, nz,
                                                                    h2inv, (T)c.nu, (T)c.kap, (T)(sqDf * sqDf), lsn,
                                                                    L.fine, L.r, L.sat, ctx->red_partials, L.lamp,
-                                                                   nullptr);
+                                                                   nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                                   ctx->red_out);
             }
-            ctx->end();
-            ctx->begin(PM_K_REDUCE, false, 0);
-            k_finalize<<<1, 256, 0, ctx->stream>>>(ctx->red_partials, nb, ctx->red_out);
             ctx->end();
             return nb;
         }
@@ -859,18 +837,15 @@ static int residual(Exec* ctx, Level<T>& L, const T* u, const T* F, T fscale, T 
         ctx->begin(sizeof(T) == 8 ? PM_K_RESID64 : PM_K_RESID32, L.fine, (long long)L.cells);
         k_residual<T, true, WRITE_R, MIXED><<<grid, kThreads, 0, ctx->stream>>>(
             u, F, fscale, lam, L.kmask, L.bg, L.gap, n, h2inv, (T)c.nu, (T)c.kap, (T)(sqDf * sqDf), lsn, L.fine, L.r,
-            L.sat, ctx->red_partials, rplain, chi32, gap32, L.lamp);
+            L.sat, ctx->red_partials, rplain, chi32, gap32, L.lamp, ctx->red_out);
         ctx->end();
     } else {
         ctx->begin(sizeof(T) == 8 ? PM_K_RESID64 : PM_K_RESID32, L.fine, (long long)L.cells);
         k_residual<T, false, WRITE_R, MIXED><<<grid, kThreads, 0, ctx->stream>>>(
             u, F, fscale, lam, L.kmask, nullptr, nullptr, n, h2inv, (T)c.nu, (T)c.kap, (T)(sqDf * sqDf), lsn, L.fine,
-            L.r, L.sat, ctx->red_partials, rplain, chi32, gap32, L.lamp);
+            L.r, L.sat, ctx->red_partials, rplain, chi32, gap32, L.lamp, ctx->red_out);
         ctx->end();
     }
-    ctx->begin(PM_K_REDUCE, false, 0);
-    k_finalize<<<1, 256, 0, ctx->stream>>>(ctx->red_partials, grid, ctx->red_out);
-    ctx->end();
     return grid;
 }
 
@@ -895,22 +870,19 @@ static bool residual_restrict_f32(Exec* ctx, Level<float>& L, Level<float>& C, c
         constexpr size_t sm = resid_zm_smem_bytes<true, true>();
         k_residual_zm<true, true, true><<<g3, 256, sm, ctx->stream>>>(
             u, F, fscale, lam, L.kmask, L.bg, L.gap, n, nz, h2inv, (float)c.nu, (float)c.kap, (float)(sqDf * sqDf),
-            lsn, L.fine, nullptr, nullptr, ctx->red_partials, L.lamp, L.coef, C.ur, C.u[0], C.r, C.kmask);
+            lsn, L.fine, nullptr, nullptr, ctx->red_partials, L.lamp, L.coef, C.ur, C.u[0], C.r, C.kmask, ctx->red_out);
     } else if (L.bg) {
         constexpr size_t sm = resid_zm_smem_bytes<true>();
         k_residual_zm<true, false, true><<<g3, 256, sm, ctx->stream>>>(
             u, F, fscale, lam, L.kmask, L.bg, L.gap, n, nz, h2inv, (float)c.nu, (float)c.kap, (float)(sqDf * sqDf),
-            lsn, L.fine, nullptr, nullptr, ctx->red_partials, L.lamp, nullptr, C.ur, C.u[0], C.r, C.kmask);
+            lsn, L.fine, nullptr, nullptr, ctx->red_partials, L.lamp, nullptr, C.ur, C.u[0], C.r, C.kmask, ctx->red_out);
     } else {
         constexpr size_t sm = resid_zm_smem_bytes<false>();
         k_residual_zm<false, false, true><<<g3, 256, sm, ctx->stream>>>(
             u, F, fscale, lam, L.kmask, nullptr, nullptr, n, nz, h2inv, (float)c.nu, (float)c.kap,
             (float)(sqDf * sqDf), lsn, L.fine, nullptr, nullptr, ctx->red_partials, L.lamp, nullptr, C.ur, C.u[0],
-            C.r, C.kmask);
+            C.r, C.kmask, ctx->red_out);
     }
-    ctx->end();
-    ctx->begin(PM_K_REDUCE, false, 0);
-    k_finalize<<<1, 256, 0, ctx->stream>>>(ctx->red_partials, nb, ctx->red_out);
     ctx->end();
     return true;
 }
@@ -994,10 +966,7 @@ static void recentre(Exec* ctx, T* x, size_t cells)
     int grid = grid_for(ctx, cells);
     if (grid > kMaxPartials) grid = kMaxPartials;
     ctx->begin(PM_K_REDUCE, false, 0);
-    k_sum<T><<<grid, kThreads, 0, ctx->stream>>>(x, cells, ctx->red_partials);
-    ctx->end();
-    ctx->begin(PM_K_REDUCE, false, 0);
-    k_finalize<<<1, 256, 0, ctx->stream>>>(ctx->red_partials, grid, ctx->red_out + 16);
+    k_sum<T><<<grid, kThreads, 0, ctx->stream>>>(x, cells, ctx->red_partials, ctx->red_out + 16);
     ctx->end();
     ctx->begin(PM_K_REDUCE, false, 0);
     k_sub_mean<T><<<grid_for(ctx, cells), kThreads, 0, ctx->stream>>>(x, cells, ctx->red_out + 16);
@@ -1017,16 +986,11 @@ static pm_status source_norm(Exec* ctx, const double* delta, size_t cells, doubl
     int grid = grid_for(ctx, cells);
     if (grid > kMaxPartials) grid = kMaxPartials;
     ctx->begin(PM_K_REDUCE, false, 0);
-    k_sum<double><<<grid, kThreads, 0, ctx->stream>>>(delta, cells, ctx->red_partials);
+    k_sum<double><<<grid, kThreads, 0, ctx->stream>>>(delta, cells, ctx->red_partials, ctx->red_out + 32);
     ctx->end();
     ctx->begin(PM_K_REDUCE, false, 0);
-    k_finalize<<<1, 256, 0, ctx->stream>>>(ctx->red_partials, grid, ctx->red_out + 32);
-    ctx->end();
-    ctx->begin(PM_K_REDUCE, false, 0);
-    k_sum_centred<<<grid, kThreads, 0, ctx->stream>>>(delta, cells, ctx->red_out + 32, ctx->red_partials);
-    ctx->end();
-    ctx->begin(PM_K_REDUCE, false, 0);
-    k_finalize<<<1, 256, 0, ctx->stream>>>(ctx->red_partials, grid, ctx->red_out + 48);
+    k_sum_centred<<<grid, kThreads, 0, ctx->stream>>>(delta, cells, ctx->red_out + 32, ctx->red_partials,
+                                                       ctx->red_out + 48);
     ctx->end();
     PM_CUDA(cudaMemcpyAsync(ctx->host_out, ctx->red_out + 48, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     PM_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -1053,18 +1017,15 @@ static void residual_ff(Exec* ctx, Workspace* w, const float2* xff, const float2
         if (e)
             k_residual_ff_zm<true><<<g3, 256, kFzSmemCorr, ctx->stream>>>(
                 xff, fff, lam, lamp, n, nz, fk, w->rplain, w->s[0].bg, w->s[0].gap, w->s[0].coef,
-                ctx->red_partials, e, ctx->red_out + 16, xout);
+                ctx->red_partials, e, ctx->red_out + 16, xout, ctx->red_out);
         else
             k_residual_ff_zm<false><<<g3, 256, kFzSmem, ctx->stream>>>(
                 xff, fff, lam, lamp, n, nz, fk, w->rplain, w->s[0].bg, w->s[0].gap, w->s[0].coef,
-                ctx->red_partials, nullptr, nullptr, nullptr);
+                ctx->red_partials, nullptr, nullptr, nullptr, ctx->red_out);
     } else {
         k_residual_ff<<<grid, kThreads, 0, ctx->stream>>>(xff, fff, lam, lamp, n, fk, w->rplain, w->s[0].bg,
-                                                          w->s[0].gap, ctx->red_partials);
+                                                          w->s[0].gap, ctx->red_partials, ctx->red_out);
     }
-    ctx->end();
-    ctx->begin(PM_K_REDUCE, false, 0);
-    k_finalize<<<1, 256, 0, ctx->stream>>>(ctx->red_partials, grid, ctx->red_out);
     ctx->end();
 }
 
@@ -1074,10 +1035,7 @@ static void correction_sum(Exec* ctx, const float* e, size_t cells)
     int grid = grid_for(ctx, cells);
     if (grid > kMaxPartials) grid = kMaxPartials;
     ctx->begin(PM_K_REDUCE, false, 0);
-    k_sum<float><<<grid, kThreads, 0, ctx->stream>>>(e, cells, ctx->red_partials);
-    ctx->end();
-    ctx->begin(PM_K_REDUCE, false, 0);
-    k_finalize<<<1, 256, 0, ctx->stream>>>(ctx->red_partials, grid, ctx->red_out + 16);
+    k_sum<float><<<grid, kThreads, 0, ctx->stream>>>(e, cells, ctx->red_partials, ctx->red_out + 16);
     ctx->end();
 }
 

@@ -148,7 +148,8 @@ __global__ void k_add_correction_ff(float2* __restrict__ x, const float* __restr
 __global__ void __launch_bounds__(256) k_residual_ff(const float2* __restrict__ U, const float2* __restrict__ F,
                                                      double lam_host, const double* __restrict__ lamp, int n,
                                                      FFCoef k, float* __restrict__ rplain, float* __restrict__ chi32,
-                                                     float* __restrict__ gap32, double* __restrict__ partials)
+                                                     float* __restrict__ gap32, double* __restrict__ partials,
+                                                     double* __restrict__ fin_out = nullptr)
 {
     const double lam_d = lam_host + (lamp ? *lamp : 0.0);
     const ff lam = ff_from_double(lam_d);
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(256) k_residual_ff(const float2* __restrict__ 
     double acc[5];
 #pragma unroll
     for (int q = 0; q < 5; ++q) acc[q] = (double)fa[q];
-    block_sums<5>(acc, partials);
+    block_sums<5>(acc, partials, fin_out);
 }
 
 
@@ -338,7 +339,7 @@ __global__ void __launch_bounds__(256, 3) k_residual_ff_zm(const float2* __restr
                                                         float* __restrict__ chi32, float* __restrict__ gap32,
                                                         uint32_t* __restrict__ coef, double* __restrict__ partials,
                                                         const float* __restrict__ E, const double* __restrict__ esum,
-                                                        float2* __restrict__ Uout)
+                                                        float2* __restrict__ Uout, double* __restrict__ fin_out = nullptr)
 {
     const ff lam1 = ff_from_double(lam_host + (lamp ? *lamp : 0.0));
     const ff2 lam = ff2_splat(lam1);
@@ -544,7 +545,7 @@ __global__ void __launch_bounds__(256, 3) k_residual_ff_zm(const float2* __restr
     double acc[5];
 #pragma unroll
     for (int q = 0; q < 5; ++q) acc[q] = (double)fa[q];
-    block_sums<5>(acc, partials, (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
+    block_sums<5>(acc, partials, (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x, fin_out);
 }
 
 }  // namespace pmeft

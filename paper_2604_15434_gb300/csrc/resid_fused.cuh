@@ -40,7 +40,8 @@ __global__ void __launch_bounds__(256) k_residual_zm(const float* __restrict__ u
                                                      uint8_t* __restrict__ sat, double* __restrict__ partials,
                                                      const float* __restrict__ lamp, const uint32_t* __restrict__ coef,
                                                      float* __restrict__ urc = nullptr, float* __restrict__ ucc = nullptr,
-                                                     float* __restrict__ rcc = nullptr, uint8_t* __restrict__ kmc = nullptr)
+                                                     float* __restrict__ rcc = nullptr, uint8_t* __restrict__ kmc = nullptr,
+                                                     double* __restrict__ fin_out = nullptr)
 {
     constexpr bool BGRING = BG && !COEF;
     if (lamp) lam += *lamp;
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(256) k_residual_zm(const float* __restrict__ u
     double acc[5];
 #pragma unroll
     for (int q = 0; q < 5; ++q) acc[q] = (double)fa[q];
-    block_sums<5>(acc, partials, (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
+    block_sums<5>(acc, partials, (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x, fin_out);
 }
 
 }  // namespace pmeft
