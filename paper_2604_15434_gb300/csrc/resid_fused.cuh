@@ -8,7 +8,7 @@
 // read from DRAM once, the halos from L2.
 #pragma once
 
-#include "sweep_fused.cuh"
+#include "sweep_pair.cuh"
 
 namespace pmeft {
 
@@ -80,17 +80,6 @@ __global__ void __launch_bounds__(256) k_residual_zm(const float* __restrict__ u
     const int x = t & 63, yA = t >> 6;
     const int cs[2] = {(yA + 1) * kRzW + x + 1, (yA + 5) * kRzW + x + 1};
     const int gxy[2] = {(y0 + yA) * n + x0 + x, (y0 + yA + 4) * n + x0 + x};
-    auto stencil = [&](const float* rp, const float* rc, const float* rn, int c) {
-        Stencil<float> s;
-        s.c0 = rc[c];
-        s.ax = rc[c + 1] + rc[c - 1];
-        s.ay = rc[c + kRzW] + rc[c - kRzW];
-        s.az = rn[c] + rp[c];
-        s.exy = rc[c + 1 + kRzW] - rc[c + 1 - kRzW] - rc[c - 1 + kRzW] + rc[c - 1 - kRzW];
-        s.exz = rn[c + 1] - rp[c + 1] - rn[c - 1] + rp[c - 1];
-        s.eyz = rn[c + kRzW] - rp[c + kRzW] - rn[c - kRzW] + rp[c - kRzW];
-        return s;
-    };
     float fa[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     // RESTRICT: per cell h the running sums over the plane pair of iterate, residual,
     // unscreened eighths and unfloored children; xch carries rows y+1 to rows y
@@ -125,26 +114,46 @@ __global__ void __launch_bounds__(256) k_residual_zm(const float* __restrict__ u
         const float* bp = sb + slot(s - 1);
         const float* bc = sb + slot(s);
         const float* bn = sb + slot(s + 1);
+        // both cells of the thread evaluated together on the paired FP32 instructions
+        // (local_eval2 / local_eval2_cf of the pair sweep)
+        auto st2 = [&](const float* rp, const float* rc, const float* rn) {
+            auto at = [&](const float* p, int d) { return make_float2(p[cs[0] + d], p[cs[1] + d]); };
+            constexpr int W = kRzW;
+            Stencil2 q;
+            q.c0 = at(rc, 0);
+            q.ax = f2add(at(rc, 1), at(rc, -1));
+            q.ay = f2add(at(rc, W), at(rc, -W));
+            q.az = f2add(at(rn, 0), at(rp, 0));
+            q.exy = f2add(f2sub(f2sub(at(rc, 1 + W), at(rc, 1 - W)), at(rc, -1 + W)), at(rc, -1 - W));
+            q.exz = f2add(f2sub(f2sub(at(rn, 1), at(rp, 1)), at(rn, -1)), at(rp, -1));
+            q.eyz = f2add(f2sub(f2sub(at(rn, W), at(rp, W)), at(rn, -W)), at(rp, -W));
+            return q;
+        };
+        const Stencil2 a2 = st2(up, uc, un);
+        const float2 kc2 = make_float2(kap * wk[0], kap * wk[1]);
+        const float2 lsat2 = make_float2(kc2.x != 0.f ? lsat_c / wk[0] : 0.f, kc2.y != 0.f ? lsat_c / wk[1] : 0.f);
+        const float2 rhs2 = make_float2(fscale * fv[0] + lam, fscale * fv[1] + lam);
+        const float2 gap2 = make_float2(gv[0], gv[1]);
+        Local2 o2;
+        if (COEF) {
+            o2 = local_eval2_cf(a2, unpack_bg_coef(cw[0][0], cw[0][1], cw[0][2]),
+                                unpack_bg_coef(cw[1][0], cw[1][1], cw[1][2]), ih2, nu, kc2, rhs2, lsat2, gap2);
+        } else {
+            Stencil2 b2;
+            if (BG) b2 = st2(bp, bc, bn);
+            o2 = gap ? local_eval2<BG, true>(a2, b2, ih2, nu, kc2, rhs2, lsat2, gap2)
+                     : local_eval2<BG, false>(a2, b2, ih2, nu, kc2, rhs2, lsat2, gap2);
+        }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            Stencil<float> a = stencil(up, uc, un, cs[h]);
-            const float kc = kap * wk[h];
-            const float lsat = kc != 0.f ? lsat_c / wk[h] : 0.f;
-            Local<float> o;
-            if (COEF) {
-                o = local_eval_cf(a, unpack_bg_coef(cw[h][0], cw[h][1], cw[h][2]), ih2, nu, kc, fscale * fv[h] + lam,
-                                  lsat, gv[h]);
-            } else {
-                Stencil<float> b;
-                if (BG) b = stencil(bp, bc, bn, cs[h]);
-                o = local_eval<float, BG>(a, b, ih2, nu, kc, fscale * fv[h] + lam, lsat, gap != nullptr, gv[h]);
-            }
+            const float oG = h ? o2.G.y : o2.G.x, oP = h ? o2.P.y : o2.P.x, oD = h ? o2.D.y : o2.D.x,
+                        og = h ? o2.g.y : o2.g.x;
             // the floored piece exists on the finest level only (see k_residual)
-            const bool fl = floor_piece && (o.P != 0.f) && (o.D < Df);
-            const float rv = fl ? nu * o.g : -o.G;
+            const bool fl = floor_piece && (oP != 0.f) && (oD < Df);
+            const float rv = fl ? nu * og : -oG;
             if (RESTRICT) {
                 const int kf = kmask ? (kmask[os + gxy[h]] < 8 ? kmask[os + gxy[h]] : 8) : 0;
-                au[h] += a.c0;
+                au[h] += h ? a2.c0.y : a2.c0.x;
                 ar[h] += rv;
                 ac[h] += fl ? 8.f : (float)kf;
                 an[h] += fl ? 0.f : 1.f;
