@@ -107,6 +107,24 @@ def _dist():
     return ws, rank, local
 
 
+def job_step_ms(ms_step, ws, device=None):
+    """The step time of the whole job: the maximum over the ranks (every rank runs the same
+    workload on its own GPU, with no collective on the data path)."""
+    if ws <= 1:
+        return ms_step
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms_step], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ms_step, solves, ws):
+    """ms per 512^3 solve of the whole job: every rank does `solves` solves in ms_step."""
+    return ms_step / (solves * ws)
+
+
 def cpu_baseline(n_sample=128, combo=(-0.5, 0.0), target_n=512):
     """The CPU oracle as it stands, on a bounded sample: one cold-start solve of the same
     recipe at n_sample^3 to 1e-8, extrapolated to target_n^3 by the cell count (multigrid
@@ -380,12 +398,9 @@ def main():
     ctx.trace(False)
     ms_total = e0.elapsed_time(e1)
     ms_step = ms_total / args.steps
-    if ws > 1:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = job_step_ms(ms_step, ws, dev)
     solves = len(COMBOS)
-    value = ms_step / (solves * ws)  # ms per 512^3 solve, whole job
+    value = job_value(ms_step, solves, ws)  # ms per 512^3 solve, whole job
 
     # one more step with every launch traced, outside the timed region: the per-class breakdown
     ctx.trace(True)
