@@ -236,7 +236,8 @@ pm_status pm_unet_zero_grad(pm_unet* net);
 pm_status pm_unet_target(pm_ctx* ctx, const double* chi, int n, double alpha_B0, double alpha_M0, double a,
                          float* T_out);
 /* initial guesses for scalar_mg_solve: the learned one, and the linear solution
- * L chi_0 = (xi / nu)(3/2)(G_eff/G) a Omega_m0 delta that the paper's PySCo-EFT starts from (Sec. 3.5.1) */
+ * L chi_0 = (xi / nu)(3/2)(G_eff/G) a Omega_m0 delta that the paper's PySCo-EFT starts from (Sec. 3.5.1).
+ * Being guesses, both come from an FP32 FFT Poisson solve (relative accuracy ~1e-6); phi_out is FP64. */
 pm_status pm_unet_warm_start(pm_unet* net, const double* delta, int n, double alpha_B0, double alpha_M0, double a,
                              double* phi_out);
 pm_status pm_linear_start(pm_ctx* ctx, const double* delta, int n, double alpha_B0, double alpha_M0, double a,

@@ -144,6 +144,23 @@ pm_status ensure_fft(pm_ctx* ctx, Workspace* w)
     return PM_OK;
 }
 
+pm_status ensure_fft32(pm_ctx* ctx, Workspace* w)
+{
+    if (w->fft32_ready) return PM_OK;
+    const int n = w->n;
+    if (cufftPlan3d(&w->plan_r2c32, n, n, n, CUFFT_R2C) != CUFFT_SUCCESS ||
+        cufftPlan3d(&w->plan_c2r32, n, n, n, CUFFT_C2R) != CUFFT_SUCCESS) {
+        ctx->set_error("cufftPlan3d (FP32) failed");
+        return PM_ERR_CUDA;
+    }
+    cufftSetStream(w->plan_r2c32, ctx->stream);
+    cufftSetStream(w->plan_c2r32, ctx->stream);
+    PM_CUDA(cudaMalloc(&w->spec32, (size_t)n * n * (n / 2 + 1) * sizeof(float2)));
+    PM_CUDA(cudaMalloc(&w->buf32, (size_t)n * n * n * sizeof(float)));
+    w->fft32_ready = true;
+    return PM_OK;
+}
+
 void delete_workspace(Workspace* w)
 {
     if (!w) return;
@@ -157,6 +174,10 @@ void delete_workspace(Workspace* w)
     cudaFree(w->acc);
     cudaFree(w->spec);
     if (w->plan_r2c) cufftDestroy(w->plan_r2c);
+    if (w->plan_r2c32) cufftDestroy(w->plan_r2c32);
+    if (w->plan_c2r32) cufftDestroy(w->plan_c2r32);
+    cudaFree(w->spec32);
+    cudaFree(w->buf32);
     if (w->plan_c2r) cufftDestroy(w->plan_c2r);
     cudaFree(w->partials);
     cudaFree(w->out);

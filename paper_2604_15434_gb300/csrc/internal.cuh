@@ -163,6 +163,10 @@ struct Workspace {
     cufftHandle plan_r2c = 0, plan_c2r = 0;
     double2* spec = nullptr;       // n*n*(n/2+1) complex
     bool fft_ready = false;
+    cufftHandle plan_r2c32 = 0, plan_c2r32 = 0;  // FP32 transforms of the start fields (guesses)
+    float2* spec32 = nullptr;
+    float* buf32 = nullptr;
+    bool fft32_ready = false;
     // own stream, reductions and device scalars of one box of a batched solve
     cudaStream_t stream = nullptr;
     double* partials = nullptr;    // kMaxPartials * 8
@@ -322,6 +326,9 @@ pm_status mg_solve(pm_ctx* ctx, const double* delta, int n, const pm_coeffs& c, 
                    pm_solve_info* info);
 // Poisson (psi_N) and the particle kernels.
 pm_status poisson(pm_ctx* ctx, const double* delta, int n, double fac, double* psi);
+// the same solve through FP32 transforms (for initial guesses); delta and psi FP64
+pm_status poisson32(pm_ctx* ctx, const double* delta, int n, double fac, double* psi);
+pm_status ensure_fft32(pm_ctx* ctx, Workspace* w);
 pm_status deposit(pm_ctx* ctx, const double* pos, long long np, int n, long long* acc);
 pm_status density(pm_ctx* ctx, const long long* acc, int n, long long np, double* delta);
 pm_status interp_force(pm_ctx* ctx, const double* psiN, const double* chi, double xi, int n, const double* pos,

@@ -83,6 +83,43 @@ __global__ void k_green(double2* __restrict__ spec, int n, double fac)
     }
 }
 
+// k_green in FP32 (the start fields' solve): the same eigenvalues, zero mode and 1/n^3
+__global__ void k_green32(float2* __restrict__ spec, int n, float fac)
+{
+    const int nh = n / 2 + 1;
+    const size_t total = (size_t)n * n * nh;
+    const float h2inv = (float)n * (float)n;
+    const float scale = fac / ((float)n * (float)n * (float)n);
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const int mx = (int)(t % nh);
+        const size_t row = t / nh;
+        const int my = (int)(row % n), mz = (int)(row / n);
+        const float sx = sinpif((float)mx / n), sy = sinpif((float)my / n), sz = sinpif((float)mz / n);
+        const float lam = -4.f * h2inv * (sx * sx + sy * sy + sz * sz);
+        float2 v = spec[t];
+        if (t == 0) {
+            v = make_float2(0.f, 0.f);
+        } else {
+            const float g = scale / lam;
+            v.x *= g;
+            v.y *= g;
+        }
+        spec[t] = v;
+    }
+}
+
+__global__ void k_d2f(const double* __restrict__ x, size_t total, float* __restrict__ y)
+{
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x)
+        y[c] = (float)x[c];
+}
+
+__global__ void k_f2d(const float* __restrict__ x, size_t total, double* __restrict__ y)
+{
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x)
+        y[c] = (double)x[c];
+}
+
 // g = -grad(psiN + xi chi) at each particle: for every one of the 8 CIC corners (in the
 // deposit's corner order) the five-point difference (-f+2 + 8 f+1 - 8 f-1 + f-2)/(12 h) per
 // axis, weighted by the corner's CIC weight.  No force grid is written.
@@ -198,6 +235,34 @@ pm_status poisson(pm_ctx* ctx, const double* delta, int n, double fac, double* p
         ctx->set_error("cufftExecZ2D failed");
         return PM_ERR_CUDA;
     }
+    PM_CUDA(cudaGetLastError());
+    return PM_OK;
+}
+
+pm_status poisson32(pm_ctx* ctx, const double* delta, int n, double fac, double* psi)
+{
+    Workspace* w = nullptr;
+    PM_TRY(get_workspace(ctx, n, &w));
+    PM_TRY(ensure_fft32(ctx, w));
+    const size_t cells = (size_t)n * n * n;
+    ctx->begin(PM_K_PM, false, 0);
+    k_d2f<<<grid_for(ctx, cells), kThreads, 0, ctx->stream>>>(delta, cells, w->buf32);
+    ctx->end();
+    ctx->prof.launches[PM_K_PM] += 2;  // the two cuFFT executions (library kernels)
+    if (cufftExecR2C(w->plan_r2c32, (cufftReal*)w->buf32, (cufftComplex*)w->spec32) != CUFFT_SUCCESS) {
+        ctx->set_error("cufftExecR2C failed");
+        return PM_ERR_CUDA;
+    }
+    ctx->begin(PM_K_PM, false, 0);
+    k_green32<<<grid_for(ctx, (size_t)n * n * (n / 2 + 1)), kThreads, 0, ctx->stream>>>(w->spec32, n, (float)fac);
+    ctx->end();
+    if (cufftExecC2R(w->plan_c2r32, (cufftComplex*)w->spec32, (cufftReal*)w->buf32) != CUFFT_SUCCESS) {
+        ctx->set_error("cufftExecC2R failed");
+        return PM_ERR_CUDA;
+    }
+    ctx->begin(PM_K_PM, false, 0);
+    k_f2d<<<grid_for(ctx, cells), kThreads, 0, ctx->stream>>>(w->buf32, cells, psi);
+    ctx->end();
     PM_CUDA(cudaGetLastError());
     return PM_OK;
 }

@@ -735,7 +735,7 @@ extern "C" pm_status pm_unet_warm_start(pm_unet* u, const double* delta, int n, 
     PM_TRY(ensure_acts(u, n, false));
     PM_TRY(unet_forward(u, delta, n, aB0, aM0, a));
     // L chi_0 = (src / nu) T_hat, zero mean
-    return poisson(ctx, u->acts.that, n, cf.src / cf.nu, phi_out);
+    return poisson32(ctx, u->acts.that, n, cf.src / cf.nu, phi_out);
 }
 
 extern "C" pm_status pm_linear_start(pm_ctx* ctx, const double* delta, int n, double aB0, double aM0, double a,
@@ -748,5 +748,5 @@ extern "C" pm_status pm_linear_start(pm_ctx* ctx, const double* delta, int n, do
         PM_CUDA(cudaMemsetAsync(phi_out, 0, (size_t)n * n * n * sizeof(double), ctx->stream));
         return PM_OK;
     }
-    return poisson(ctx, delta, n, cf.src / cf.nu, phi_out);
+    return poisson32(ctx, delta, n, cf.src / cf.nu, phi_out);
 }

@@ -100,7 +100,8 @@ def test_target_and_linear_start(gpu_lib):
     lin = gpu_lib.linear_start(cu(d), -0.5, 0.0, 1.0).cpu().numpy()
     f = O.source(d, c)
     chi_lin, _, st = O.mg_solve(f, c["nu"], 0.0, 1e-13)
-    assert np.linalg.norm(lin - chi_lin) / np.linalg.norm(chi_lin) < 1e-10
+    # the start fields come from an FP32 FFT solve (they are guesses): FP32 accuracy
+    assert np.linalg.norm(lin - chi_lin) / np.linalg.norm(chi_lin) < 2e-6
 
 
 def test_training_reduces_the_loss(gpu_lib):
