@@ -31,9 +31,9 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 COMBOS = [(-2.0, 0.0), (-2.0, 0.5), (-0.5, 0.0), (-0.5, 0.5)]
-# DRAM bytes per cell of one finest-level sweep launch, from the ncu capture summarised in
-# profiles/k_sweep_pair_256.md (dram__bytes_read.sum + dram__bytes_write.sum of one 512^3
-# launch of the coefficient variant over its cells).  It exceeds the 20 algorithmic bytes
+# DRAM bytes per cell of one finest-level sweep launch, from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of one 512^3 launch of the coefficient
+# variant over its cells).  It exceeds the 20 algorithmic bytes
 # by design: the kernel reads 12 bytes of background coefficients in place of the 4-byte
 # background and its 19-point stencil.
 SWEEP_DRAM_BYTES_PER_CELL = 29.7
@@ -459,7 +459,7 @@ def main():
                           "autotuned: " + (tuned[-1].split(": ", 1)[1].split(" (variants")[0] if tuned else "?") + ")", "bound": "hbm",
                 "achieved": ach, "peak": hbm,
                 "unit": "GB/s", "frac": ach / hbm, "traffic": SWEEP_DRAM_BYTES_PER_CELL * cells,
-                "traffic_source": "ncu capture of a 512^3 launch (profiles/k_sweep_pair_256.md)",
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 512^3 launch of this kernel",
                 "peak_source": src, "frac_of_nominal_8000": ach / 8000.0,
                 "bytes_per_launch": bytes_launch, "avg_launch_ms": avg_ms, "launches": fine["fine_launches"]}
     r64 = prof_all["resid64"]

@@ -207,7 +207,7 @@ pm_status pm_run(pm_ctx* ctx, double* pos, double* vel, long long np, int n, dou
  */
 pm_status pm_deposit_cic_static(const double* pos, long long np, int n, double* delta, void* cuda_stream);
 
-/* ---- learned warm start (spec systems pattern; not in the paper) ----
+/* ---- learned warm start (not in the paper) ----
  * A periodic 3D U-Net (3 levels, 16/32/64 channels, 3x3x3 convolutions, ReLU) maps
  * (asinh delta, alpha_B0, alpha_M0, a) to the screened source T = nu L(chi) / src, which is
  * delta where screening is off.  The warm start is chi_0 = (src/nu) L^-1 T_hat (one FFT

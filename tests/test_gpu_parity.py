@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path, called through the C ABI, against the CPU oracle.
 
-Tolerances (the benchmark spec): deposit bit-exact; FP64 chi within 1e-10 relative L2 of the
+Tolerances: deposit bit-exact; FP64 chi within 1e-10 relative L2 of the
 oracle when both are converged to relative residual 1e-13; the mixed-precision path
 reaches the requested residual with chi within 1e-6 relative L2 and forces within 1e-5.
 Single kernels (one sweep, residual, transfers, Poisson, force) are compared to

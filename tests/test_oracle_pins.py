@@ -273,7 +273,7 @@ def _fft_linear_solve(f, nu):
 
 def test_linear_limit_matches_fft_solve():
     """Screening off (kappa = 0): the FAS solve equals the FFT solve of nu L chi = f - <f>
-    to 1e-10 relative (the benchmark spec's first oracle check; Eq. linearised)."""
+    to 1e-10 relative (Eq. linearised)."""
     pos = synth.zeldovich_particles(32, -1.5, 1.0, 1001, nyquist_cutoff=True)
     d = O.density(O.deposit_cic(pos, 32), pos.shape[1])
     c = O.coefficients(-0.5, 0.0, 1.0)
@@ -341,7 +341,7 @@ def _newton_dense(f, nu, kap, eta, chi0):
 
 @pytest.mark.parametrize("amp", [0.5, 3.0])
 def test_fas_matches_dense_newton_8cubed(amp):
-    """The benchmark spec's third oracle check: a full Newton solve of the discrete system on an
+    """A full Newton solve of the discrete system on an
     8^3 grid agrees with the FAS multigrid to 1e-12 (amp = 3 exercises the screening term)."""
     rng = np.random.default_rng(21)
     n = 8
