@@ -510,3 +510,35 @@ def test_trace_select_times_only_the_selected_launches(gpu_lib):
         if k != "sweep32":
             assert v["ms"] == 0.0 and v["fine_ms"] == 0.0
     assert full["resid64"]["ms"] > 0.0
+
+
+# ------------------------------------------------------------------ the benchmark's size
+
+
+@pytest.fixture(scope="module")
+def delta_512():
+    return synth.lognormal_delta(512, -2.0, 1.5, 1003)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("aB0,aM0", [(-2.0, 0.0), (-0.5, 0.5)])
+def test_mixed_solve_512_meets_tolerance_by_oracle_residual(gpu_lib, delta_512, aB0, aM0):
+    """At the benchmark's size and settings (512^3 lognormal, mixed precision, defaults) the
+    FP64 oracle recomputes the residual of the returned chi with the returned lambda: its
+    gauge-projected relative norm meets the 1e-8 stop test, and <chi> = 0."""
+    d = delta_512
+    ctx = gpu_lib.Context(precision=1, max_cycles=100)
+    chi_t, info = gpu_lib.scalar_mg_solve(cu(d), aB0, aM0, 1.0, 1e-8, ctx=ctx)
+    chi = chi_t.cpu().numpy()
+    del chi_t
+    c = O.coefficients(aB0, aM0, 1.0)
+    f = O.source(d, c)
+    r, fl = O.residual(chi, f, info["lambda"], c["nu"], c["kappa"], 0.35)
+    w = fl == 0
+    r -= w * (r.sum() / w.sum())
+    rel = np.linalg.norm(r) / np.linalg.norm(f - f.mean())
+    assert info["rel_res"] <= 1e-8
+    assert rel <= 1.01e-8, rel
+    assert abs(chi.mean()) <= 1e-12 * np.abs(chi).max()
+    if c["nu"] < 0:
+        assert fl.sum() > 0  # the floored branch is part of the checked residual
