@@ -320,7 +320,7 @@ __device__ __forceinline__ ff2 ff2_splat(ff a) { return ff2{p_splat(a.hi), p_spl
 constexpr int kFzTX = 64, kFzTY = 8;
 constexpr int kFzW = kFzTX + 2, kFzP = kFzW * (kFzTY + 2);  // plane region with a 1-cell halo
 constexpr size_t kFzSmem = sizeof(float) * 2 * 4 * kFzP;       // hi and lo, 4 ring slots
-constexpr size_t kFzSmemCorr = sizeof(float) * 3 * 4 * kFzP;   // + the pending correction e
+constexpr size_t kFzSmemCorr = sizeof(float) * 3 * 5 * kFzP;   // + the pending correction e, 5 slots
 
 // The float-float residual of k_residual_ff, z-marching: a block owns a 64 x 8 (x, y) tile
 // and NZ planes; the hi and lo parts of the iterate's planes (tile + 1 halo) arrive in
@@ -347,9 +347,13 @@ __global__ void __launch_bounds__(256, 3) k_residual_ff_zm(const float2* __restr
     const ff2 lsat = ff2_splat(ff{k.lsat_hi, k.lsat_lo}), nu = ff2_splat(ff{k.nu_hi, k.nu_lo});
     const bool screened = k.kap_f != 0.f;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* sh = reinterpret_cast<float*>(smem_raw);  // [4][H][W] hi parts
-    float* sl = sh + 4 * kFzP;                        // [4][H][W] lo parts
-    float* se = sl + 4 * kFzP;                        // [4][H][W] correction (CORR)
+    // ring slots: 4 (planes s-1 .. s+1 read, s+2 arriving); CORR 5 (s+2 being corrected,
+    // s+3 arriving), so that a plane is corrected one step before it is read and the next
+    // step's barrier publishes it
+    constexpr int NSL = CORR ? 5 : 4;
+    float* sh = reinterpret_cast<float*>(smem_raw);  // [NSL][H][W] hi parts
+    float* sl = sh + NSL * kFzP;                      // [NSL][H][W] lo parts
+    float* se = sl + NSL * kFzP;                      // [NSL][H][W] correction (CORR)
     const unsigned sh_s = (unsigned)__cvta_generic_to_shared(sh);
     const unsigned sl_s = (unsigned)__cvta_generic_to_shared(sl);
     const unsigned se_s = (unsigned)__cvta_generic_to_shared(se);
@@ -363,7 +367,7 @@ __global__ void __launch_bounds__(256, 3) k_residual_ff_zm(const float2* __restr
     const int x0 = blockIdx.x * kFzTX, y0 = blockIdx.y * kFzTY, z0 = blockIdx.z * NZ;
     const int t = threadIdx.x;
     const size_t plane = (size_t)n * n;
-    auto slot = [&](int p) { return ((p - z0 + 4) & 3) * kFzP; };  // p >= z0 - 1
+    auto slot = [&](int p) { return ((p - z0 + 1) % NSL) * kFzP; };  // p >= z0 - 1
     constexpr int K = (kFzP + 255) / 256;
     int off[K];
 #pragma unroll
@@ -423,20 +427,29 @@ __global__ void __launch_bounds__(256, 3) k_residual_ff_zm(const float2* __restr
     issue(z0 - 1);
     issue(z0);
     issue(z0 + 1);
+    if (CORR) {
+        // each thread corrects the elements it copied itself (no barrier needed for that)
+        issue(z0 + 2);  // NZ >= 2
+        cp_async_wait_all();
+        correct(z0 - 1);
+        correct(z0);
+        correct(z0 + 1);
+        correct(z0 + 2);
+    }
     for (int s = z0; s < z0 + NZ; ++s) {
         const size_t os = (size_t)s * plane;  // s is inside [0, n)
         const float2 fA = F[os + gA], fB = F[os + gB];
-        cp_async_wait_all();  // planes up to s+1
-        __syncthreads();
-        if (s + 2 <= z0 + NZ) issue(s + 2);  // its slot held plane s-2, no longer read
         if (CORR) {
-            // each thread corrects the elements it copied itself, then all see the result
-            if (s == z0) {
-                correct(z0 - 1);
-                correct(z0);
+            if (s > z0) {
+                cp_async_wait_all();  // plane s+2, issued during the previous step
+                if (s + 2 <= z0 + NZ) correct(s + 2);
             }
-            correct(s + 1);
+            __syncthreads();  // planes up to s+2 corrected and visible; step s-1 done
+            if (s + 3 <= z0 + NZ) issue(s + 3);  // its slot held plane s-2, no longer read
+        } else {
+            cp_async_wait_all();  // planes up to s+1
             __syncthreads();
+            if (s + 2 <= z0 + NZ) issue(s + 2);  // its slot held plane s-2, no longer read
         }
         const int bp = slot(s - 1), bc = slot(s), bn = slot(s + 1);
         constexpr int W = kFzW;
