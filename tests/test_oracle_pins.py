@@ -216,6 +216,50 @@ def test_method_ii_fas_solve_matches_method_i():
     assert np.abs(chi1 - chi2).max() <= 1e-10 * np.abs(chi1).max()
 
 
+def test_restriction_keeps_block_constants_and_the_mean():
+    """R-mg restriction: a field constant on every 2x2x2 block restricts to those constants,
+    and any field keeps its mean."""
+    rng = np.random.default_rng(12)
+    nc = 8
+    blocks = rng.standard_normal((nc, nc, nc))
+    fine = np.repeat(np.repeat(np.repeat(blocks, 2, 0), 2, 1), 2, 2)
+    assert np.allclose(O.restrict(fine), blocks, rtol=1e-15, atol=1e-15)  # 8 equal terms summed, then / 8
+    u = rng.standard_normal((16, 16, 16))
+    assert abs(O.restrict(u).mean() - u.mean()) < 1e-15
+
+
+def _centres(n):
+    x = (np.arange(n) + 0.5) / n
+    return np.meshgrid(x, x, x, indexing="ij")
+
+
+def test_periodic_prolongation_is_second_order_and_keeps_constants_and_mean():
+    """R-mg prolongation (trilinear, cell-centred, periodic): it adds a constant exactly, it
+    keeps the mean, and for a smooth periodic field its error falls 4x per halving of h."""
+    assert np.allclose(O.prolong_add(np.full((4, 4, 4), 2.5), np.zeros((8, 8, 8))), 2.5, rtol=0, atol=1e-15)
+    u = np.random.default_rng(13).standard_normal((8, 8, 8))
+    assert abs(O.prolong_add(u, np.zeros((16, 16, 16))).mean() - u.mean()) < 1e-15
+    errs = []
+    for nc in (8, 16, 32):
+        g = lambda x, y, z: np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y) * np.sin(2 * np.pi * (z + 0.1))
+        coarse = g(*_centres(nc))
+        want = g(*_centres(2 * nc))
+        errs.append(np.abs(O.prolong_add(coarse, np.zeros_like(want)) - want).max())
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5, errs
+
+
+def test_dirichlet_prolongation_is_second_order_for_fields_vanishing_on_the_faces():
+    """The fixed-boundary form (outside neighbours take minus their mirror cell) is second
+    order for a field that vanishes on the box faces."""
+    errs = []
+    for nc in (8, 16, 32):
+        g = lambda x, y, z: np.sin(np.pi * x) * np.sin(2 * np.pi * y) * np.sin(np.pi * z)
+        coarse = g(*_centres(nc))
+        want = g(*_centres(2 * nc))
+        errs.append(np.abs(O.prolong_add(coarse, np.zeros_like(want), periodic=False) - want).max())
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5, errs
+
+
 @pytest.mark.parametrize("k", [0, 3, 8, 11])
 def test_partial_screening_mask_scales_kappa(k):
     """The mask byte k of a cell keeps (8 - k)/8 of the screening term (none for k >= 8):
