@@ -1,6 +1,6 @@
 // outer_ff.cuh -- the outer loop of the mixed-precision solve in float-float arithmetic.
 //
-// GB300 runs FP64 at 1/64 of its FP32 rate, and the outer residual of the defect
+// GB300 runs FP64 at about 1/58 of its FP32 rate (measured), and the outer residual of the defect
 // correction (19-point stencil, the quadratic q2, the floor test) costs ~60 FP64
 // instructions per cell: on the FP64 pipe it took longer than the whole FP32 inner cycle.
 // The outer iterate chi is therefore kept as an unevaluated sum hi + lo of two floats
@@ -11,7 +11,9 @@
 //   * TwoProd with a fused multiply-add: p + e == a * b exactly.
 // Sums use the "sloppy" pairing (TwoSum of the high parts, low parts added, Fast2Sum),
 // whose error is ~2^-47 of the operands' magnitude: the same kind of bound as FP64's
-// 2^-53, a factor 64 looser, far below the 1e-8 relative residual the loop stops at.
+// 2^-53, a factor 64 looser, far below the 1e-8 relative residual the loop stops at.  The
+// z-marching kernel keeps chains of such sums unnormalised (high parts by TwoSum, every
+// tail summed in FP32) and normalises once per quantity, with the same kind of bound.
 // The right-hand side src*delta is converted to float-float once per solve; the caller's
 // FP64 guess once on entry and the result once on exit, where one FP64 residual of the
 // returned chi confirms the stop test.
