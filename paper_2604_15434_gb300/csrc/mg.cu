@@ -589,12 +589,13 @@ constexpr int kResidZmMinN = 128;  // FP32 residual: z-marching kernel from this
 struct FusedCfg {
     int tx, ty, nz;
     bool pair;  // k_sweep_pair (two cells per thread) instead of k_sweep_fused
+    bool bal;   // k_sweep_pair with one warp per red unit (coefficient levels)
 };
-static const FusedCfg kFusedCfgs[] = {{64, 16, 32, false}, {64, 8, 32, false}, {64, 8, 64, false},
-                                     {32, 8, 32, false},  {32, 8, 64, false}, {64, 4, 64, false},
-                                     {64, 16, 16, false}, {64, 8, 16, false}, {64, 8, 32, true},
-                                     {64, 8, 64, true},   {64, 16, 32, true}, {64, 16, 64, true},
-                                     {64, 4, 64, true},   {64, 8, 16, true}};
+static const FusedCfg kFusedCfgs[] = {
+    {64, 16, 32, false, false}, {64, 8, 32, false, false}, {64, 8, 64, false, false}, {32, 8, 32, false, false},
+    {32, 8, 64, false, false},  {64, 4, 64, false, false}, {64, 16, 16, false, false}, {64, 8, 16, false, false},
+    {64, 8, 32, true, false},   {64, 8, 64, true, false},  {64, 16, 32, true, false},  {64, 16, 64, true, false},
+    {64, 4, 64, true, false},   {64, 8, 16, true, false},  {64, 16, 32, true, true},   {64, 8, 32, true, true}};
 constexpr int kNumFusedCfgs = sizeof(kFusedCfgs) / sizeof(kFusedCfgs[0]);
 
 template <int TX, int TY, bool BG, bool GAP>
@@ -610,16 +611,16 @@ static void launch_fused(Exec* ctx, const float* A, float* B, const float* F, fl
                                       (float)c.kap, sp, Df, lsn, L.lamp);
 }
 
-template <int TY, bool BG, bool GAP, bool COEF = false>
+template <int TY, bool BG, bool GAP, bool COEF = false, bool BAL = false>
 static void launch_pair(Exec* ctx, const float* A, float* B, const float* F, float fscale, float lam,
                         const Level<float>& L, int nz, float h2inv, const Coef& c, float sp, float Df, float lsn)
 {
     const int n = L.n;
     constexpr size_t sm = pair_smem_bytes<TY, BG, COEF>();
-    auto k = k_sweep_pair<TY, BG, GAP, COEF>;
+    auto k = k_sweep_pair<TY, BG, GAP, COEF, BAL>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     const dim3 grid(n / 64, n / TY, n / nz);
-    k<<<grid, PairGeom<TY>::NT, sm, ctx->stream>>>(A, B, F, fscale, lam, L.kmask, L.bg, L.gap, n, nz, h2inv,
+    k<<<grid, PairGeom<TY, BAL>::NT, sm, ctx->stream>>>(A, B, F, fscale, lam, L.kmask, L.bg, L.gap, n, nz, h2inv,
                                                    (float)c.nu, (float)c.kap, sp, Df, lsn, L.lamp,
                                                    COEF ? L.coef : nullptr);
 }
@@ -636,7 +637,9 @@ static void launch_fused_cfg(Exec* ctx, int cfg, const float* A, float* B, const
     }
 #define PM_PAIR_CASE(TY_)                                                                              \
     if (g.pair && g.ty == TY_) {                                                                       \
-        if (BG && GAP && L.coef)                                                                       \
+        if (BG && GAP && L.coef && g.bal)                                                              \
+            launch_pair<TY_, true, true, true, true>(ctx, A, B, F, fscale, lam, L, g.nz, h2inv, c, sp, Df, lsn); \
+        else if (BG && GAP && L.coef)                                                                  \
             launch_pair<TY_, true, true, true>(ctx, A, B, F, fscale, lam, L, g.nz, h2inv, c, sp, Df, lsn); \
         else                                                                                           \
             launch_pair<TY_, BG, GAP>(ctx, A, B, F, fscale, lam, L, g.nz, h2inv, c, sp, Df, lsn);      \
@@ -702,6 +705,7 @@ static int tuned_cfg(Exec* ctx, Level<float>& L, const float* F, float fscale, f
         for (int cfg = 0; cfg < kNumFusedCfgs; ++cfg) {
             if (!fused_cfg_fits(cfg, L.n)) continue;
             if (L.coef && L.gap && !kFusedCfgs[cfg].pair) continue;  // only the pair kernel reads coefficients
+            if (kFusedCfgs[cfg].bal && !(L.coef && L.gap)) continue;  // the balanced form exists for them only
             // one untimed launch, then three timed back to back
             for (int rep = 0; rep < 2; ++rep) {
                 const int launches = rep == 0 ? 1 : 3;
@@ -730,7 +734,7 @@ static int tuned_cfg(Exec* ctx, Level<float>& L, const float* F, float fscale, f
         ctx->tune_log += "sweep32 n=" + std::to_string(L.n) + (L.bg ? " bg" : "") + (L.gap ? " gap" : "") +
                          (cf ? " coef" : "") +
                          ": tile " + std::to_string(kFusedCfgs[best].tx) + "x" + std::to_string(kFusedCfgs[best].ty) +
-                         " nz " + std::to_string(kFusedCfgs[best].nz) + (kFusedCfgs[best].pair ? " pair" : " single") +
+                         " nz " + std::to_string(kFusedCfgs[best].nz) + (kFusedCfgs[best].pair ? (kFusedCfgs[best].bal ? " pair bal" : " pair") : " single") +
                          " " + std::to_string(best_ms) + " ms (variants tried, ms:" + trials + ")\n";
     }
     ctx->tuned[key] = best;

@@ -18,14 +18,16 @@
 
 namespace pmeft {
 
-template <int TY>
+// BAL: one warp per red unit (TY/2 + 2 warps), so that the red update takes one round; the
+// black update then leaves two warps idle.  Otherwise TY/2 warps (16 TY threads).
+template <int TY, bool BAL = false>
 struct PairGeom {
     static constexpr int TX = 64;
     static constexpr int WU = TX + 4, HU = TY + 4;  // old-value / background region
     static constexpr int WR = TX + 2, HR = TY + 2;  // red-update region
     static constexpr int PU = WU * HU, PR = WR * HR;
     static constexpr int NS = 5;                    // ring slots of old planes: s-2 .. s+2
-    static constexpr int NT = 16 * TY;              // threads
+    static constexpr int NT = BAL ? 32 * (TY / 2 + 2) : 16 * TY;  // threads
     static constexpr int NW = NT / 32;
     static constexpr int RED_MAIN = HR / 2;         // row-pair units of red pairs (k, k+16)
     static constexpr int RED_UNITS = RED_MAIN + 1;  // + the unit of the 33rd cells
@@ -159,8 +161,8 @@ __device__ __forceinline__ float pick_update(float G, float Ep, float P, float D
 
 // COEF (with BG and GAP): the finest inner level, the background entering through its
 // per-cell coefficients (three packed BF16 planes) instead of a ring of its planes.
-template <int TY, bool BG, bool GAP, bool COEF = false>
-__global__ void __launch_bounds__(16 * TY, TY >= 16 ? 3 : 1) k_sweep_pair(const float* __restrict__ U, float* __restrict__ V,
+template <int TY, bool BG, bool GAP, bool COEF = false, bool BAL = false>
+__global__ void __launch_bounds__(PairGeom<TY, BAL>::NT, TY >= 16 ? (BAL ? 2 : 3) : 1) k_sweep_pair(const float* __restrict__ U, float* __restrict__ V,
                                                        const float* __restrict__ F, float fscale, float lam,
                                                        const uint8_t* __restrict__ kmask, const float* __restrict__ bg,
                                                        const float* __restrict__ gap, int n, int NZ, float ih2,
@@ -168,7 +170,7 @@ __global__ void __launch_bounds__(16 * TY, TY >= 16 ? 3 : 1) k_sweep_pair(const 
                                                        const float* __restrict__ lamp,
                                                        const uint32_t* __restrict__ coef)
 {
-    using G = PairGeom<TY>;
+    using G = PairGeom<TY, BAL>;
     constexpr bool BGRING = BG && !COEF;
     constexpr int NS = G::NS, NT = G::NT, NW = G::NW, WU = G::WU, WR = G::WR;
     if (lamp) lam += *lamp;
