@@ -57,3 +57,22 @@ def test_coefficients_through_the_abi_match_the_oracle(lib):
         want = O.coefficients(*args)
         for k in ("nu", "xi", "kappa", "C2", "C4", "geff", "src"):
             assert got[k] == pytest.approx(want[k], rel=1e-14, abs=1e-15)
+
+
+def test_product_path_refuses_host_tensors(lib):
+    """No CPU fallback: the binding accepts only CUDA tensors, and every entry point called
+    with host tensors raises instead of computing anything."""
+    import torch
+
+    from paper_2604_15434_gb300 import api
+
+    x = torch.zeros((8, 8, 8), dtype=torch.float64)
+    with pytest.raises(TypeError):
+        api._ptr(x)
+    calls = (lambda: api.scalar_mg_solve(x, -0.5, 0.0, 1.0, 1e-8),
+             lambda: api.pm_deposit_cic(torch.zeros((3, 8), dtype=torch.float64), 8),
+             lambda: api.poisson_solve(x, 1.0, 0.0),
+             lambda: api.pm_mg_sweep(x, x, 0.0, 0.475, 0.5, 0.35))
+    for call in calls:
+        with pytest.raises(Exception):
+            call()
