@@ -864,8 +864,7 @@ static bool residual_restrict_f32(Exec* ctx, Level<float>& L, Level<float>& C, c
     if (n < kResidZmMinN || !C.kmask) return false;
     int nz = 8;
     while ((size_t)(n / kRzTX) * (n / kRzTY) * (n / nz) > (size_t)kMaxPartials) nz *= 2;
-    const dim3 g3(n / kRzTX, n / kRzTY, n / nz);
-    const int nb = (int)(g3.x * g3.y * g3.z);
+    const dim3 g3(n / kRzTX, n / kRzTY, n / nz);  // at most kMaxPartials blocks
     const float h2inv = (float)((double)n * (double)n);
     const double sqDf = c.eta * 6.0 * std::fabs(c.nu) * (double)n * (double)n;
     const float lsn = c.kap != 0.0 ? (float)(0.75 * c.nu * (1.0 - c.eta) / c.kap) : 0.f;  // L_sat
