@@ -400,9 +400,13 @@ def pm_deposit_cic_static(pos, n, delta=None, stream=None):
     Returns (delta, status) without raising, so callers can handle PM_ERR_TOO_LARGE."""
     if delta is None:
         delta = torch.empty((n, n, n), dtype=torch.float64, device=pos.device)
-    s = stream if stream is not None else torch.cuda.current_stream(pos.device)
-    st = load().pm_deposit_cic_static(_ptr(pos, name="pos"), pos.shape[1], n, _ptr(delta, shape=(n, n, n)),
-                                      ctypes.c_void_p(s.cuda_stream))
+    if delta.device != pos.device:
+        raise ValueError(f"delta is on {delta.device}, pos on {pos.device}: both must be on the same GPU")
+    # the entry point works on the current device: make it the one holding the buffers
+    with torch.cuda.device(pos.device):
+        s = stream if stream is not None else torch.cuda.current_stream(pos.device)
+        st = load().pm_deposit_cic_static(_ptr(pos, name="pos"), pos.shape[1], n, _ptr(delta, shape=(n, n, n)),
+                                          ctypes.c_void_p(s.cuda_stream))
     return delta, st
 
 

@@ -65,11 +65,13 @@ extern "C" pm_status pm_deposit_cic_static(const double* pos, long long np, int 
     // the array keeps the previous call's contents: clear the part this call uses
     if (cudaMemsetAsync(slot.acc, 0, cells * sizeof(unsigned long long), s) != cudaSuccess) return PM_ERR_CUDA;
     if (cudaMemsetAsync(slot.flag, 0, sizeof(int), s) != cudaSuccess) return PM_ERR_CUDA;
+    // each launch is checked at once, so that a failure is reported by the call that made it
     launch_deposit_on(s, slot.sms, pos, np, n, slot.acc);
+    if (cudaGetLastError() != cudaSuccess) return PM_ERR_CUDA;
     launch_density_on(s, slot.sms, (const long long*)slot.acc, n, np, delta, slot.flag);
+    if (cudaGetLastError() != cudaSuccess) return PM_ERR_CUDA;
     int hflag = 0;
     if (cudaMemcpyAsync(&hflag, slot.flag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return PM_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return PM_ERR_CUDA;
-    if (cudaGetLastError() != cudaSuccess) return PM_ERR_CUDA;
     return hflag ? PM_ERR_OVERFLOW : PM_OK;
 }
