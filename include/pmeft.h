@@ -46,7 +46,11 @@ typedef struct {
     int max_cycles;        /* cap on V-cycles (FP64) or outer iterations (mixed) (100) */
     int coarsest_n;        /* coarsest grid of the V-cycle (4) */
     int coarse_sweeps;     /* sweeps of the coarsest-level solve (8) */
-    int precision;         /* 0: FP64 FAS cycle; 1: FP32 inner cycle inside an FP64 defect-correction loop */
+    int precision;         /* 0: FP64 FAS cycle; 1: FP32 inner cycle inside a defect-correction loop whose
+                              outer residual is evaluated in float-float arithmetic (two FP32 words per value,
+                              about 48 significant bits) and whose stop is confirmed by an FP64 residual;
+                              2: the same FP32 inner cycle inside an FP64 defect-correction loop (FP64 outer
+                              residual and FP64 iterate) */
     int include_dot_alphaB;/* 1: keep alpha_B-dot/H = d alpha_B/d ln a in C2 (Sec. 2.2) */
     int inner_cycles;      /* precision 1: FP32 V-cycles on the correction per FP64 outer residual (1) */
     int autotune;          /* 1: time the tile variants of the FP32 sweep on first use of each size (1) */
@@ -58,6 +62,13 @@ typedef struct {
                               operator splitting, the quadratic in the cell's Laplacian with the
                               traceless Hessian from the neighbours (Sec. 3.2.2, Eq. opsplit).  The two
                               give the same update in exact arithmetic; FP32 levels use Method I (0) */
+    int coarse_exact;      /* 1: the coarsest grid (at most 4^3 cells; coarsest_n <= 4) is solved exactly in FP64
+                              by Newton's method with a dense Jacobian and LU with partial pivoting, the gauge
+                              multiplier as an extra unknown and the mean constraint as an extra row (Sec. 3.4
+                              leaves the coarse solve open), in the FP64 cycle and in the FP32 inner cycle alike;
+                              0: coarse_sweeps red-black sweeps with gauge updates (0) */
+    int grad_order;        /* force_interp / pm_step gradient: 4 the five-point fourth-order difference of
+                              Sec. 3.5.2, 2 the two-point central difference (4) */
 } pm_params;
 
 /* Report of one solve.  rel_res = |r|_2 / |f - <f>|_2 of the FP64 residual. */
@@ -314,6 +325,13 @@ pm_status pm_mg_sweep_f32(pm_ctx* ctx, float* u, const float* f, float lambda, i
  * cells; floored (device n^3 bytes, nullable) receives the floored-cell flags. */
 pm_status pm_mg_residual(pm_ctx* ctx, const double* u, const double* f, double lambda, int n, double nu,
                          double kappa, double eta, const unsigned char* kmask, double* r, unsigned char* floored);
+/* The exact coarsest-level solve of pm_params.coarse_exact alone, on a periodic n^3 grid with
+ * n = 2 or 4 (h = 1/n): u (device n^3, in: start, out: solution) of N(u) = f + lambda in
+ * cells with a real root and L(u) = L_sat where the discriminant is floored, the mean of u
+ * kept; kmask as for pm_mg_sweep (nullable); *lambda_out (host, nullable) receives lambda.
+ * PM_ERR_INVALID_ARG for other n or NULL u / f. */
+pm_status pm_mg_coarse_exact(pm_ctx* ctx, double* u, const double* f, int n, double nu, double kappa, double eta,
+                             const unsigned char* kmask, double* lambda_out);
 /* Restriction (average of 8 children) fine n^3 -> coarse (n/2)^3. */
 pm_status pm_mg_restrict(pm_ctx* ctx, const double* fine, int n, double* coarse);
 /* fine (n^3) += trilinear cell-centred prolongation of coarse ((n/2)^3), periodic. */

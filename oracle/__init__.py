@@ -28,6 +28,7 @@ _lock = threading.Lock()
 _handle = None
 
 OMEGA_M0 = 0.3  # the paper's Omega_m0 for the static sphere (Sec. 3.6.1); used as the default
+ETA_DEFAULT = 0.35  # void floor sqrt(D_floor) = eta 6|nu|/h^2 (reading R-sat of Sec. 3.3)
 
 
 def build(force: bool = False) -> str:
@@ -55,13 +56,15 @@ def _lib():
             h.orc_smooth_sweep_opsplit.argtypes = [P, P, D, I, D, D, D, D, P]
             h.orc_residual.argtypes = [P, P, D, I, D, D, D, D, P, P, P]
             h.orc_residual.restype = LL
+            h.orc_coarse_exact.argtypes = [P, P, I, D, D, D, D, P]
+            h.orc_coarse_exact.restype = D
             h.orc_restrict.argtypes = [P, I, P]
             h.orc_prolong_add.argtypes = [P, I, P, I]
             h.orc_mg_solve.argtypes = [P, I, P, D, P, P]
             h.orc_mg_solve.restype = I
             h.orc_deposit_cic.argtypes = [P, LL, I, P]
             h.orc_density.argtypes = [P, I, LL, P]
-            h.orc_accel_grid.argtypes = [P, P, D, I, P]
+            h.orc_accel_grid.argtypes = [P, P, D, I, I, P]
             h.orc_interp_cic.argtypes = [P, I, P, LL, P]
             h.orc_kick_drift.argtypes = [P, P, P, LL, D]
             _handle = h
@@ -145,6 +148,18 @@ def residual(u, f, lam, nu, kappa, eta, kmask=None):
     return r, sat
 
 
+def coarse_exact(u, f, nu, kappa, eta=ETA_DEFAULT, kmask=None):
+    """The exact coarsest-level solve alone (Sec. 3.4 FAS, reading of the coarse solve): Newton
+    with a dense Jacobian and LU on the residual pieces of a periodic grid, the gauge multiplier
+    as an extra unknown and the mean of u kept.  Returns (u, lambda)."""
+    u = _f64(u).copy()
+    f = _f64(f)
+    n = u.shape[0]
+    km = None if kmask is None else np.ascontiguousarray(kmask, dtype=np.uint8)
+    lam = _lib().orc_coarse_exact(_p(u), _p(f), n, 1.0 / n, nu, kappa, eta, _p(km))
+    return u, lam
+
+
 def restrict(u):
     """Average of the 8 children."""
     u = _f64(u)
@@ -166,7 +181,8 @@ class _MGParams(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_double), ("kappa", ctypes.c_double), ("eta", ctypes.c_double),
                 ("npre", ctypes.c_int), ("npost", ctypes.c_int), ("max_cycles", ctypes.c_int),
                 ("coarsest_n", ctypes.c_int), ("coarse_sweeps", ctypes.c_int),
-                ("dirichlet", ctypes.c_int), ("ghosts", ctypes.c_void_p), ("smoother", ctypes.c_int)]
+                ("dirichlet", ctypes.c_int), ("ghosts", ctypes.c_void_p), ("smoother", ctypes.c_int),
+                ("coarse_exact", ctypes.c_int)]
 
 
 class _MGInfo(ctypes.Structure):
@@ -174,16 +190,16 @@ class _MGInfo(ctypes.Structure):
                 ("sat_cells", ctypes.c_longlong), ("hist", ctypes.c_double * 256)]
 
 
-ETA_DEFAULT = 0.35
-
 
 def mg_solve(f, nu, kappa, tol, chi0=None, eta=ETA_DEFAULT, npre=2, npost=2, max_cycles=200,
-             coarsest_n=4, coarse_sweeps=100, ghosts=None, smoother=0):
+             coarsest_n=4, coarse_sweeps=100, ghosts=None, smoother=0, coarse_exact=False):
     """FAS multigrid solve of nu L(chi) - kappa q2(chi) = f (+ lambda) (Sec. 3.4).
 
     Periodic by default (with the gauge multiplier and <chi> = 0); with ``ghosts`` (a
     list of padded ghost arrays, finest level first) the faces are Dirichlet.  smoother 0
-    is Method I (Sec. 3.2.1), 1 Method II (Sec. 3.2.2).
+    is Method I (Sec. 3.2.1), 1 Method II (Sec. 3.2.2).  coarse_exact: the coarsest grid is
+    solved by Newton with a dense Jacobian and LU (gauge multiplier and mean constraint as
+    the extra unknown and row) instead of coarse_sweeps sweeps.
     Returns (chi, info dict, status) with status 0 = converged, 2 = not converged.
     """
     f = _f64(f)
@@ -193,7 +209,8 @@ def mg_solve(f, nu, kappa, tol, chi0=None, eta=ETA_DEFAULT, npre=2, npost=2, max
     if ghosts is not None:
         gbuf = np.concatenate([_f64(g).ravel() for g in ghosts])
     prm = _MGParams(nu, kappa, eta, npre, npost, max_cycles, coarsest_n, coarse_sweeps,
-                    int(ghosts is not None), _p(gbuf) if gbuf is not None else None, int(smoother))
+                    int(ghosts is not None), _p(gbuf) if gbuf is not None else None, int(smoother),
+                    int(bool(coarse_exact)))
     info = _MGInfo()
     st = _lib().orc_mg_solve(_p(f), n, ctypes.byref(prm), tol, _p(chi), ctypes.byref(info))
     d = {"cycles": info.cycles, "rel_res": info.rel_res, "lambda": info.lam, "sat_cells": info.sat_cells,
@@ -255,12 +272,13 @@ def poisson_fft(delta, coeffs, a, omega_m0=OMEGA_M0):
     return np.fft.irfftn(pk, s=(n, n, n), axes=(0, 1, 2))
 
 
-def accel_grid(psiN, chi, xi_force, n):
-    """g = -grad(Psi_N + xi_force chi) with the 5-point stencil (Eq. force, Sec. 3.5.2); [3][n^3]."""
+def accel_grid(psiN, chi, xi_force, n, order=4):
+    """g = -grad(Psi_N + xi_force chi) with the 5-point stencil (Eq. force, Sec. 3.5.2), or with
+    the 2-point central difference for order 2; [3][n^3]."""
     psiN = _f64(psiN)
     chi = None if chi is None else _f64(chi)
     out = np.empty((3, n, n, n))
-    _lib().orc_accel_grid(_p(psiN), _p(chi), xi_force, n, _p(out))
+    _lib().orc_accel_grid(_p(psiN), _p(chi), xi_force, n, int(order), _p(out))
     return out
 
 
@@ -284,7 +302,7 @@ def kick_drift(pos, vel, acc, dt):
 
 
 def pm_step(pos, vel, n, alpha_B0, alpha_M0, a, dt, tol, chi0=None, omega_m0=OMEGA_M0, include_dot=True,
-            linear=False, **kw):
+            linear=False, grad_order=4, **kw):
     """One particle-mesh step: deposit, Poisson, chi solve, force, kick-drift (Sec. 3.5.1 step order).
     linear: the linearised equations (Sec. 2.5, Eq. linearised): nu L chi = xi S with L Psi_N = S,
     so chi = (xi / nu) Psi_N, with no screening term and no multigrid solve."""
@@ -297,7 +315,7 @@ def pm_step(pos, vel, n, alpha_B0, alpha_M0, a, dt, tol, chi0=None, omega_m0=OME
         info, st = {"cycles": 0}, 0
     else:
         chi, info, st = scalar_solve(delta, alpha_B0, alpha_M0, a, tol, omega_m0, include_dot, chi0=chi0, **kw)
-    g = accel_grid(psiN, chi, c["xi"], n)
+    g = accel_grid(psiN, chi, c["xi"], n, grad_order)
     accp = interp_cic(g, pos)
     pos2, vel2 = kick_drift(pos, vel, accp, dt)
     return {"acc_fixed": acc_grid_i, "delta": delta, "psiN": psiN, "chi": chi, "info": info, "status": st,

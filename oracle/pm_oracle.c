@@ -408,6 +408,12 @@ long long orc_residual(const double* u, const double* f, double lam, int n, doub
     return ns;
 }
 
+/* The exact coarsest-level solve alone on a periodic n^3 grid: u (in: start, out: solution)
+ * of the residual pieces of R-res for right-hand side f, with the gauge multiplier and the
+ * mean of u kept; kmask as for the sweep (nullable).  Returns the final lambda. */
+double orc_coarse_exact(double* u, const double* f, int n, double h, double nu, double kap, double eta,
+                        const unsigned char* kmask);
+
 /* Restriction: average of the 8 children (Sec. 3.4 FAS; the paper leaves R open). */
 void orc_restrict(const double* fine, int nf, double* coarse)
 {
@@ -467,6 +473,7 @@ typedef struct {
     int dirichlet;              /* 0: periodic with gauge multiplier; 1: fixed ghosts */
     const double* ghosts;       /* Dirichlet: padded ghost arrays of every level, finest first */
     int smoother;               /* 0: Method I (quadratic in the cell value); 1: Method II */
+    int coarse_exact;           /* 1: Newton with a dense Jacobian and LU on the coarsest grid */
 } orc_mg_params;
 
 
@@ -520,11 +527,184 @@ static void coarse_solve(level_t* L, const orc_mg_params* prm, int periodic)
     }
 }
 
+/* ------------------------------------------------------------------ */
+/* Exact coarsest-level solve (Sec. 3.4 FAS; the paper leaves the coarse
+ * solve open).  Reading: Newton's method on the whole discrete system of
+ * the level, with its Jacobian written out as a dense matrix and solved by
+ * LU with partial pivoting.  Unknowns: the m cell values and, on a periodic
+ * grid, the gauge multiplier lambda.  Equations: each cell's residual piece
+ * of R-res with its sign flipped (N - f - lambda where the discriminant has
+ * a real root, nu (L - L_sat) where it is floored) and, on a periodic grid,
+ * the mean constraint sum(chi) = its value on entry, scaled by 6|nu|/h^2 so
+ * that its row is of the size of the others.  The floored set is taken
+ * afresh at every iterate; a backtracking line search on the residual norm
+ * keeps each step from increasing it.                                   */
+/* ------------------------------------------------------------------ */
+
+/* A x = b for a dense m x m matrix (row-major), by Gaussian elimination with partial
+ * pivoting; A is overwritten, b receives x.  Returns 1 on a zero pivot. */
+static int dense_solve(double* A, double* b, int m)
+{
+    for (int k = 0; k < m; ++k) {
+        int piv = k;
+        for (int i = k + 1; i < m; ++i)
+            if (fabs(A[(size_t)i * m + k]) > fabs(A[(size_t)piv * m + k])) piv = i;
+        if (A[(size_t)piv * m + k] == 0.0) return 1;
+        if (piv != k) {
+            for (int j = 0; j < m; ++j) {
+                double t = A[(size_t)k * m + j];
+                A[(size_t)k * m + j] = A[(size_t)piv * m + j];
+                A[(size_t)piv * m + j] = t;
+            }
+            double t = b[k]; b[k] = b[piv]; b[piv] = t;
+        }
+        for (int i = k + 1; i < m; ++i) {
+            double l = A[(size_t)i * m + k] / A[(size_t)k * m + k];
+            if (l == 0.0) continue;
+            for (int j = k; j < m; ++j) A[(size_t)i * m + j] -= l * A[(size_t)k * m + j];
+            b[i] -= l * b[k];
+        }
+    }
+    for (int k = m - 1; k >= 0; --k) {
+        double s = b[k];
+        for (int j = k + 1; j < m; ++j) s -= A[(size_t)k * m + j] * b[j];
+        b[k] = s / A[(size_t)k * m + k];
+    }
+    return 0;
+}
+
+/* Unknown index of cell (i, j, k) of an n^3 level: the wrapped cell on a periodic grid,
+ * -1 for a fixed (Dirichlet) ghost. */
+static int exact_col(int i, int j, int k, int n, int periodic)
+{
+    if (periodic) return (int)uidx(wrap(i, n), wrap(j, n), wrap(k, n), n);
+    if (i < 0 || i >= n || j < 0 || j >= n || k < 0 || k >= n) return -1;
+    return (int)uidx(i, j, k, n);
+}
+
+/* Residual pieces F (size m + periodic) at the padded iterate p, and with J != NULL the
+ * Jacobian dF/d(chi, lambda).  Returns |F|_2. */
+static double exact_system(const level_t* L, const orc_mg_params* prm, int periodic, const double* p, double lam,
+                           double msum, double* F, double* J)
+{
+    int n = L->n, m = n * n * n, M = m + (periodic ? 1 : 0);
+    double h = L->h, h2 = h * h, Df = floor_disc(prm->nu, h, prm->eta), nu = prm->nu;
+    double scale = 6.0 * fabs(nu) / h2;
+    if (J) memset(J, 0, (size_t)M * M * sizeof(double));
+    double f2 = 0.0;
+    for (int k = 0; k < n; ++k)
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                int c = (int)uidx(i, j, k, n);
+                double kc = prm->kappa * screen_w(L->kmask, (size_t)c);
+                orc_local o;
+                size_t pc = pidx(i, j, k, n);
+                local_eval(p, pc, n, h, nu, kc, L->f[c] + (periodic ? lam : 0.0), &o);
+                int fl = (o.P != 0.0 && o.D < Df);
+                if (fl) F[c] = nu * (o.L - 3.0 * nu * (1.0 - prm->eta) / (4.0 * kc));
+                else F[c] = o.G;
+                f2 += F[c] * F[c];
+                if (!J) continue;
+                double* row = J + (size_t)c * M;
+                /* d/d(own and face values) of nu L */
+                row[exact_col(i, j, k, n, periodic)] += -6.0 * nu / h2;
+                int fi[6][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+                for (int q = 0; q < 6; ++q) {
+                    int d = exact_col(i + fi[q][0], j + fi[q][1], k + fi[q][2], n, periodic);
+                    if (d >= 0) row[d] += nu / h2;
+                }
+                if (fl) continue;
+                if (periodic) row[m] = -1.0;
+                if (kc == 0.0) continue;
+                /* -kappa dq2: q2 = 2(XY + YZ + ZX) - 2(cxy^2 + cxz^2 + cyz^2) */
+                size_t sx = 1, sy = (size_t)n + 2, sz = sy * sy;
+                double X = (p[pc + sx] + p[pc - sx] - 2.0 * p[pc]) / h2;
+                double Y = (p[pc + sy] + p[pc - sy] - 2.0 * p[pc]) / h2;
+                double Z = (p[pc + sz] + p[pc - sz] - 2.0 * p[pc]) / h2;
+                double cxy = (p[pc + sx + sy] - p[pc + sx - sy] - p[pc - sx + sy] + p[pc - sx - sy]) / (4.0 * h2);
+                double cxz = (p[pc + sx + sz] - p[pc + sx - sz] - p[pc - sx + sz] + p[pc - sx - sz]) / (4.0 * h2);
+                double cyz = (p[pc + sy + sz] - p[pc + sy - sz] - p[pc - sy + sz] + p[pc - sy - sz]) / (4.0 * h2);
+                double dX = 2.0 * (Y + Z), dY = 2.0 * (X + Z), dZ = 2.0 * (X + Y);
+                row[exact_col(i, j, k, n, periodic)] -= kc * (-2.0 / h2) * (dX + dY + dZ);
+                double dd[3] = {dX, dY, dZ};
+                for (int q = 0; q < 6; ++q) {
+                    int d = exact_col(i + fi[q][0], j + fi[q][1], k + fi[q][2], n, periodic);
+                    if (d >= 0) row[d] -= kc * dd[q / 2] / h2;
+                }
+                /* cross differences: d(-2 c^2)/dc = -4c, dc/d(corner) = +-1/(4h^2) */
+                double cc[3] = {cxy, cxz, cyz};
+                int ax[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+                for (int q = 0; q < 3; ++q)
+                    for (int s1 = -1; s1 <= 1; s1 += 2)
+                        for (int s2 = -1; s2 <= 1; s2 += 2) {
+                            int o3[3] = {0, 0, 0};
+                            o3[ax[q][0]] = s1;
+                            o3[ax[q][1]] = s2;
+                            int d = exact_col(i + o3[0], j + o3[1], k + o3[2], n, periodic);
+                            if (d >= 0) row[d] -= kc * (-4.0 * cc[q]) * (double)(s1 * s2) / (4.0 * h2);
+                        }
+            }
+    if (periodic) {
+        double s = 0.0;
+        for (int k = 0; k < n; ++k)
+            for (int j = 0; j < n; ++j)
+                for (int i = 0; i < n; ++i) s += p[pidx(i, j, k, n)];
+        F[m] = scale * (s - msum);
+        f2 += F[m] * F[m];
+        if (J)
+            for (int d = 0; d < m; ++d) J[(size_t)m * M + d] = scale;
+    }
+    return sqrt(f2);
+}
+
+static void coarse_exact(level_t* L, const orc_mg_params* prm, int periodic)
+{
+    int n = L->n, m = n * n * n, M = m + (periodic ? 1 : 0);
+    size_t mp = (size_t)(n + 2) * (n + 2) * (n + 2);
+    double* J = (double*)malloc((size_t)M * M * sizeof(double));
+    double* F = (double*)malloc((size_t)M * sizeof(double));
+    double* Ft = (double*)malloc((size_t)M * sizeof(double));
+    double* pt = (double*)malloc(mp * sizeof(double));
+    fill_ghosts(L->p, n, L->ghost);
+    double msum = 0.0, fm = 0.0, fn = 0.0;
+    for (int k = 0; k < n; ++k)
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) msum += L->p[pidx(i, j, k, n)];
+    for (int c = 0; c < m; ++c) fm += L->f[c] / (double)m;
+    for (int c = 0; c < m; ++c) fn += (L->f[c] - (periodic ? fm : 0.0)) * (L->f[c] - (periodic ? fm : 0.0));
+    fn = sqrt(fn);
+    double lam = 0.0;
+    double nrm = exact_system(L, prm, periodic, L->p, lam, msum, F, J);
+    for (int it = 0; it < 50; ++it) {
+        if (nrm <= 1e-14 * fn || nrm == 0.0) break;
+        for (int q = 0; q < M; ++q) F[q] = -F[q];
+        if (dense_solve(J, F, M)) break;
+        double step = 1.0, nt = nrm, lt = lam;
+        for (;;) {
+            memcpy(pt, L->p, mp * sizeof(double));
+            for (int k = 0; k < n; ++k)
+                for (int j = 0; j < n; ++j)
+                    for (int i = 0; i < n; ++i) pt[pidx(i, j, k, n)] += step * F[uidx(i, j, k, n)];
+            fill_ghosts(pt, n, L->ghost);
+            lt = periodic ? lam + step * F[m] : 0.0;
+            nt = exact_system(L, prm, periodic, pt, lt, msum, Ft, NULL);
+            if (nt < (1.0 - 1e-4 * step) * nrm || step < 1e-4) break;
+            step *= 0.5;
+        }
+        if (!(nt < nrm)) break; /* no decrease along the Newton direction: keep the iterate */
+        memcpy(L->p, pt, mp * sizeof(double));
+        lam = lt;
+        nrm = exact_system(L, prm, periodic, L->p, lam, msum, F, J);
+    }
+    free(J); free(F); free(Ft); free(pt);
+}
+
 static void vcycle(level_t* lv, int l, int nlev, double lam, const orc_mg_params* prm, int periodic)
 {
     level_t* L = &lv[l];
     if (l == nlev - 1) {
-        coarse_solve(L, prm, periodic);
+        if (prm->coarse_exact) coarse_exact(L, prm, periodic);
+        else coarse_solve(L, prm, periodic);
         return;
     }
     level_t* C = &lv[l + 1];
@@ -579,6 +759,37 @@ static void vcycle(level_t* lv, int l, int nlev, double lam, const orc_mg_params
     free(nh);
     for (int s = 0; s < prm->npost; ++s)
         smooth_level(L, lam, prm);
+}
+
+double orc_coarse_exact(double* u, const double* f, int n, double h, double nu, double kap, double eta,
+                        const unsigned char* kmask)
+{
+    size_t m = (size_t)n * n * n, mp = (size_t)(n + 2) * (n + 2) * (n + 2);
+    level_t L;
+    memset(&L, 0, sizeof(L));
+    L.n = n;
+    L.h = h;
+    L.p = (double*)calloc(mp, sizeof(double));
+    L.f = (double*)malloc(m * sizeof(double));
+    L.kmask = (unsigned char*)kmask;
+    memcpy(L.f, f, m * sizeof(double));
+    pad_from(u, n, L.p);
+    orc_mg_params prm;
+    memset(&prm, 0, sizeof(prm));
+    prm.nu = nu;
+    prm.kappa = kap;
+    prm.eta = eta;
+    coarse_exact(&L, &prm, 1);
+    unpad_to(L.p, n, u);
+    /* the multiplier of the solution: the mean residual of the unfloored cells at lambda 0 */
+    double* r = (double*)malloc(m * sizeof(double));
+    unsigned char* sat = (unsigned char*)malloc(m);
+    residual_padded(L.p, f, 0.0, n, h, nu, kap, eta, kmask, NULL, r, sat);
+    double s = 0.0, w = 0.0;
+    for (size_t i = 0; i < m; ++i)
+        if (!sat[i]) { s += r[i]; w += 1.0; }
+    free(r); free(sat); free(L.p); free(L.f);
+    return w > 0.0 ? -s / w : 0.0;
 }
 
 /*
@@ -722,9 +933,10 @@ void orc_density(const int64_t* acc, int n, long long np, double* delta)
 /*
  * Acceleration grid g = -grad Psi with Psi = Psi_N + xi_f * chi
  * (Eq. phipsi_mod; xi_f = alpha_B - alpha_M) and the five-point
- * fourth-order central difference of Sec. 3.5.2.  acc is [3][n^3].
+ * fourth-order central difference of Sec. 3.5.2 (order 4), or the
+ * two-point central difference (order 2).  acc is [3][n^3].
  */
-void orc_accel_grid(const double* psiN, const double* chi, double xi_f, int n, double* acc)
+void orc_accel_grid(const double* psiN, const double* chi, double xi_f, int n, int order, double* acc)
 {
     double h = 1.0 / (double)n;
     size_t m = (size_t)n * n * n;
@@ -734,6 +946,12 @@ void orc_accel_grid(const double* psiN, const double* chi, double xi_f, int n, d
         for (int j = 0; j < n; ++j)
             for (int i = 0; i < n; ++i) {
                 size_t u = uidx(i, j, k, n);
+                if (order == 2) {
+                    acc[u] = -(psi[uidx(wrap(i + 1, n), j, k, n)] - psi[uidx(wrap(i - 1, n), j, k, n)]) / (2.0 * h);
+                    acc[m + u] = -(psi[uidx(i, wrap(j + 1, n), k, n)] - psi[uidx(i, wrap(j - 1, n), k, n)]) / (2.0 * h);
+                    acc[2 * m + u] = -(psi[uidx(i, j, wrap(k + 1, n), n)] - psi[uidx(i, j, wrap(k - 1, n), n)]) / (2.0 * h);
+                    continue;
+                }
                 double gx = (-psi[uidx(wrap(i + 2, n), j, k, n)] + 8.0 * psi[uidx(wrap(i + 1, n), j, k, n)]
                              - 8.0 * psi[uidx(wrap(i - 1, n), j, k, n)] + psi[uidx(wrap(i - 2, n), j, k, n)]) / (12.0 * h);
                 double gy = (-psi[uidx(i, wrap(j + 2, n), k, n)] + 8.0 * psi[uidx(i, wrap(j + 1, n), k, n)]

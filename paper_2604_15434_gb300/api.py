@@ -33,7 +33,7 @@ class Params(ctypes.Structure):
                 ("npost", ctypes.c_int), ("max_cycles", ctypes.c_int), ("coarsest_n", ctypes.c_int),
                 ("coarse_sweeps", ctypes.c_int), ("precision", ctypes.c_int), ("include_dot_alphaB", ctypes.c_int),
                 ("inner_cycles", ctypes.c_int), ("autotune", ctypes.c_int), ("linear_eft", ctypes.c_int),
-                ("smoother", ctypes.c_int)]
+                ("smoother", ctypes.c_int), ("coarse_exact", ctypes.c_int), ("grad_order", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -76,6 +76,7 @@ SIGNATURES = {
     "pm_step": (_I, [_P, _P, _P, _LL, _I, _D, _D, _D, _D, _D, _P, _P]),
     "pm_mg_sweep": (_I, [_P, _P, _P, _D, _I, _D, _D, _D, _P]),
     "pm_mg_residual": (_I, [_P, _P, _P, _D, _I, _D, _D, _D, _P, _P, _P]),
+    "pm_mg_coarse_exact": (_I, [_P, _P, _P, _I, _D, _D, _D, _P, _P]),
     "pm_mg_restrict": (_I, [_P, _P, _I, _P]),
     "pm_mg_prolong_add": (_I, [_P, _P, _I, _P]),
     "pm_trace_enable": (_I, [_P, _I]),
@@ -355,6 +356,16 @@ def pm_mg_sweep(u, f, lam, nu, kappa, eta, kmask=None, ctx=None):
     ctx._check(load().pm_mg_sweep(ctx._h, _ptr(u, shape=(n, n, n)), _ptr(f, shape=(n, n, n)), lam, n, nu, kappa, eta,
                                   _ptr(kmask, torch.uint8, (n, n, n), "kmask")))
     return u
+
+
+def pm_mg_coarse_exact(u, f, nu, kappa, eta, kmask=None, ctx=None):
+    """The exact coarsest-level solve alone (n = 2 or 4): u solved in place; returns (u, lambda)."""
+    ctx = ctx or default_context()
+    n = u.shape[0]
+    lam = ctypes.c_double(0.0)
+    ctx._check(load().pm_mg_coarse_exact(ctx._h, _ptr(u, shape=(n, n, n)), _ptr(f, shape=(n, n, n)), n, nu, kappa,
+                                         eta, _ptr(kmask, torch.uint8, (n, n, n), "kmask"), ctypes.byref(lam)))
+    return u, lam.value
 
 
 def pm_mg_sweep_f32(u, f, lam, nu, kappa, eta, kmask=None, mode=1, bg=None, gap=None, ctx=None):

@@ -209,6 +209,8 @@ extern "C" void pm_default_params(pm_params* p)
     p->autotune = 1;
     p->linear_eft = 0;
     p->smoother = 0;
+    p->coarse_exact = 0;
+    p->grad_order = 4;
 }
 
 static bool params_ok(const pm_params* p)
@@ -216,9 +218,10 @@ static bool params_ok(const pm_params* p)
     return p->omega_m0 > 0.0 && p->omega_m0 < 1.0 && p->eta >= 0.0 && p->eta < 1.0 && p->npre >= 0 &&
            p->npost >= 0 && p->npre + p->npost > 0 && p->max_cycles >= 0 && p->coarsest_n >= 2 &&
            p->coarsest_n <= 8 && (p->coarsest_n & (p->coarsest_n - 1)) == 0 && p->coarse_sweeps >= 1 &&
-           (p->precision == 0 || p->precision == 1) && p->inner_cycles >= 1 && p->inner_cycles <= 16 &&
+           (p->precision >= 0 && p->precision <= 2) && p->inner_cycles >= 1 && p->inner_cycles <= 16 &&
            (p->autotune == 0 || p->autotune == 1) && (p->linear_eft == 0 || p->linear_eft == 1) &&
-           (p->smoother == 0 || p->smoother == 1);
+           (p->smoother == 0 || p->smoother == 1) && (p->coarse_exact == 0 || (p->coarse_exact == 1 &&
+           p->coarsest_n <= 4)) && (p->grad_order == 2 || p->grad_order == 4);
 }
 
 extern "C" pm_status pm_coefficients(double aB0, double aM0, double a, double om0, int include_dot, pm_coeffs* out)

@@ -514,6 +514,238 @@ __global__ void __launch_bounds__(256) k_coarsest(T* __restrict__ u, const T* __
     for (int c = t; c < cells; c += blockDim.x) u[c] = su[c];
 }
 
+// ------------------------------------------------------------------ exact coarsest solve
+
+// Exact solve of a coarsest level of at most kExactMaxCells cells, in FP64 whatever the
+// storage type, in one block: Newton's method on the level's whole discrete system (the
+// paper's FAS leaves the coarse solve open; Sec. 3.4), its Jacobian written out as a dense
+// matrix and solved by LU with partial pivoting.  Unknowns: the m cell values and the gauge
+// multiplier lambda.  Equations: each cell's residual piece with its sign flipped (N - f -
+// lambda where the discriminant has a real root, nu (L - L_sat) where it is floored; Sec. 3.3)
+// and the mean constraint sum(chi) = its value on entry, scaled by 6|nu|/h^2.  The floored set
+// is taken afresh at every iterate, and a backtracking line search on |F| keeps each step from
+// increasing it.  Stops at |F| <= 1e-14 |f - <f>| or after kExactMaxIter iterations.  With a
+// background (the FP32 inner cycle's correction form) the unknown is the total field bg + u
+// and the right-hand side f + N(bg), i.e. N(bg + u) - N(bg) = f + lambda; u is written back
+// in the storage type.  lam_out (nullable) receives lambda.
+constexpr int kExactMaxCells = 64;
+constexpr int kExactThreads = 128;
+constexpr int kExactMaxIter = 30;
+
+template <bool JAC>
+__device__ double exact_eval(const double* __restrict__ x, double lam, const double* __restrict__ rhs,
+                             const double* __restrict__ wk, int n, double ih2, double nu, double kap, double eta,
+                             double* __restrict__ Fv, double* __restrict__ J, int ld, double* red, double scale,
+                             double msum)
+{
+    const int m = n * n * n, t = threadIdx.x, M = m + 1;
+    const double sqDf = eta * 6.0 * fabs(nu) * ih2, Df = sqDf * sqDf;
+    double f2 = 0.0;
+    for (int c = t; c < m; c += blockDim.x) {
+        const int mm = n - 1, i = c & mm, j = (c / n) & mm, k = c / (n * n);
+        const Stencil<double> s = load_stencil<double>(x, x, i, j, k, n);
+        const double kc = kap * wk[c];
+        const double lsat = kc != 0.0 ? 0.75 * nu * (1.0 - eta) / kc : 0.0;
+        const Local<double> o = local_eval<double, false>(s, s, ih2, nu, kc, rhs[c] + lam, lsat);
+        const bool fl = (o.P != 0.0) && (o.D < Df);
+        const double Fc = fl ? -nu * o.g : o.G;  // nu (L - L_sat) = -nu g
+        Fv[c] = Fc;
+        f2 += Fc * Fc;
+        if (!JAC) continue;
+        double* row = J + (size_t)c * ld;
+        for (int q = 0; q < M; ++q) row[q] = 0.0;
+        auto at = [&](int di, int dj, int dk) { return (((k + dk) & mm) * n + ((j + dj) & mm)) * n + ((i + di) & mm); };
+        row[c] += -6.0 * nu * ih2;
+        const int fo[6][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+        for (int q = 0; q < 6; ++q) row[at(fo[q][0], fo[q][1], fo[q][2])] += nu * ih2;
+        if (fl) continue;
+        row[m] = -1.0;
+        if (kc == 0.0) continue;
+        // -kappa dq2, q2 = 2(XY + YZ + ZX) - 2(cxy^2 + cxz^2 + cyz^2), physical units
+        const double X = (s.ax - 2.0 * s.c0) * ih2, Y = (s.ay - 2.0 * s.c0) * ih2, Z = (s.az - 2.0 * s.c0) * ih2;
+        const double dq[3] = {2.0 * (Y + Z), 2.0 * (X + Z), 2.0 * (X + Y)};
+        row[c] -= kc * (-2.0 * ih2) * (dq[0] + dq[1] + dq[2]);
+        for (int q = 0; q < 6; ++q) row[at(fo[q][0], fo[q][1], fo[q][2])] -= kc * dq[q / 2] * ih2;
+        const double cc[3] = {s.exy * 0.25 * ih2, s.exz * 0.25 * ih2, s.eyz * 0.25 * ih2};
+        const int ax[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+        for (int q = 0; q < 3; ++q)
+            for (int s1 = -1; s1 <= 1; s1 += 2)
+                for (int s2 = -1; s2 <= 1; s2 += 2) {
+                    int o3[3] = {0, 0, 0};
+                    o3[ax[q][0]] = s1;
+                    o3[ax[q][1]] = s2;
+                    // d(-2 c^2)/dc = -4c and dc/d(corner) = s1 s2 / (4 h^2)
+                    row[at(o3[0], o3[1], o3[2])] += kc * cc[q] * (double)(s1 * s2) * ih2;
+                }
+    }
+    // the mean row
+    double sx = 0.0;
+    for (int c = t; c < m; c += blockDim.x) sx += x[c];
+    for (int o = 16; o > 0; o >>= 1) {
+        f2 += __shfl_down_sync(0xffffffffu, f2, o);
+        sx += __shfl_down_sync(0xffffffffu, sx, o);
+    }
+    const int lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) {
+        red[wid] = f2;
+        red[8 + wid] = sx;
+    }
+    __syncthreads();
+    double a = 0.0, b = 0.0;
+    for (int q = 0; q < nw; ++q) {  // every thread, the same order
+        a += red[q];
+        b += red[8 + q];
+    }
+    const double Fm = scale * (b - msum);
+    if (t == 0) Fv[m] = Fm;
+    if (JAC)
+        for (int q = t; q < m; q += blockDim.x) J[(size_t)m * ld + q] = scale;
+    if (JAC && t == 0) J[(size_t)m * ld + m] = 0.0;
+    __syncthreads();
+    return sqrt(a + Fm * Fm);
+}
+
+template <typename T, bool BG>
+__global__ void __launch_bounds__(kExactThreads) k_coarsest_exact(T* __restrict__ u, const T* __restrict__ F,
+                                                                  T fscale, const uint8_t* __restrict__ kmask,
+                                                                  const T* __restrict__ bg, int n, double ih2,
+                                                                  double nu, double kap, double eta,
+                                                                  double* __restrict__ lam_out)
+{
+    constexpr int MX = kExactMaxCells + 1, LD = MX + 1;
+    __shared__ double J[MX * LD];
+    __shared__ double b[MX], Fv[MX];
+    __shared__ double x[kExactMaxCells], xt[kExactMaxCells], rhs[kExactMaxCells], wk[kExactMaxCells];
+    __shared__ double red[16];
+    __shared__ int piv;
+    __shared__ bool singular;
+    const int m = n * n * n, M = m + 1, t = threadIdx.x;
+    const double scale = 6.0 * fabs(nu) * ih2;
+    for (int c = t; c < m; c += blockDim.x) {
+        x[c] = (double)u[c] + (BG ? (double)bg[c] : 0.0);
+        wk[c] = kmask ? (kmask[c] >= 8 ? 0.0 : (double)(8 - kmask[c]) * 0.125) : 1.0;
+        xt[c] = BG ? (double)bg[c] : 0.0;
+    }
+    __syncthreads();
+    // right-hand side f (+ N(bg) in the correction form) and its centred norm
+    double fs = 0.0, fq = 0.0;
+    for (int c = t; c < m; c += blockDim.x) {
+        double r = (double)fscale * (double)F[c];
+        if (BG) {
+            const int mm = n - 1, i = c & mm, j = (c / n) & mm, k = c / (n * n);
+            const Stencil<double> s = load_stencil<double>(xt, xt, i, j, k, n);
+            const double kc = kap * wk[c];
+            r += local_eval<double, false>(s, s, ih2, nu, kc, 0.0, 0.0).G;  // N(bg)
+        }
+        rhs[c] = r;
+        fs += r;
+        fq += r * r;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        fs += __shfl_down_sync(0xffffffffu, fs, o);
+        fq += __shfl_down_sync(0xffffffffu, fq, o);
+    }
+    if ((t & 31) == 0) {
+        red[t >> 5] = fs;
+        red[8 + (t >> 5)] = fq;
+    }
+    __syncthreads();
+    double sfs = 0.0, sfq = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+        sfs += red[q];
+        sfq += red[8 + q];
+    }
+    const double fnorm = sqrt(fmax(sfq - sfs * sfs / (double)m, 0.0));
+    double msum = 0.0;
+    for (int c = 0; c < m; ++c) msum += x[c];  // every thread, the same order
+    __syncthreads();
+    double lam = 0.0;
+    double nrm = exact_eval<true>(x, lam, rhs, wk, n, ih2, nu, kap, eta, Fv, J, LD, red, scale, msum);
+    for (int it = 0; it < kExactMaxIter; ++it) {
+        if (!(nrm > 1e-14 * fnorm) || nrm == 0.0) break;
+        // J d = -F by LU with partial pivoting (the multipliers stored below the diagonal)
+        for (int q = t; q < M; q += blockDim.x) b[q] = -Fv[q];
+        if (t == 0) singular = false;
+        __syncthreads();
+        for (int k = 0; k < M; ++k) {
+            if (t < 32) {
+                double best = -1.0;
+                int bi = k;
+                for (int i = k + t; i < M; i += 32) {
+                    const double v = fabs(J[(size_t)i * LD + k]);
+                    if (v > best) {
+                        best = v;
+                        bi = i;
+                    }
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    const double ov = __shfl_down_sync(0xffffffffu, best, o);
+                    const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+                    if (ov > best || (ov == best && oi < bi)) {
+                        best = ov;
+                        bi = oi;
+                    }
+                }
+                if (t == 0) {
+                    piv = bi;
+                    if (best == 0.0) singular = true;
+                }
+            }
+            __syncthreads();
+            if (singular) break;
+            const int p = piv;
+            if (p != k) {
+                for (int q = k + t; q < M; q += blockDim.x) {
+                    const double a = J[(size_t)k * LD + q];
+                    J[(size_t)k * LD + q] = J[(size_t)p * LD + q];
+                    J[(size_t)p * LD + q] = a;
+                }
+                if (t == 0) {
+                    const double a = b[k];
+                    b[k] = b[p];
+                    b[p] = a;
+                }
+                __syncthreads();
+            }
+            const double dinv = 1.0 / J[(size_t)k * LD + k];
+            for (int i = k + 1 + t; i < M; i += blockDim.x) J[(size_t)i * LD + k] *= dinv;
+            __syncthreads();
+            const int w = M - k;  // columns k..M-1; column k carries the right-hand side update
+            for (int q = t; q < (M - k - 1) * w; q += blockDim.x) {
+                const int i = k + 1 + q / w, j = k + q % w;
+                const double l = J[(size_t)i * LD + k];
+                if (j == k) b[i] -= l * b[k];
+                else J[(size_t)i * LD + j] -= l * J[(size_t)k * LD + j];
+            }
+            __syncthreads();
+        }
+        if (singular) break;
+        for (int k = M - 1; k >= 0; --k) {
+            if (t == 0) b[k] /= J[(size_t)k * LD + k];
+            __syncthreads();
+            for (int i = t; i < k; i += blockDim.x) b[i] -= J[(size_t)i * LD + k] * b[k];
+            __syncthreads();
+        }
+        // backtracking line search on |F|
+        double step = 1.0, nt = nrm, lt = lam;
+        for (;;) {
+            for (int c = t; c < m; c += blockDim.x) xt[c] = x[c] + step * b[c];
+            lt = lam + step * b[m];
+            __syncthreads();
+            nt = exact_eval<false>(xt, lt, rhs, wk, n, ih2, nu, kap, eta, Fv, J, LD, red, scale, msum);
+            if (nt < (1.0 - 1e-4 * step) * nrm || step < 1e-4) break;
+            step *= 0.5;
+        }
+        if (!(nt < nrm)) break;  // no decrease along the Newton direction: keep the iterate
+        for (int c = t; c < m; c += blockDim.x) x[c] = xt[c];
+        lam = lt;
+        __syncthreads();
+        nrm = exact_eval<true>(x, lam, rhs, wk, n, ih2, nu, kap, eta, Fv, J, LD, red, scale, msum);
+    }
+    for (int c = t; c < m; c += blockDim.x) u[c] = (T)(x[c] - (BG ? (double)bg[c] : 0.0));
+    if (lam_out && t == 0) *lam_out = lam;
+}
+
 // ------------------------------------------------------------------ misc
 
 template <typename T>
@@ -574,6 +806,15 @@ __global__ void k_add_correction(double* __restrict__ x, const float* __restrict
 {
     for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x)
         x[c] += (double)e[c];
+}
+
+// x += e - <e> in FP64, the mean of e read from the device (sums[0] = sum e)
+__global__ void k_add_correction_centred(double* __restrict__ x, const float* __restrict__ e, size_t total,
+                                         const double* __restrict__ sums)
+{
+    const double mean = sums[0] / (double)total;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x)
+        x[c] += (double)e[c] - mean;
 }
 
 // ------------------------------------------------------------------ host drivers
@@ -900,6 +1141,17 @@ static void vcycle(Exec* ctx, std::vector<Level<T>>& lv, int l, const T* F0, T f
     const int nlev = (int)lv.size();
     if (l == nlev - 1) {
         const double ih2 = (double)L.n * (double)L.n;
+        if (ctx->prm.coarse_exact && L.cells <= (size_t)kExactMaxCells) {
+            ctx->begin(PM_K_COARSEST, false, 0);
+            if (L.bg)
+                k_coarsest_exact<T, true><<<1, kExactThreads, 0, ctx->stream>>>(
+                    L.u[L.cur], F, fs, L.kmask, L.bg, L.n, ih2, c.nu, c.kap, c.eta, nullptr);
+            else
+                k_coarsest_exact<T, false><<<1, kExactThreads, 0, ctx->stream>>>(
+                    L.u[L.cur], F, fs, L.kmask, nullptr, L.n, ih2, c.nu, c.kap, c.eta, nullptr);
+            ctx->end();
+            return;
+        }
         if (L.bg) {
             ctx->begin(PM_K_COARSEST, false, 0);
             k_coarsest<T, true><<<1, 256, 0, ctx->stream>>>(L.u[L.cur], F, fs, L.kmask, L.bg, L.n, ih2, c.nu, c.kap,
@@ -1088,8 +1340,27 @@ pm_status mg_solve(pm_ctx* pctx, const double* delta, int n, const pm_coeffs& cf
     }
     Workspace* w = nullptr;
     PM_TRY(get_workspace(pctx, n, &w));
-    const bool mixed = P.precision == 1;
+    // mixed: an FP32 inner cycle on the correction; ffo: its outer loop in float-float
+    // (precision 1), else in FP64 (precision 2)
+    const bool mixed = P.precision >= 1;
+    const bool ffo = P.precision == 1;
     PM_TRY(ensure_mg(pctx, w, mixed));
+    // The BF16 background coefficients of the finest inner level are written by the
+    // float-float residual only: with the FP64 outer residual that level sweeps through the
+    // background's own planes (the coefficient pointer is hidden for this solve).
+    struct CoefHide {
+        Level<float>* L = nullptr;
+        uint32_t* saved = nullptr;
+        ~CoefHide()
+        {
+            if (L) L->coef = saved;
+        }
+    } hide;
+    if (mixed && !ffo) {
+        hide.L = &w->s[0];
+        hide.saved = w->s[0].coef;
+        w->s[0].coef = nullptr;
+    }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -1100,10 +1371,11 @@ pm_status mg_solve(pm_ctx* pctx, const double* delta, int n, const pm_coeffs& cf
     Level<double>& L0 = w->d[0];
     L0.cur = 0;
     PM_CUDA(cudaMemcpyAsync(L0.u[0], phi, cells * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-    float2* xff = mixed ? ff_chi(w) : nullptr;
-    float2* fff = mixed ? ff_rhs(w) : nullptr;
+    float2* xff = ffo ? ff_chi(w) : nullptr;
+    float2* fff = ffo ? ff_rhs(w) : nullptr;
     const FFCoef fk = make_ffcoef(cf.nu, cf.kappa, P.eta, n);
-    if (mixed) {
+    if (mixed && !ffo) recentre<double>(ctx, L0.u[0], cells);
+    if (ffo) {
         recentre<double>(ctx, L0.u[0], cells);
         ctx->begin(PM_K_REDUCE, false, 0);
         k_to_ff<<<grid_for(ctx, cells), kThreads, 0, ctx->stream>>>(delta, cf.src, cells, fff);
@@ -1120,11 +1392,15 @@ pm_status mg_solve(pm_ctx* pctx, const double* delta, int n, const pm_coeffs& cf
     // other buffer
     const float* pend = nullptr;
     for (;;) {
-        if (mixed) {
+        if (ffo) {
             float2* xo = xff == ff_chi(w) ? w->ff_alt : ff_chi(w);
             residual_ff(ctx, w, xff, fff, lam, nullptr, fk, pend, pend ? xo : nullptr);
             if (pend) xff = xo;
             pend = nullptr;
+        } else if (mixed) {
+            // FP64 outer residual; it also writes the inner right-hand side, background and gap
+            residual<double, false, true>(ctx, L0, L0.u[L0.cur], delta, cf.src, lam, c, w->rplain, w->s[0].bg,
+                                          w->s[0].gap);
         } else
             residual<double, false, false>(ctx, L0, L0.u[L0.cur], delta, cf.src, lam, c, nullptr, nullptr);
         PM_TRY(read_sums(ctx, 9));
@@ -1139,7 +1415,7 @@ pm_status mg_solve(pm_ctx* pctx, const double* delta, int n, const pm_coeffs& cf
                 // the guess is far worse than chi = 0: start from zero instead
                 inf->guess_rejected = 1;
                 lam = 0.0;
-                if (mixed)
+                if (ffo)
                     PM_CUDA(cudaMemsetAsync(xff, 0, cells * sizeof(float2), ctx->stream));
                 else
                     PM_CUDA(cudaMemsetAsync(L0.u[L0.cur], 0, cells * sizeof(double), ctx->stream));
@@ -1153,7 +1429,7 @@ pm_status mg_solve(pm_ctx* pctx, const double* delta, int n, const pm_coeffs& cf
             break;
         }
         if (rr <= tol || fnorm == 0.0) {
-            if (!mixed) {
+            if (!ffo) {
                 st = PM_OK;
                 break;
             }
@@ -1191,7 +1467,14 @@ pm_status mg_solve(pm_ctx* pctx, const double* delta, int n, const pm_coeffs& cf
                 vcycle<float>(ctx, s, 0, w->rplain, 1.0f, (float)(-gm), c);
                 ++vcyc;
             }
-            if (n >= kFzTX) {
+            if (!ffo) {
+                // FP64 iterate: chi += e - <e>
+                correction_sum(ctx, s[0].u[s[0].cur], cells);
+                ctx->begin(PM_K_REDUCE, false, 0);
+                k_add_correction_centred<<<grid_for(ctx, cells), kThreads, 0, ctx->stream>>>(
+                    L0.u[L0.cur], s[0].u[s[0].cur], cells, ctx->red_out + 16);
+                ctx->end();
+            } else if (n >= kFzTX) {
                 correction_sum(ctx, s[0].u[s[0].cur], cells);
                 pend = s[0].u[s[0].cur];
             } else {
@@ -1204,13 +1487,15 @@ pm_status mg_solve(pm_ctx* pctx, const double* delta, int n, const pm_coeffs& cf
         }
         ++cyc;
     }
-    if (mixed) {
+    if (ffo) {
         if (st != PM_OK) {
             ctx->begin(PM_K_REDUCE, false, 0);
             k_from_ff<<<grid_for(ctx, cells), kThreads, 0, ctx->stream>>>(xff, cells, L0.u[0]);
             ctx->end();
         }
         recentre<double>(ctx, L0.u[0], cells);  // <chi> = 0 to FP64 rounding
+    } else if (mixed) {
+        recentre<double>(ctx, L0.u[L0.cur], cells);
     }
     PM_CUDA(cudaMemcpyAsync(phi, L0.u[L0.cur], cells * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
     cudaEventRecord(e1, ctx->stream);
@@ -1339,6 +1624,26 @@ extern "C" pm_status pm_mg_prolong_add(pm_ctx* ctx, const double* coarse, int n,
                                                                                                 fine);
     ctx->end();
     PM_CUDA(cudaGetLastError());
+    return PM_OK;
+}
+
+extern "C" pm_status pm_mg_coarse_exact(pm_ctx* ctx, double* u, const double* f, int n, double nu, double kappa,
+                                        double eta, const unsigned char* kmask, double* lambda_out)
+{
+    if (!ctx) return PM_ERR_INVALID_ARG;
+    if (!(n == 2 || n == 4) || !u || !f || nu == 0.0 || !std::isfinite(nu) || !std::isfinite(kappa) ||
+        !(eta >= 0.0 && eta < 1.0)) {
+        ctx->set_error("pm_mg_coarse_exact: n must be 2 or 4, u and f non-null, nu finite and nonzero");
+        return PM_ERR_INVALID_ARG;
+    }
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return PM_ERR_CUDA;
+    double* d_lam = ctx->red_out + 60;  // a slot no solve uses between calls
+    k_coarsest_exact<double, false><<<1, kExactThreads, 0, ctx->stream>>>(
+        u, f, 1.0, kmask, nullptr, n, (double)n * (double)n, nu, kappa, eta, d_lam);
+    PM_CUDA(cudaGetLastError());
+    PM_CUDA(cudaMemcpyAsync(ctx->host_out + 60, d_lam, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (lambda_out) *lambda_out = ctx->host_out[60];
     return PM_OK;
 }
 

@@ -122,13 +122,15 @@ __global__ void k_f2d(const float* __restrict__ x, size_t total, double* __restr
 
 // g = -grad(psiN + xi chi) at each particle: for every one of the 8 CIC corners (in the
 // deposit's corner order) the five-point difference (-f+2 + 8 f+1 - 8 f-1 + f-2)/(12 h) per
-// axis, weighted by the corner's CIC weight.  No force grid is written.
+// axis (FOUR; else the two-point (f+1 - f-1)/(2 h)), weighted by the corner's CIC weight.
+// No force grid is written.
+template <bool FOUR>
 __global__ void __launch_bounds__(256) k_force(const double* __restrict__ psiN, const double* __restrict__ chi,
                                                double xi, int n, const double* __restrict__ pos, long long np,
                                                double* __restrict__ acc)
 {
     const int m = n - 1;
-    const double inv12h = (double)n / 12.0;
+    const double inv12h = (double)n / 12.0, inv2h = (double)n * 0.5;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (long long)gridDim.x * blockDim.x) {
         int ix[2], iy[2], iz[2];
         double wx[2], wy[2], wz[2];
@@ -145,9 +147,16 @@ __global__ void __launch_bounds__(256) k_force(const double* __restrict__ psiN, 
             const int a = c & 1, b = (c >> 1) & 1, e = (c >> 2) & 1;
             const int i = ix[a], j = iy[b], k = iz[e];
             const double w = __dmul_rn(__dmul_rn(wx[a], wy[b]), wz[e]);
-            const double gx = (-psi(i + 2, j, k) + 8.0 * psi(i + 1, j, k) - 8.0 * psi(i - 1, j, k) + psi(i - 2, j, k)) * inv12h;
-            const double gy = (-psi(i, j + 2, k) + 8.0 * psi(i, j + 1, k) - 8.0 * psi(i, j - 1, k) + psi(i, j - 2, k)) * inv12h;
-            const double gz = (-psi(i, j, k + 2) + 8.0 * psi(i, j, k + 1) - 8.0 * psi(i, j, k - 1) + psi(i, j, k - 2)) * inv12h;
+            double gx, gy, gz;
+            if (FOUR) {
+                gx = (-psi(i + 2, j, k) + 8.0 * psi(i + 1, j, k) - 8.0 * psi(i - 1, j, k) + psi(i - 2, j, k)) * inv12h;
+                gy = (-psi(i, j + 2, k) + 8.0 * psi(i, j + 1, k) - 8.0 * psi(i, j - 1, k) + psi(i, j - 2, k)) * inv12h;
+                gz = (-psi(i, j, k + 2) + 8.0 * psi(i, j, k + 1) - 8.0 * psi(i, j, k - 1) + psi(i, j, k - 2)) * inv12h;
+            } else {
+                gx = (psi(i + 1, j, k) - psi(i - 1, j, k)) * inv2h;
+                gy = (psi(i, j + 1, k) - psi(i, j - 1, k)) * inv2h;
+                gz = (psi(i, j, k + 1) - psi(i, j, k - 1)) * inv2h;
+            }
             s0 += w * -gx;
             s1 += w * -gy;
             s2 += w * -gz;
@@ -271,7 +280,10 @@ pm_status interp_force(pm_ctx* ctx, const double* psiN, const double* chi, doubl
                        long long np, double* acc)
 {
     ctx->begin(PM_K_PM, false, 0);
-    k_force<<<grid_for(ctx, (size_t)np), kThreads, 0, ctx->stream>>>(psiN, chi, xi, n, pos, np, acc);
+    if (ctx->prm.grad_order == 2)
+        k_force<false><<<grid_for(ctx, (size_t)np), kThreads, 0, ctx->stream>>>(psiN, chi, xi, n, pos, np, acc);
+    else
+        k_force<true><<<grid_for(ctx, (size_t)np), kThreads, 0, ctx->stream>>>(psiN, chi, xi, n, pos, np, acc);
     ctx->end();
     PM_CUDA(cudaGetLastError());
     return PM_OK;

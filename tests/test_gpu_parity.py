@@ -206,6 +206,66 @@ def test_mixed_precision_solve(gpu_lib, c1_particles, case):
     assert rel(got.cpu().numpy(), want) < 1e-6
 
 
+def test_exact_coarse_solve_matches_oracle(gpu_lib):
+    """The exact coarsest-level solve (FP64 Newton with a dense Jacobian and LU in one block)
+    against the oracle's on a 4^3 grid with partial screening weights and floored cells."""
+    rng = np.random.default_rng(31)
+    n = 4
+    for aB0, aM0, amp in ((-0.5, 0.0, 0.5), (-2.0, 0.5, 2.0)):
+        c = O.coefficients(aB0, aM0, 1.0)
+        f = O.source(amp * rng.standard_normal((n, n, n)), c)
+        km = rng.integers(0, 9, size=(n, n, n)).astype(np.uint8)
+        u0 = 1e-3 * rng.standard_normal((n, n, n))
+        want, lam_o = O.coarse_exact(u0, f, c["nu"], c["kappa"], kmask=km)
+        got, lam_g = gpu_lib.pm_mg_coarse_exact(cu(u0), cu(f), c["nu"], c["kappa"], 0.35, kmask=cu(km, torch.uint8))
+        assert rel(got.cpu().numpy(), want) < 1e-12
+        assert lam_g == pytest.approx(lam_o, abs=1e-12 * np.abs(f).max())
+
+
+@pytest.mark.parametrize("aB0,aM0", [(-0.5, 0.0), (-2.0, 0.0)])
+def test_fp64_solve_with_exact_coarsest_matches_oracle(gpu_lib, aB0, aM0):
+    """The FP64 cycle with the exact coarsest solve reaches the oracle's chi (which uses the
+    same exact solve) to 1e-10, in the same number of cycles give or take one."""
+    d = synth.lognormal_delta(32, -2.0, 1.5, 1003)
+    want, info_o, st = O.scalar_solve(d, aB0, aM0, 1.0, 1e-13, coarse_exact=True)
+    assert st == 0
+    ctx = gpu_lib.Context(precision=0, max_cycles=200, coarse_exact=1)
+    got, info = gpu_lib.scalar_mg_solve(cu(d), aB0, aM0, 1.0, 1e-13, ctx=ctx)
+    assert info["rel_res"] <= 1e-13
+    assert rel(got.cpu().numpy(), want) < 1e-10
+    assert abs(info["cycles"] - info_o["cycles"]) <= 1
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("aB0,aM0", [(-0.5, 0.0), (-2.0, 0.5)])
+def test_mixed_solves_with_exact_coarsest_and_fp64_outer_loop(gpu_lib, precision, aB0, aM0):
+    """The FP32 inner cycle with the exact FP64 coarsest solve (correction form), under the
+    float-float (precision 1) and the FP64 (precision 2) outer loop, at 64^3: residual 1e-8
+    and chi within 1e-6 of the oracle."""
+    d = synth.lognormal_delta(64, -2.0, 1.5, 1003)
+    want, _, st = O.scalar_solve(d, aB0, aM0, 1.0, 1e-12)
+    assert st == 0
+    for exact in (0, 1):
+        ctx = gpu_lib.Context(precision=precision, max_cycles=200, coarse_exact=exact)
+        got, info = gpu_lib.scalar_mg_solve(cu(d), aB0, aM0, 1.0, 1e-8, ctx=ctx)
+        assert info["rel_res"] <= 1e-8
+        assert rel(got.cpu().numpy(), want) < 1e-6, (precision, exact, info["cycles"])
+
+
+def test_two_point_gradient_option_matches_oracle(gpu_lib, c1_particles):
+    """pm_params.grad_order = 2: the force with the two-point central difference."""
+    n = 32
+    rng = np.random.default_rng(18)
+    psi = rng.standard_normal((n, n, n))
+    chi = rng.standard_normal((n, n, n))
+    pos = np.concatenate([c1_particles, rng.random((3, 777))], axis=1)
+    c = O.coefficients(-1.0, 0.2, 1.0)
+    want = O.interp_cic(O.accel_grid(psi, chi, c["xi"], n, order=2), pos)
+    ctx = gpu_lib.Context(grad_order=2)
+    got = gpu_lib.force_interp(cu(psi), cu(chi), -1.0, 0.2, 1.0, cu(pos), ctx=ctx).cpu().numpy()
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
 def test_solve_zero_coupling_and_errors(gpu_lib):
     n = 16
     d = cu(synth.lognormal_delta(n, -2.0, 1.0, 1))

@@ -401,6 +401,56 @@ def test_fas_matches_dense_newton_8cubed(amp):
     assert info["lambda"] == pytest.approx(lam, abs=1e-10 * np.abs(f).max())
 
 
+@pytest.mark.parametrize("amp", [0.5, 3.0])
+def test_exact_coarse_solve_matches_dense_newton_8cubed(amp):
+    """The exact coarsest-level solve (Newton, analytic dense Jacobian, LU; Sec. 3.4 FAS reading)
+    run as the only level of an 8^3 grid is the whole discrete problem: it must land on the
+    brute-force Newton solution (finite-difference Jacobian) to 1e-12, with the same lambda."""
+    rng = np.random.default_rng(21)
+    n = 8
+    g = rng.standard_normal((n, n, n))
+    d = amp * (g - g.mean())
+    c = O.coefficients(-0.5, 0.0, 1.0)
+    f = O.source(d, c)
+    chi_ex, info, st = O.mg_solve(f, c["nu"], c["kappa"], 1e-14, coarsest_n=8, coarse_exact=True)
+    assert st == 0 and info["cycles"] <= 4
+    chi_nt, lam, _ = _newton_dense(f, c["nu"], c["kappa"], O.ETA_DEFAULT, _fft_linear_solve(f, c["nu"]))
+    assert np.linalg.norm(chi_ex - chi_nt) / np.linalg.norm(chi_nt) < 1e-12
+    assert info["lambda"] == pytest.approx(lam, abs=1e-10 * np.abs(f).max())
+    if amp == 3.0:
+        assert info["sat_cells"] > 0  # the floored pieces are part of the solved system
+
+
+def test_exact_coarse_solve_alone_zeroes_the_residual_with_a_mask():
+    """One exact solve of a 4^3 level with partial screening weights: every residual piece of
+    R-res vanishes to 1e-12 of |f| at the returned lambda, and the mean of the start is kept."""
+    rng = np.random.default_rng(31)
+    n = 4
+    c = O.coefficients(-2.0, 0.5, 1.0)
+    f = O.source(2.0 * rng.standard_normal((n, n, n)), c)
+    km = rng.integers(0, 9, size=(n, n, n)).astype(np.uint8)
+    u0 = 1e-3 * rng.standard_normal((n, n, n))
+    u, lam = O.coarse_exact(u0, f, c["nu"], c["kappa"], kmask=km)
+    r, sat = O.residual(u, f, lam, c["nu"], c["kappa"], O.ETA_DEFAULT, kmask=km)
+    assert np.abs(r).max() < 1e-12 * np.abs(f).max()
+    assert u.mean() == pytest.approx(u0.mean(), abs=1e-15)
+
+
+@pytest.mark.parametrize("aB0,aM0", [(-0.5, 0.0), (-2.0, 0.0), (-2.0, 0.5)])
+def test_exact_coarsest_level_keeps_the_solution(aB0, aM0):
+    """The coarse solve only changes how the FAS cycle converges: with the exact coarsest solve
+    the 32^3 lognormal problems (floored, nu < 0 included) reach the same chi to 1e-10 in no more
+    cycles than with sweeps."""
+    d = synth.lognormal_delta(32, -2.0, 1.5, 1003)
+    c = O.coefficients(aB0, aM0, 1.0)
+    f = O.source(d, c)
+    a, ia, sa = O.mg_solve(f, c["nu"], c["kappa"], 1e-12)
+    b, ib, sb = O.mg_solve(f, c["nu"], c["kappa"], 1e-12, coarse_exact=True)
+    assert sa == 0 and sb == 0
+    assert np.linalg.norm(a - b) / np.linalg.norm(a) < 1e-10
+    assert ib["cycles"] <= ia["cycles"]
+
+
 def test_solution_commutes_with_axis_permutation():
     pos = synth.zeldovich_particles(16, -1.5, 1.0, 1234, nyquist_cutoff=True)
     d = O.density(O.deposit_cic(pos, 16), pos.shape[1])
@@ -573,6 +623,27 @@ def test_five_point_gradient_spectral_factor():
         assert np.allclose(g[0, 0, 0, :], want, atol=1e-12 * k)
         assert np.allclose(g[1], 0.0, atol=1e-9) and np.allclose(g[2], 0.0, atol=1e-9)
         assert abs(fac - (1 - t ** 4 / 30)) < t ** 6
+
+
+def test_two_point_gradient_spectral_factor():
+    """The grad_order = 2 option: the two-point central difference on a sinusoid gives the
+    derivative times sin(t)/t, t = k h, which is 1 - t^2/6 + O(t^4) (second order); each axis
+    sees only its own variation."""
+    n = 32
+    x = (np.arange(n) + 0.5) / n
+    for m, axis in ((1, 0), (3, 2)):
+        k = 2 * np.pi * m
+        prof = np.sin(k * x)
+        psi = np.broadcast_to(prof[None, None, :] if axis == 0 else prof[:, None, None], (n, n, n)).copy()
+        g = O.accel_grid(psi, None, 0.0, n, order=2)
+        t = k / n
+        fac = np.sin(t) / t
+        want = -k * np.cos(k * x) * fac
+        line = g[0, 0, 0, :] if axis == 0 else g[2, :, 0, 0]
+        assert np.allclose(line, want, atol=1e-12 * k)
+        others = [d for d in range(3) if d != axis]
+        assert all(np.allclose(g[d], 0.0, atol=1e-9) for d in others)
+        assert abs(fac - (1 - t ** 2 / 6)) < t ** 4 / 100
 
 
 def test_force_adds_fifth_force_with_coupling():
