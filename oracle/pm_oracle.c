@@ -657,7 +657,7 @@ static double exact_system(const level_t* L, const orc_mg_params* prm, int perio
     return sqrt(f2);
 }
 
-static void coarse_exact(level_t* L, const orc_mg_params* prm, int periodic)
+static double coarse_exact(level_t* L, const orc_mg_params* prm, int periodic)
 {
     int n = L->n, m = n * n * n, M = m + (periodic ? 1 : 0);
     size_t mp = (size_t)(n + 2) * (n + 2) * (n + 2);
@@ -697,13 +697,14 @@ static void coarse_exact(level_t* L, const orc_mg_params* prm, int periodic)
         nrm = exact_system(L, prm, periodic, L->p, lam, msum, F, J);
     }
     free(J); free(F); free(Ft); free(pt);
+    return lam;
 }
 
 static void vcycle(level_t* lv, int l, int nlev, double lam, const orc_mg_params* prm, int periodic)
 {
     level_t* L = &lv[l];
     if (l == nlev - 1) {
-        if (prm->coarse_exact) coarse_exact(L, prm, periodic);
+        if (prm->coarse_exact) (void)coarse_exact(L, prm, periodic);
         else coarse_solve(L, prm, periodic);
         return;
     }
@@ -779,17 +780,11 @@ double orc_coarse_exact(double* u, const double* f, int n, double h, double nu, 
     prm.nu = nu;
     prm.kappa = kap;
     prm.eta = eta;
-    coarse_exact(&L, &prm, 1);
+    double lam = coarse_exact(&L, &prm, 1);
     unpad_to(L.p, n, u);
-    /* the multiplier of the solution: the mean residual of the unfloored cells at lambda 0 */
-    double* r = (double*)malloc(m * sizeof(double));
-    unsigned char* sat = (unsigned char*)malloc(m);
-    residual_padded(L.p, f, 0.0, n, h, nu, kap, eta, kmask, NULL, r, sat);
-    double s = 0.0, w = 0.0;
-    for (size_t i = 0; i < m; ++i)
-        if (!sat[i]) { s += r[i]; w += 1.0; }
-    free(r); free(sat); free(L.p); free(L.f);
-    return w > 0.0 ? -s / w : 0.0;
+    free(L.p);
+    free(L.f);
+    return lam;
 }
 
 /*
