@@ -313,8 +313,11 @@ pm_status pm_mg_sweep(pm_ctx* ctx, double* u, const double* f, double lambda, in
                       double eta, const unsigned char* kmask);
 /* The same sweep on an FP32 grid: mode 0 runs the two half-sweep kernels, mode k >= 1
  * the single-pass fused kernel with tile variant k-1 (pm_tune_log lists the variants the
- * autotuner chose; the inner FP32 cycle uses the fused kernel for grids >= 256^3).  A
- * variant that does not tile n falls back to mode 0.  u, f: device n^3 float.
+ * autotuner chose; the inner FP32 cycle uses the fused kernel for grids >= 256^3), and
+ * mode 100 + k variant k-1 with the background entering through its six bilinear
+ * coefficients rounded to BF16 (the form in which the finest inner level of grids >= 256^3
+ * receives it; needs bg and gap and no kmask).  A variant that does not tile n or cannot
+ * take these inputs falls back to mode 0.  u, f: device n^3 float.
  * bg (nullable): the correction form of the mixed-precision inner cycle, where u is the
  * correction to the background bg and the operator is N(bg + u) - N(bg); gap (nullable,
  * needs bg): L_sat - L(bg) per cell, as the finest inner level receives it from the outer

@@ -169,6 +169,7 @@ void delete_workspace(Workspace* w)
     for (auto& L : w->s) free_level(L);
     cudaFree(w->rplain);
     cudaFree(w->ff_alt);
+    cudaFree(w->coef_test);
     cudaFree(w->psi);
     cudaFree(w->delta);
     cudaFree(w->acc);

@@ -157,6 +157,7 @@ struct Workspace {
     float* rplain = nullptr;       // FP32 inner right-hand side f + lambda - N(chi) at level 0
     float2* ff_alt = nullptr;      // second float-float iterate buffer (the residual writes the corrected
                                    // iterate out of place)
+    uint32_t* coef_test = nullptr; // coefficients of a caller's background (pm_mg_sweep_f32, mode > 100)
     double* psi = nullptr;         // scratch n^3 (Poisson output / total potential)
     double* delta = nullptr;       // scratch n^3 (pm_step)
     long long* acc = nullptr;      // int64 fixed-point deposit grid

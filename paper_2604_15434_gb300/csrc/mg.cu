@@ -16,6 +16,7 @@
 #include "internal.cuh"
 #include "sweep_fused.cuh"
 #include "sweep_pair.cuh"
+#include "sweep_col.cuh"
 #include "outer_ff.cuh"
 #include "resid_fused.cuh"
 
@@ -808,6 +809,25 @@ __global__ void k_add_correction(double* __restrict__ x, const float* __restrict
         x[c] += (double)e[c];
 }
 
+// The bilinear coefficients of a background field b (BgCoef in internal.cuh) packed to BF16
+// pairs, as the finest inner level of a large solve receives them from the outer residual:
+// (2(Yb+Zb), 2(Xb+Zb)), (2(Xb+Yb), -bxy/4), (-bxz/4, -byz/4), h = 1 units.
+__global__ void k_bg_coef(const float* __restrict__ bg, int n, uint32_t* __restrict__ coef)
+{
+    const size_t total = (size_t)n * n * n;
+    const int lg = __ffs(n) - 1;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(c & (size_t)(n - 1));
+        const size_t row = c >> lg;
+        const int j = (int)(row & (size_t)(n - 1)), k = (int)(row >> lg);
+        const Stencil<float> b = load_stencil<float>(bg, bg, i, j, k, n);
+        const float Xb = b.ax - 2.f * b.c0, Yb = b.ay - 2.f * b.c0, Zb = b.az - 2.f * b.c0;
+        coef[c] = pack_bf16x2(2.f * (Yb + Zb), 2.f * (Xb + Zb));
+        coef[total + c] = pack_bf16x2(2.f * (Xb + Yb), -0.25f * b.exy);
+        coef[2 * total + c] = pack_bf16x2(-0.25f * b.exz, -0.25f * b.eyz);
+    }
+}
+
 // x += e - <e> in FP64, the mean of e read from the device (sums[0] = sum e)
 __global__ void k_add_correction_centred(double* __restrict__ x, const float* __restrict__ e, size_t total,
                                          const double* __restrict__ sums)
@@ -831,12 +851,16 @@ struct FusedCfg {
     int tx, ty, nz;
     bool pair;  // k_sweep_pair (two cells per thread) instead of k_sweep_fused
     bool bal;   // k_sweep_pair with one warp per red unit (coefficient levels)
+    bool col;   // k_sweep_col (column-resident stencils; coefficient levels without a mask)
 };
 static const FusedCfg kFusedCfgs[] = {
-    {64, 16, 32, false, false}, {64, 8, 32, false, false}, {64, 8, 64, false, false}, {32, 8, 32, false, false},
-    {32, 8, 64, false, false},  {64, 4, 64, false, false}, {64, 16, 16, false, false}, {64, 8, 16, false, false},
-    {64, 8, 32, true, false},   {64, 8, 64, true, false},  {64, 16, 32, true, false},  {64, 16, 64, true, false},
-    {64, 4, 64, true, false},   {64, 8, 16, true, false},  {64, 16, 32, true, true},   {64, 8, 32, true, true}};
+    {64, 16, 32, false, false, false}, {64, 8, 32, false, false, false}, {64, 8, 64, false, false, false},
+    {32, 8, 32, false, false, false},  {32, 8, 64, false, false, false}, {64, 4, 64, false, false, false},
+    {64, 16, 16, false, false, false}, {64, 8, 16, false, false, false}, {64, 8, 32, true, false, false},
+    {64, 8, 64, true, false, false},   {64, 16, 32, true, false, false}, {64, 16, 64, true, false, false},
+    {64, 4, 64, true, false, false},   {64, 8, 16, true, false, false},  {64, 16, 32, true, true, false},
+    {64, 8, 32, true, true, false},    {64, 8, 32, false, false, true},  {64, 8, 64, false, false, true},
+    {64, 16, 32, false, false, true},  {64, 16, 64, false, false, true}};
 constexpr int kNumFusedCfgs = sizeof(kFusedCfgs) / sizeof(kFusedCfgs[0]);
 
 template <int TX, int TY, bool BG, bool GAP>
@@ -866,11 +890,32 @@ static void launch_pair(Exec* ctx, const float* A, float* B, const float* F, flo
                                                    COEF ? L.coef : nullptr);
 }
 
+template <int TY>
+static void launch_col(Exec* ctx, const float* A, float* B, const float* F, float fscale, float lam,
+                       const Level<float>& L, int nz, float h2inv, const Coef& c, float sp, float Df, float lsn)
+{
+    const int n = L.n;
+    constexpr size_t sm = col_smem_bytes<TY>();
+    auto k = k_sweep_col<TY>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const dim3 grid(n / 64, n / TY, n / nz);
+    k<<<grid, ColGeom<TY>::NT, sm, ctx->stream>>>(A, B, F, fscale, lam, L.gap, n, nz, h2inv, (float)c.nu,
+                                                  (float)c.kap, sp, Df, lsn, L.lamp, L.coef);
+}
+
+// the column kernel's inputs: background coefficients and gap, no screening mask
+static bool col_level(const Level<float>& L) { return L.bg && L.gap && L.coef && !L.kmask; }
+
 template <bool BG, bool GAP>
 static void launch_fused_cfg(Exec* ctx, int cfg, const float* A, float* B, const float* F, float fscale, float lam,
                              const Level<float>& L, float h2inv, const Coef& c, float sp, float Df, float lsn)
 {
     const FusedCfg& g = kFusedCfgs[cfg];
+    if (g.col) {
+        if (g.ty == 8) launch_col<8>(ctx, A, B, F, fscale, lam, L, g.nz, h2inv, c, sp, Df, lsn);
+        else launch_col<16>(ctx, A, B, F, fscale, lam, L, g.nz, h2inv, c, sp, Df, lsn);
+        return;
+    }
 #define PM_FUSED_CASE(TX_, TY_)                                                                        \
     if (!g.pair && g.tx == TX_ && g.ty == TY_) {                                                       \
         launch_fused<TX_, TY_, BG, GAP>(ctx, A, B, F, fscale, lam, L, g.nz, h2inv, c, sp, Df, lsn);    \
@@ -903,6 +948,18 @@ static bool fused_cfg_fits(int cfg, int n)
     return n >= g.tx && n >= g.ty && n >= g.nz && n % g.tx == 0 && n % g.ty == 0 && n % g.nz == 0;
 }
 
+// a variant that can sweep level L: the column kernel only on coefficient levels without a
+// mask, the balanced pair kernel only on coefficient levels
+static bool fused_cfg_usable(int cfg, const Level<float>& L)
+{
+    const FusedCfg& g = kFusedCfgs[cfg];
+    if (!fused_cfg_fits(cfg, L.n)) return false;
+    if (g.col) return col_level(L);
+    if (g.bal) return L.coef && L.gap;
+    if (L.coef && L.gap) return g.pair;  // only the pair kernels read coefficients
+    return true;
+}
+
 // One red-black sweep of an FP32 level in a single pass (k_sweep_fused) with tile variant cfg.
 static void sweep_fused_f32(Exec* ctx, Level<float>& L, const float* F, float fscale, float lam, const Coef& c,
                             int cfg)
@@ -929,7 +986,7 @@ static void sweep_fused_f32(Exec* ctx, Level<float>& L, const float* F, float fs
 static int tuned_cfg(Exec* ctx, Level<float>& L, const float* F, float fscale, float lam, const Coef& c)
 {
     const bool cf = L.coef && L.gap;
-    const int key = L.n * 8 + (cf ? 4 : 0) + (L.bg ? 2 : 0) + (L.gap ? 1 : 0);
+    const int key = L.n * 16 + (L.kmask ? 8 : 0) + (cf ? 4 : 0) + (L.bg ? 2 : 0) + (L.gap ? 1 : 0);
     auto it = ctx->tuned.find(key);
     if (it != ctx->tuned.end()) return it->second;
     int best = 0;
@@ -944,9 +1001,7 @@ static int tuned_cfg(Exec* ctx, Level<float>& L, const float* F, float fscale, f
         const bool was = ctx->c->tracing;
         ctx->c->tracing = false;
         for (int cfg = 0; cfg < kNumFusedCfgs; ++cfg) {
-            if (!fused_cfg_fits(cfg, L.n)) continue;
-            if (L.coef && L.gap && !kFusedCfgs[cfg].pair) continue;  // only the pair kernel reads coefficients
-            if (kFusedCfgs[cfg].bal && !(L.coef && L.gap)) continue;  // the balanced form exists for them only
+            if (!fused_cfg_usable(cfg, L)) continue;
             // one untimed launch, then three timed back to back
             for (int rep = 0; rep < 2; ++rep) {
                 const int launches = rep == 0 ? 1 : 3;
@@ -973,9 +1028,11 @@ static int tuned_cfg(Exec* ctx, Level<float>& L, const float* F, float fscale, f
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         ctx->tune_log += "sweep32 n=" + std::to_string(L.n) + (L.bg ? " bg" : "") + (L.gap ? " gap" : "") +
+                         (L.kmask ? " mask" : "") +
                          (cf ? " coef" : "") +
                          ": tile " + std::to_string(kFusedCfgs[best].tx) + "x" + std::to_string(kFusedCfgs[best].ty) +
-                         " nz " + std::to_string(kFusedCfgs[best].nz) + (kFusedCfgs[best].pair ? (kFusedCfgs[best].bal ? " pair bal" : " pair") : " single") +
+                         " nz " + std::to_string(kFusedCfgs[best].nz) +
+                         (kFusedCfgs[best].col ? " col" : kFusedCfgs[best].pair ? (kFusedCfgs[best].bal ? " pair bal" : " pair") : " single") +
                          " " + std::to_string(best_ms) + " ms (variants tried, ms:" + trials + ")\n";
     }
     ctx->tuned[key] = best;
@@ -989,7 +1046,7 @@ static void sweep(Exec* ctx, Level<T>& L, const T* F, T fscale, T lam, const Coe
     // half-sweep launches, 1: single pass, -1: choose by size)
     if constexpr (sizeof(T) == 4) {
         // force_mode >= 1 selects tile variant force_mode - 1
-        if (force_mode >= 1 && force_mode <= kNumFusedCfgs && fused_cfg_fits(force_mode - 1, L.n)) {
+        if (force_mode >= 1 && force_mode <= kNumFusedCfgs && fused_cfg_usable(force_mode - 1, L)) {
             sweep_fused_f32(ctx, L, F, fscale, lam, c, force_mode - 1);
             return;
         }
@@ -1558,7 +1615,11 @@ extern "C" pm_status pm_mg_sweep_f32(pm_ctx* ctx, float* u, const float* f, floa
                                      const float* gap, int mode)
 {
     PM_TRY(check_mg_args(ctx, n));
-    if (!u || !f || mode < 0 || mode > kNumFusedCfgs || (gap && !bg)) return PM_ERR_INVALID_ARG;
+    // mode 100 + k: variant k - 1 with the background entering through its BF16 coefficients
+    const bool via_coef = mode > 100;
+    if (via_coef) mode -= 100;
+    if (!u || !f || mode < 0 || mode > kNumFusedCfgs || (gap && !bg) || (via_coef && (!bg || !gap || kmask)))
+        return PM_ERR_INVALID_ARG;
     Workspace* w = nullptr;
     PM_TRY(get_workspace(ctx, n, &w));
     PM_TRY(ensure_mg(ctx, w, true));
@@ -1569,6 +1630,12 @@ extern "C" pm_status pm_mg_sweep_f32(pm_ctx* ctx, float* u, const float* f, floa
     L.coef = nullptr;  // the background is the caller's field, not the solve's coefficients
     L.cur = 0;
     const size_t cells = L.cells;
+    if (via_coef) {
+        if (!w->coef_test) PM_CUDA(cudaMalloc(&w->coef_test, 3 * cells * sizeof(uint32_t)));
+        L.coef = w->coef_test;
+        k_bg_coef<<<grid_for(ctx, cells), kThreads, 0, ctx->stream>>>(bg, n, L.coef);
+        PM_CUDA(cudaGetLastError());
+    }
     PM_CUDA(cudaMemcpyAsync(L.u[0], u, cells * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
     Coef c{nu, kappa, eta, 1.0};
     Exec ex(ctx);

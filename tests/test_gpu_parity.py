@@ -376,6 +376,32 @@ def test_every_fused_tile_variant_equals_half_sweeps(gpu_lib, variant, mode):
     assert np.sqrt(np.mean((a - b) ** 2)) <= 1e-6 * np.sqrt(np.mean(a ** 2))
 
 
+PAIR_COEF_MODE = 100 + 9  # pair kernel, tile 64 x 8, 32 planes, background through BF16 coefficients
+
+
+@pytest.mark.parametrize("n", [64, 128, 256])
+@pytest.mark.parametrize("mode", [17, 18, 19, 20])
+def test_column_sweep_equals_pair_coefficient_sweep(gpu_lib, n, mode):
+    """The column-resident sweep (k_sweep_col, tiles 64 x 8 / 64 x 16, 32 / 64 planes per block)
+    against the pair kernel on the same BF16 background coefficients and gap: the same formulas
+    in FP32 up to rounding order, on grids that give one and several blocks in every direction."""
+    u, f, c = _sweep_inputs(n, 700 + n, 0.5)
+    rng = np.random.default_rng(n + mode)
+    bg = cu(2.0 * rng.standard_normal((n, n, n)) / n ** 2, torch.float32)
+    lsat = 0.75 * c["nu"] * (1 - 0.35) / c["kappa"]
+    gap = cu(lsat * (1.0 + 0.5 * rng.standard_normal((n, n, n))), torch.float32)
+    args = (cu(f, torch.float32), 0.01, c["nu"], c["kappa"], 0.35)
+    want = gpu_lib.pm_mg_sweep_f32(cu(u, torch.float32), *args, mode=PAIR_COEF_MODE, bg=bg, gap=gap).cpu().numpy()
+    got = gpu_lib.pm_mg_sweep_f32(cu(u, torch.float32), *args, mode=100 + mode, bg=bg, gap=gap).cpu().numpy()
+    assert np.isfinite(got).all()
+    assert np.abs(got - want).max() <= 1e-5 * np.abs(want).max()
+    assert np.sqrt(np.mean((got - want) ** 2)) <= 1e-6 * np.sqrt(np.mean(want ** 2))
+    # and the coefficient form against the background's own stencil (two half-sweep launches):
+    # they differ by the BF16 rounding of the coefficients only
+    ref = gpu_lib.pm_mg_sweep_f32(cu(u, torch.float32), *args, mode=0, bg=bg, gap=gap).cpu().numpy()
+    assert np.sqrt(np.mean((got - ref) ** 2)) <= 1e-2 * np.sqrt(np.mean((ref - u) ** 2))
+
+
 @pytest.mark.parametrize("inner", [1, 2, 3])
 def test_mixed_precision_solve_256_uses_fused_sweep(gpu_lib, inner):
     """At 256^3 the inner cycle runs the fused sweep on its finest level; the mixed solve
