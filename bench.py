@@ -125,24 +125,52 @@ def job_value(ms_step, solves, ws):
     return ms_step / (solves * ws)
 
 
-def cpu_baseline(n_sample=128, combo=(-0.5, 0.0), target_n=512):
-    """The CPU oracle as it stands, on a bounded sample: one cold-start solve of the same
-    recipe at n_sample^3 to 1e-8, extrapolated to target_n^3 by the cell count (multigrid
-    work is linear in the cells at a fixed cycle count)."""
+def _nproc():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(n_sample=128, target_n=512, cycles_target=None, sample_cycles=6):
+    """The CPU oracle as it stands (one thread), on a bounded sample of the same workload:
+    for each of the four parameter pairs, sample_cycles FAS V-cycles of the oracle from a cold
+    start on the n_sample^3 field of the same recipe, giving its time per cycle; extrapolated
+    to target_n^3 by the cell count (a V-cycle's work is linear in the cells) and by the number
+    of cycles each pair needs at target_n^3.  Those counts are the plain FP64 GPU multigrid's
+    (cycles_target, same algorithm, hence the same counts); without them the oracle's own
+    counts at n_sample^3 are used, which understates the nu < 0 pairs (their counts grow with n)."""
     import oracle as O
     from paper_2604_15434_gb300 import synth
 
     d = synth.lognormal_delta(n_sample, -2.0, 1.5, SEED)
     O.build()
-    t0 = time.perf_counter()
-    chi, info, st = O.scalar_solve(d, combo[0], combo[1], 1.0, TOL)
-    dt = time.perf_counter() - t0
     scale = (target_n / n_sample) ** 3
-    return {"value": dt * 1e3 * scale, "unit": "ms", "cores": 1, "kind": "oracle",
-            "sample": f"one FP64 oracle solve of the {n_sample}^3 lognormal (same recipe, seed {SEED}), "
-                      f"alpha=({combo[0]},{combo[1]}), cold start to {TOL:g}: {dt:.2f} s, {info['cycles']} cycles, "
-                      f"x{scale:.0f} (cells) to {target_n}^3",
-            "sample_seconds": dt}
+    per_pair, total_s = {}, 0.0
+    for aB, aM in COMBOS:
+        key = f"{aB},{aM}"
+        if cycles_target and key in cycles_target:
+            t0 = time.perf_counter()
+            O.scalar_solve(d, aB, aM, 1.0, 0.0, max_cycles=sample_cycles)
+            dt = time.perf_counter() - t0
+            per_cycle = dt / sample_cycles
+            cyc = cycles_target[key]
+            src = "cycles of the FP64 GPU multigrid at the target size"
+        else:
+            t0 = time.perf_counter()
+            _, info, _ = O.scalar_solve(d, aB, aM, 1.0, TOL)
+            dt = time.perf_counter() - t0
+            per_cycle = dt / max(info["cycles"], 1)
+            cyc = info["cycles"]
+            src = f"the oracle's own cycles at {n_sample}^3 (a lower bound for nu < 0)"
+        total_s += dt
+        per_pair[key] = {"ms": per_cycle * cyc * scale * 1e3, "cycles": cyc, "s_per_cycle_sample": per_cycle}
+    value = sum(v["ms"] for v in per_pair.values()) / len(per_pair)
+    return {"value": value, "unit": "ms", "cores": 1, "host_nproc": _nproc(), "kind": "oracle",
+            "sample": f"FP64 oracle (one thread, -O2) on the {n_sample}^3 lognormal of the same recipe (seed {SEED}), "
+                      f"four parameter pairs, time per V-cycle x{scale:.0f} (cells) x cycles per pair at "
+                      f"{target_n}^3 ({src}); {total_s:.1f} s of CPU work",
+            "per_pair": per_pair, "sample_seconds": total_s}
 
 
 def batched_leg(api, dev, stream, nbox=24, seed=1007):
@@ -307,25 +335,56 @@ def next_rows_leg(api, dev, stream):
     return out
 
 
+def precision_leg(api, delta, stream, dev):
+    """The precision options of the solve on the 512^3 workload, each pair from a cold start to
+    the same tolerance: the default float-float outer loop (precision 1), the FP64 outer loop
+    (precision 2: FP64 residual and iterate around the FP32 inner cycle), and both with the exact
+    FP64 coarsest solve (Newton with a dense Jacobian and LU on 4^3)."""
+    import torch
+
+    out = {}
+    phi = torch.zeros_like(delta)
+    for name, kw in (("float_float_outer", dict(precision=1)), ("fp64_outer", dict(precision=2)),
+                     ("float_float_outer_exact_coarsest", dict(precision=1, coarse_exact=1)),
+                     ("fp64_outer_exact_coarsest", dict(precision=2, coarse_exact=1))):
+        c = api.Context(dev.index, stream, max_cycles=100, **kw)
+        phi.zero_()
+        api.scalar_mg_solve(delta, *COMBOS[2], 1.0, TOL, phi=phi, ctx=c, raise_on_noconv=False)  # warm-up
+        rows = {}
+        for aB, aM in COMBOS:
+            phi.zero_()
+            torch.cuda.synchronize()
+            _, info = api.scalar_mg_solve(delta, aB, aM, 1.0, TOL, phi=phi, ctx=c, raise_on_noconv=False)
+            rows[f"{aB},{aM}"] = {"ms": info["ms_total"], "cycles": info["cycles"], "vcycles": info["vcycles"],
+                                  "rel_res": info["rel_res"], "status": info["status"]}
+        out[name] = {"per_pair": rows, "mean_ms": sum(r["ms"] for r in rows.values()) / len(rows)}
+        c.close()
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return
     # each step: one bounded oracle sample; the line reports the mean extrapolated value
+    # each step: the four pairs solved to tolerance by the oracle at the sample size (64^3 unless
+    # --sample-n says otherwise), extrapolated by the cell count
+    sn = args.sample_n if args.sample_n else 64
     vals = []
     for _ in range(args.warmup):
-        cpu_baseline(args.sample_n)
+        cpu_baseline(sn, args.n)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(cpu_baseline(args.sample_n))
+        vals.append(cpu_baseline(sn, args.n))
     wall = time.perf_counter() - t0
     v = sum(x["value"] for x in vals) / len(vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": wall * 1e3 / max(args.steps, 1), "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.n}^3 lognormal scalar solve, extrapolated from {args.sample_n}^3 samples",
+            "config": {"workload": f"{args.n}^3 lognormal scalar solve, extrapolated from {sn}^3 samples",
                        "n": args.n, "tol": TOL},
-            "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": vals[0]["sample"]},
+            "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "host_nproc": _nproc(), "kind": "oracle",
+                             "sample": vals[0]["sample"], "per_pair": vals[0]["per_pair"]},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -337,13 +396,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=512)
-    ap.add_argument("--sample-n", type=int, default=128)
+    ap.add_argument("--sample-n", type=int, default=0, help="CPU-oracle sample size (default 128; 64 for the "
+                                                           "reference arm)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the 24-box batched-solve leg")
     ap.add_argument("--no-warm", action="store_true", help="skip the cold / linear / learned warm-start leg")
     ap.add_argument("--no-next", action="store_true", help="skip the PM-step / run / linearised / lensing / "
                                                             "Method II leg")
+    ap.add_argument("--no-precision", action="store_true", help="skip the FP64-outer / exact-coarsest leg")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -425,21 +486,26 @@ def main():
             torch.cuda.synchronize()
             fp64[f"{aB},{aM}"] = {"ms": e0.elapsed_time(e1), "cycles": info["cycles"], "rel_res": info["rel_res"]}
 
-    # end to end through the C ABI with host buffers: H2D delta, solve, D2H chi (headline pair)
+    # end to end through the C ABI with host buffers: H2D delta, solve, D2H chi (headline pair),
+    # with events between the three parts
     host_in = torch.from_numpy(delta_h).pin_memory()
     host_out = torch.empty((n, n, n), dtype=torch.float64).pin_memory()
     dev_in = torch.empty_like(delta)
-    e2e_ms = []
+    e2e_ms, e2e_parts = [], []
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(max(1, args.steps)):
         phis[0].zero_()
         torch.cuda.synchronize()
         e0.record(stream)
         dev_in.copy_(host_in, non_blocking=True)
+        ea.record(stream)
         api.scalar_mg_solve(dev_in, COMBOS[0][0], COMBOS[0][1], 1.0, TOL, phi=phis[0], ctx=ctx)
+        eb.record(stream)
         host_out.copy_(phis[0], non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
+        e2e_parts.append((e0.elapsed_time(ea), ea.elapsed_time(eb), eb.elapsed_time(e1)))
 
     # roofline of the dominant kernel class, finest-level launches
     hbm, src = _peaks()
@@ -483,7 +549,12 @@ def main():
                    "l2": f"inputs larger than L2 ({n ** 3 * 8 / 2 ** 30:g} GiB per field)" if n ** 3 * 8 > 129e6
                          else "inputs smaller than L2 (no flush: small-case profiling run)"},
         "e2e": {"value": sum(e2e_ms) / len(e2e_ms), "unit": "ms", "h2d_bytes_per_step": cells * 8,
-                "d2h_bytes_per_step": cells * 8, "per": "one solve (alpha_B0=-2, alpha_M0=0) incl. H2D delta, D2H chi"},
+                "d2h_bytes_per_step": cells * 8, "per": "one solve (alpha_B0=-2, alpha_M0=0) incl. H2D delta, D2H chi",
+                "h2d_ms": sum(p[0] for p in e2e_parts) / len(e2e_parts),
+                "solve_ms": sum(p[1] for p in e2e_parts) / len(e2e_parts),
+                "d2h_ms": sum(p[2] for p in e2e_parts) / len(e2e_parts),
+                "h2d_gbs": cells * 8 / (sum(p[0] for p in e2e_parts) / len(e2e_parts) * 1e-3) / 1e9,
+                "d2h_gbs": cells * 8 / (sum(p[2] for p in e2e_parts) / len(e2e_parts) * 1e-3) / 1e9},
         "roofline": roof,
         "gpu_launches": launches,
         "clocks": clk.summary(),
@@ -491,7 +562,12 @@ def main():
         "fp64_ms_per_solve": (sum(v["ms"] for v in fp64.values()) / len(fp64)) if fp64 else None,
         "speedup_vs_fp64": ((sum(v["ms"] for v in fp64.values()) / len(fp64)) / value) if fp64 else None,
         "solves": {f"{k[0]},{k[1]}": {"cycles": v["cycles"], "rel_res": v["rel_res"], "floored": v["floored_cells"],
-                                       "ms": v["ms_total"]} for k, v in infos.items()},
+                                       "floored_frac": v["floored_cells"] / cells, "ms": v["ms_total"]}
+                   for k, v in infos.items()},
+        "eta": ctx.params.eta,
+        "eta_reading": "discriminant floor sqrt(D_floor) = eta 6|nu|/h^2 with the linear residual piece in floored "
+                       "cells (reading of 'a very low value close to zero'); floored_frac per pair is the share of "
+                       "cells on that floor in the converged field",
         # fine-equivalent smoother throughput: every level's cells x sweeps of the inner V-cycles
         # (one per outer iteration), per second of solve time; and n^3 per time to tolerance
         "cell_updates_per_s": sum(v["vcycles"] * 4 * sum((n >> l) ** 3 for l in range(int(math.log2(n)) - 1))
@@ -512,12 +588,15 @@ def main():
             line["learned_mixed_ms_per_solve"] = ws_leg["mean_total_ms"]["learned"]
             if fp64:
                 line["speedup_learned_vs_fp64"] = line["fp64_ms_per_solve"] / ws_leg["mean_total_ms"]["learned"]
+    if not args.no_precision:
+        line["precision_variants"] = precision_leg(api, delta, stream, dev)
     if not args.no_batch:
         line["batched"] = batched_leg(api, dev, stream)
     if not args.no_next:
         line["next_rows"] = next_rows_leg(api, dev, stream)
     if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(args.sample_n)
+        cyc = {k: v["cycles"] for k, v in fp64.items()} if fp64 else None
+        line["cpu_baseline"] = cpu_baseline(args.sample_n or 128, n, cyc)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

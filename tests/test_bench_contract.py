@@ -26,6 +26,7 @@ def test_reference_arm_prints_one_contract_line():
     assert line["n_gpus"] == 1 and line["steps"] == 1
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and "32^3" in cb["sample"]
+    assert cb["host_nproc"] >= 1 and set(cb["per_pair"]) == {"-2.0,0.0", "-2.0,0.5", "-0.5,0.0", "-0.5,0.5"}
     assert line["e2e"] == {"value": line["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert "workload" in line["config"]
 
