@@ -362,6 +362,29 @@ def precision_leg(api, delta, stream, dev):
     return out
 
 
+def void_floor_leg(api, delta, stream, dev, phis):
+    """The literal void floor (eta = 0: only cells with a negative discriminant are floored, at
+    the parabola's vertex; Sec. 3.3) against the default eta on the nu > 0 pairs of the 512^3
+    workload: cycles, time, floored fraction and the relative change of chi (phis holds the
+    timed steps' solutions at the default eta)."""
+    import torch
+
+    cells = delta.numel()
+    c = api.Context(dev.index, stream, precision=1, max_cycles=100, eta=0.0)
+    out = {}
+    phi = torch.zeros_like(delta)
+    for i, (aB, aM) in enumerate(COMBOS):
+        if api.coefficients(aB, aM, 1.0)["nu"] <= 0.0:
+            continue
+        phi.zero_()
+        _, info = api.scalar_mg_solve(delta, aB, aM, 1.0, TOL, phi=phi, ctx=c, raise_on_noconv=False)
+        out[f"{aB},{aM}"] = {"ms": info["ms_total"], "cycles": info["cycles"], "rel_res": info["rel_res"],
+                             "status": info["status"], "floored_frac": info["floored_cells"] / cells,
+                             "rel_change_chi_vs_default_eta": float((phi - phis[i]).norm() / phis[i].norm())}
+    c.close()
+    return {"eta": 0.0, "per_pair": out}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -589,6 +612,7 @@ def main():
             if fp64:
                 line["speedup_learned_vs_fp64"] = line["fp64_ms_per_solve"] / ws_leg["mean_total_ms"]["learned"]
     if not args.no_precision:
+        line["void_floor_literal"] = void_floor_leg(api, delta, stream, dev, phis)
         line["precision_variants"] = precision_leg(api, delta, stream, dev)
     if not args.no_batch:
         line["batched"] = batched_leg(api, dev, stream)

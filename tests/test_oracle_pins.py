@@ -460,7 +460,7 @@ def test_solution_commutes_with_axis_permutation():
     assert np.linalg.norm(np.transpose(chi, (2, 0, 1)) - chi2) / np.linalg.norm(chi) < 1e-11
 
 
-@pytest.mark.parametrize("aB0,aM0", [(-0.5, 0.0), (-2.0, 0.0)])
+@pytest.mark.parametrize("aB0,aM0", [(-0.5, 0.0), (-2.0, 0.0), (-2.0, 0.5)])
 def test_floored_solution_is_unique(aB0, aM0):
     """Reading R-sat (Sec. 3.3): with the floored discriminant the discrete problem has one
     solution.  Two different starting points (zero and the linear FFT solution) and two
@@ -472,6 +472,50 @@ def test_floored_solution_is_unique(aB0, aM0):
     b, ib, sb = O.mg_solve(f, c["nu"], c["kappa"], 1e-13, chi0=_fft_linear_solve(f, c["nu"]), npre=3, npost=1)
     assert sa == 0 and sb == 0 and ia["sat_cells"] > 0
     assert np.linalg.norm(a - b) / np.linalg.norm(a) < 1e-10
+
+
+def test_void_floor_sensitivity_on_the_benchmark_pairs():
+    """Reading R-sat (Sec. 3.3: the discriminant of void cells without a real root is set to
+    'a very low value close to zero'): how much the floor value eta decides the solution, on a
+    32^3 field of the benchmark recipe (lognormal, P ~ k^-2, sigma_ln 1.5).  eta = 0 is the
+    literal reading: only cells with D < 0 are floored, and they sit at the parabola's vertex
+    L = 3 nu / (4 kappa).  The nu > 0 pairs are barely touched: (-0.5, 0.5) has no floored cell,
+    so every eta gives the same chi, and (-0.5, 0) moves by at most 4% in chi and 1.5% in the
+    force from eta = 0.35 down to the literal floor.  For the nu < 0 pair (-2, 0) the floor
+    covers more than half of the box and eta decides the solution at the 10-30% level."""
+    n = 32
+    d = synth.lognormal_delta(n, -2.0, 1.5, 1003)
+    res = {}
+    for aB0, aM0 in ((-0.5, 0.5), (-0.5, 0.0), (-2.0, 0.0)):
+        c = O.coefficients(aB0, aM0, 1.0)
+        f = O.source(d, c)
+        psi = O.poisson_fft(d, c, 1.0)
+        ref, iref, st = O.mg_solve(f, c["nu"], c["kappa"], 1e-11)
+        assert st == 0
+        gref = O.accel_grid(psi, ref, c["xi"], n)
+        rows = [(O.ETA_DEFAULT, iref["sat_cells"] / n ** 3, 0.0, 0.0)]
+        for eta in (0.25, 0.05, 0.0):
+            x, info, st = O.mg_solve(f, c["nu"], c["kappa"], 1e-11, eta=eta, max_cycles=400)
+            assert st == 0
+            g = O.accel_grid(psi, x, c["xi"], n)
+            rows.append((eta, info["sat_cells"] / n ** 3, np.linalg.norm(x - ref) / np.linalg.norm(ref),
+                         np.linalg.norm(g - gref) / np.linalg.norm(gref)))
+            if eta == 0.0:
+                # the literal floor: floored cells exactly at the vertex, the rest with D >= 0 and
+                # a zero residual
+                r, sat = O.residual(x, f, info["lambda"], c["nu"], c["kappa"], 0.0)
+                w = sat == 0
+                r = r - w * (r.sum() / max(w.sum(), 1))
+                assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(f - f.mean())
+        res[(aB0, aM0)] = rows
+    assert all(r[1] == 0.0 and r[2] < 1e-9 for r in res[(-0.5, 0.5)])
+    rows = res[(-0.5, 0.0)]
+    assert all(rows[k + 1][1] < rows[k][1] for k in range(3))  # a lower floor floors fewer cells
+    assert all(rows[k + 1][2] > rows[k][2] for k in range(3))  # and moves chi further from eta = 0.35
+    assert rows[-1][2] < 0.045 and rows[-1][3] < 0.016
+    rows = res[(-2.0, 0.0)]
+    assert all(r[1] > 0.5 for r in rows)
+    assert rows[1][2] > 0.05 and rows[-1][2] > 0.2
 
 
 # ---------------------------------------------------------------- spherical closed form
