@@ -7,10 +7,13 @@
 // confirmed by one FP64 residual, as in the single-box solve.  One outer iteration of
 // every unconverged box is captured into a single CUDA graph with one branch per box, so
 // the small boxes' kernels run side by side and the host issues one launch per iteration.
-// The host reads all boxes' residual norms after each launch (one synchronisation) and
-// rebuilds the graph only when a box converges.  The first iteration runs eagerly so the
-// autotuner has chosen every tile before capture.
+// The host reads all boxes' residual norms after each launch (one synchronisation); a box
+// that has converged has its nodes disabled in the executable graph, so the graph is captured
+// and instantiated once per call.  The first iteration runs eagerly so the autotuner has
+// chosen every tile before capture.
 #pragma once
+
+#include <set>
 
 namespace pmeft {
 
@@ -218,61 +221,95 @@ pm_status mg_solve_batched(pm_ctx* ctx, int nbox, const int* nn, const double* c
             B[b].vcyc += P.inner_cycles;
             box_check(P, B[b], tol);
         }
-    // graph-captured iterations
+    // graph-captured iterations.  The boxes still active after the eager iteration are captured
+    // once, each box's kernel, memset and memcpy nodes recorded; a box that converges later has
+    // its nodes disabled in the executable graph (cudaGraphNodeSetEnabled) instead of a new
+    // capture and instantiation of the remaining boxes.
     cudaGraphExec_t exec = nullptr;
-    std::vector<int> members;
-    pm_profile per_launch{};
-    for (;;) {
+    std::vector<std::vector<cudaGraphNode_t>> box_nodes(nbox);
+    std::vector<pm_profile> box_prof(nbox);
+    std::vector<char> enabled(nbox, 0);
+    {
         std::vector<int> act;
         for (int b = 0; b < nbox; ++b)
             if (B[b].active) act.push_back(b);
-        if (act.empty()) break;
-        if (!exec || act != members) {
-            if (exec) cudaGraphExecDestroy(exec);
-            exec = nullptr;
-            members = act;
+        if (!act.empty()) {
             const pm_profile before = ctx->prof;
             cudaStream_t ms = ctx->batch_stream;
-            cudaEvent_t fork, join;
+            cudaEvent_t fork;
             cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
             PM_CUDA(cudaStreamBeginCapture(ms, cudaStreamCaptureModeThreadLocal));
             cudaEventRecord(fork, ms);
+            cudaGraph_t cg = nullptr;
+            cudaStreamCaptureStatus cs;
+            PM_CUDA(cudaStreamGetCaptureInfo(ms, &cs, nullptr, &cg, nullptr, nullptr, nullptr));
+            std::set<cudaGraphNode_t> seen;
+            auto new_nodes = [&](std::vector<cudaGraphNode_t>& out) {
+                size_t nn = 0;
+                cudaGraphGetNodes(cg, nullptr, &nn);
+                std::vector<cudaGraphNode_t> all(nn);
+                cudaGraphGetNodes(cg, all.data(), &nn);
+                for (auto nd : all) {
+                    if (!seen.insert(nd).second) continue;
+                    cudaGraphNodeType ty;
+                    cudaGraphNodeGetType(nd, &ty);
+                    if (ty == cudaGraphNodeTypeKernel || ty == cudaGraphNodeTypeMemset || ty == cudaGraphNodeTypeMemcpy)
+                        out.push_back(nd);
+                }
+            };
+            std::vector<cudaGraphNode_t> dummy;
+            new_nodes(dummy);  // the fork
             std::vector<cudaEvent_t> joins;
             for (int b : act) {
                 Workspace* w = B[b].w;
+                const pm_profile pb = ctx->prof;
                 cudaStreamWaitEvent(w->stream, fork, 0);
                 Exec x(ctx, w->stream, w->partials, w->out, w->host, false);
                 box_iteration(&x, B[b]);
+                cudaEvent_t join;
                 cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
                 cudaEventRecord(join, w->stream);
                 cudaStreamWaitEvent(ms, join, 0);
                 joins.push_back(join);
+                new_nodes(box_nodes[b]);
+                for (int k = 0; k < PM_K_COUNT; ++k) {
+                    box_prof[b].launches[k] = ctx->prof.launches[k] - pb.launches[k];
+                    box_prof[b].fine_launches[k] = ctx->prof.fine_launches[k] - pb.fine_launches[k];
+                    box_prof[b].cells[k] = ctx->prof.cells[k] - pb.cells[k];
+                }
+                enabled[b] = 1;
             }
             cudaGraph_t g = nullptr;
             cudaError_t ce = cudaStreamEndCapture(ms, &g);
             for (auto e : joins) cudaEventDestroy(e);
             cudaEventDestroy(fork);
+            ctx->prof = before;  // capture launched nothing; replays are counted below
             if (ce != cudaSuccess) {
                 ctx->set_error(std::string("graph capture failed: ") + cudaGetErrorString(ce));
                 return PM_ERR_CUDA;
             }
             PM_CUDA(cudaGraphInstantiate(&exec, g, 0));
             cudaGraphDestroy(g);
-            for (int k = 0; k < PM_K_COUNT; ++k) {
-                per_launch.launches[k] = ctx->prof.launches[k] - before.launches[k];
-                per_launch.fine_launches[k] = ctx->prof.fine_launches[k] - before.fine_launches[k];
-                per_launch.cells[k] = ctx->prof.cells[k] - before.cells[k];
-            }
-            ctx->prof = before;  // capture launched nothing; replays are counted below
         }
+    }
+    for (;;) {
+        std::vector<int> act;
+        for (int b = 0; b < nbox; ++b)
+            if (B[b].active) act.push_back(b);
+        if (act.empty() || !exec) break;
+        for (int b = 0; b < nbox; ++b)
+            if (enabled[b] && !B[b].active) {
+                for (auto nd : box_nodes[b]) PM_CUDA(cudaGraphNodeSetEnabled(exec, nd, 0));
+                enabled[b] = 0;
+            }
         PM_CUDA(cudaGraphLaunch(exec, ctx->batch_stream));
         PM_CUDA(cudaStreamSynchronize(ctx->batch_stream));
-        for (int k = 0; k < PM_K_COUNT; ++k) {
-            ctx->prof.launches[k] += per_launch.launches[k];
-            ctx->prof.fine_launches[k] += per_launch.fine_launches[k];
-            ctx->prof.cells[k] += per_launch.cells[k];
-        }
         for (int b : act) {
+            for (int k = 0; k < PM_K_COUNT; ++k) {
+                ctx->prof.launches[k] += box_prof[b].launches[k];
+                ctx->prof.fine_launches[k] += box_prof[b].fine_launches[k];
+                ctx->prof.cells[k] += box_prof[b].cells[k];
+            }
             ++B[b].cyc;
             B[b].vcyc += P.inner_cycles;
             box_check(P, B[b], tol);
