@@ -225,7 +225,19 @@ pm_status mg_solve_batched(pm_ctx* ctx, int nbox, const int* nn, const double* c
     // once, each box's kernel, memset and memcpy nodes recorded; a box that converges later has
     // its nodes disabled in the executable graph (cudaGraphNodeSetEnabled) instead of a new
     // capture and instantiation of the remaining boxes.
-    cudaGraphExec_t exec = nullptr;
+    // the executable graph and the captured graph (kept until the end: its nodes name the
+    // executable graph's nodes), released on every return path
+    struct GraphHold {
+        cudaGraphExec_t exec = nullptr;
+        cudaGraph_t graph = nullptr;
+        ~GraphHold()
+        {
+            if (exec) cudaGraphExecDestroy(exec);
+            if (graph) cudaGraphDestroy(graph);
+        }
+    } hold;
+    cudaGraphExec_t& exec = hold.exec;
+    cudaGraph_t& graph = hold.graph;
     std::vector<std::vector<cudaGraphNode_t>> box_nodes(nbox);
     std::vector<pm_profile> box_prof(nbox);
     std::vector<char> enabled(nbox, 0);
@@ -288,8 +300,8 @@ pm_status mg_solve_batched(pm_ctx* ctx, int nbox, const int* nn, const double* c
                 ctx->set_error(std::string("graph capture failed: ") + cudaGetErrorString(ce));
                 return PM_ERR_CUDA;
             }
+            graph = g;
             PM_CUDA(cudaGraphInstantiate(&exec, g, 0));
-            cudaGraphDestroy(g);
         }
     }
     for (;;) {
@@ -315,7 +327,6 @@ pm_status mg_solve_batched(pm_ctx* ctx, int nbox, const int* nn, const double* c
             box_check(P, B[b], tol);
         }
     }
-    if (exec) cudaGraphExecDestroy(exec);
     // FP64 result of every box; a converged box's stop test is confirmed by its FP64
     // residual (a box that misses it by rounding gets further outer iterations, eagerly)
     for (int b = 0; b < nbox; ++b) {

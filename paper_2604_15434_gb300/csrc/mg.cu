@@ -59,10 +59,39 @@ __device__ __forceinline__ T opsplit_update(const Stencil<T>& s, T ih2, T nu, T 
     return s.c0 + (Lnow - Lroot) / (T(6) * ih2);
 }
 
-// One colour half-sweep over the n^3/2 cells of `colour` ((i+j+k) & 1 == colour).
-// own: array holding this colour's current values; oth: the other colour's; out:
-// receives the new values of this colour.  rhs = fscale * F + lam.  OPS: the local solve
-// of Method II (opsplit_update; etanu = eta |nu|) instead of Method I's.
+// One cell of a colour half-sweep: element t of the n^3/2 cells of `colour`
+// ((i+j+k) & 1 == colour), lg = log2 n.  own: array holding this colour's current values;
+// oth: the other colour's; out: receives the new values of this colour.  rhs = fscale * F +
+// lam.  OPS: the local solve of Method II (opsplit_update; etanu = eta |nu|) instead of
+// Method I's.
+template <typename T, bool BG, bool OPS>
+__device__ __forceinline__ void half_sweep_cell(const T* __restrict__ own, const T* __restrict__ oth,
+                                                T* __restrict__ out, const T* __restrict__ F, T fscale, T lam,
+                                                const uint8_t* __restrict__ kmask, const T* __restrict__ bg,
+                                                const T* __restrict__ gap, int n, int lg, int colour, T ih2, T nu,
+                                                T kap, T sp, T Df, T lsat_c, T etanu, size_t t)
+{
+    const int hn = n >> 1;
+    const int m = (int)(t & (size_t)(hn - 1));  // n (hence hn) is a power of two
+    const size_t row = t >> (lg - 1);
+    const int j = (int)(row & (size_t)(n - 1)), k = (int)(row >> lg);
+    const int i = 2 * m + ((j + k + colour) & 1);
+    const size_t c = row * n + i;
+    Stencil<T> s = load_stencil(own, oth, i, j, k, n);
+    Stencil<T> b;
+    if (BG) b = load_stencil(bg, bg, i, j, k, n);
+    const T w = screen_w<T>(kmask, c);
+    const T kc = kap * w;
+    if (OPS) {
+        out[c] = opsplit_update<T>(s, ih2, nu, kc, fscale * F[c] + lam, etanu);
+        return;
+    }
+    const T lsat = kc != T(0) ? lsat_c / w : T(0);
+    Local<T> o = local_eval<T, BG>(s, b, ih2, nu, kc, fscale * F[c] + lam, lsat, gap != nullptr, gap ? gap[c] : T(0));
+    out[c] = s.c0 + local_update(o, sp, Df, ih2);
+}
+
+// One colour half-sweep over the n^3/2 cells of `colour` (half_sweep_cell).
 template <typename T, bool BG, bool OPS = false>
 __global__ void __launch_bounds__(256) k_half_sweep(const T* __restrict__ own, const T* __restrict__ oth,
                                                     T* __restrict__ out, const T* __restrict__ F, T fscale, T lam,
@@ -71,36 +100,69 @@ __global__ void __launch_bounds__(256) k_half_sweep(const T* __restrict__ own, c
                                                     T sp, T Df, T lsat_c, const T* __restrict__ lamp, T etanu)
 {
     if (lamp) lam += *lamp;
-    const int hn = n >> 1;
-    const size_t total = (size_t)n * n * hn;
+    const size_t total = (size_t)n * n * (n >> 1);
     const int lg = __ffs(n) - 1;
-    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-        const int m = (int)(t & (size_t)(hn - 1));  // n (hence hn) is a power of two
-        const size_t row = t >> (lg - 1);
-        const int j = (int)(row & (size_t)(n - 1)), k = (int)(row >> lg);
-        const int i = 2 * m + ((j + k + colour) & 1);
-        const size_t c = row * n + i;
-        Stencil<T> s = load_stencil(own, oth, i, j, k, n);
-        Stencil<T> b;
-        if (BG) b = load_stencil(bg, bg, i, j, k, n);
-        const T w = screen_w<T>(kmask, c);
-        const T kc = kap * w;
-        if (OPS) {
-            out[c] = opsplit_update<T>(s, ih2, nu, kc, fscale * F[c] + lam, etanu);
-            continue;
-        }
-        const T lsat = kc != T(0) ? lsat_c / w : T(0);
-        Local<T> o = local_eval<T, BG>(s, b, ih2, nu, kc, fscale * F[c] + lam, lsat, gap != nullptr, gap ? gap[c] : T(0));
-        out[c] = s.c0 + local_update(o, sp, Df, ih2);
-    }
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x)
+        half_sweep_cell<T, BG, OPS>(own, oth, out, F, fscale, lam, kmask, bg, gap, n, lg, colour, ih2, nu, kap, sp, Df,
+                                    lsat_c, etanu, t);
 }
 
 // ------------------------------------------------------------------ residual
 
-// r = f + lam - N (real root) or nu (L_sat - L) (floored), its floored flag, and the
-// block sums used for the gauge update and the norm.  MIXED (FP64 level 0 of the
-// defect-correction loop) also writes the FP32 copies: the plain residual -G for the
-// inner right-hand side, and the iterate as the inner background.
+// One cell of the residual: r = f + lam - N (real root) or nu (L_sat - L) (floored), its
+// floored flag, and the cell's share of the sums fa: [0] sum r, [1] sum r over unfloored,
+// [2] sum r^2, [3] count unfloored, [4] count non-finite.  MIXED (FP64 level 0 of the
+// defect-correction loop) also writes the FP32 copies: the plain residual -G for the inner
+// right-hand side, the iterate as the inner background, and the floored gap.
+template <typename T, bool BG, bool WRITE_R, bool MIXED>
+__device__ __forceinline__ void residual_cell(const T* __restrict__ u, const T* __restrict__ F, T fscale, T lam,
+                                              const uint8_t* __restrict__ kmask, const T* __restrict__ bg,
+                                              const T* __restrict__ gap, int n, int lg, T ih2, T nu, T kap, T Df,
+                                              T lsat_c, bool floor_piece, T* __restrict__ r,
+                                              uint8_t* __restrict__ sat, float* __restrict__ rplain,
+                                              float* __restrict__ chi32, float* __restrict__ gap32, size_t c,
+                                              float (&fa)[5])
+{
+    const int i = (int)(c & (size_t)(n - 1));  // n is a power of two
+    const size_t row = c >> lg;
+    const int j = (int)(row & (size_t)(n - 1)), k = (int)(row >> lg);
+    Stencil<T> s = load_stencil(u, u, i, j, k, n);
+    Stencil<T> b;
+    if (BG) b = load_stencil(bg, bg, i, j, k, n);
+    const T w = screen_w<T>(kmask, c);
+    const T kc = kap * w;
+    const T lsat = kc != T(0) ? lsat_c / w : T(0);
+    Local<T> o = local_eval<T, BG>(s, b, ih2, nu, kc, fscale * F[c] + lam, lsat, gap != nullptr, gap ? gap[c] : T(0));
+    // the floored piece exists on the finest level only; coarse levels take their
+    // pieces from the restricted mask (linear where masked, quadratic elsewhere), so
+    // their right-hand side and their smoother solve the same equation (FAS consistency)
+    const bool fl = floor_piece && (o.P != T(0)) && (o.D < Df);
+    // floored piece nu (L_sat - L) = nu g
+    const T rv = fl ? nu * o.g : -o.G;
+    if (WRITE_R) r[c] = rv;
+    if (sat) sat[c] = fl ? 1 : 0;
+    if (MIXED) {
+        rplain[c] = (float)(-o.G);
+        chi32[c] = (float)s.c0;
+        gap32[c] = (float)o.g;
+    }
+    // per-thread partial sums in FP32 (a few hundred terms each); the block and grid
+    // reductions are FP64.  The sums only set the gauge shift and the stopping norm.
+    const float d = (float)rv;
+    if (!isfinite(d)) {
+        fa[4] += 1.f;
+    } else {
+        fa[0] += d;
+        fa[2] += d * d;
+        if (!fl) {
+            fa[1] += d;
+            fa[3] += 1.f;
+        }
+    }
+}
+
+// The residual of a level (residual_cell) and its block sums for the gauge update and the
+// norm.
 template <typename T, bool BG, bool WRITE_R, bool MIXED>
 __global__ void __launch_bounds__(256) k_residual(const T* __restrict__ u, const T* __restrict__ F, T fscale, T lam,
                                                   const uint8_t* __restrict__ kmask, const T* __restrict__ bg,
@@ -115,44 +177,9 @@ __global__ void __launch_bounds__(256) k_residual(const T* __restrict__ u, const
     float fa[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     const size_t total = (size_t)n * n * n;
     const int lg = __ffs(n) - 1;
-    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(c & (size_t)(n - 1));  // n is a power of two
-        const size_t row = c >> lg;
-        const int j = (int)(row & (size_t)(n - 1)), k = (int)(row >> lg);
-        Stencil<T> s = load_stencil(u, u, i, j, k, n);
-        Stencil<T> b;
-        if (BG) b = load_stencil(bg, bg, i, j, k, n);
-        const T w = screen_w<T>(kmask, c);
-        const T kc = kap * w;
-        const T lsat = kc != T(0) ? lsat_c / w : T(0);
-        Local<T> o = local_eval<T, BG>(s, b, ih2, nu, kc, fscale * F[c] + lam, lsat, gap != nullptr, gap ? gap[c] : T(0));
-        // the floored piece exists on the finest level only; coarse levels take their
-        // pieces from the restricted mask (linear where masked, quadratic elsewhere), so
-        // their right-hand side and their smoother solve the same equation (FAS consistency)
-        const bool fl = floor_piece && (o.P != T(0)) && (o.D < Df);
-        // floored piece nu (L_sat - L) = nu g
-        const T rv = fl ? nu * o.g : -o.G;
-        if (WRITE_R) r[c] = rv;
-        if (sat) sat[c] = fl ? 1 : 0;
-        if (MIXED) {
-            rplain[c] = (float)(-o.G);
-            chi32[c] = (float)s.c0;
-            gap32[c] = (float)o.g;
-        }
-        // per-thread partial sums in FP32 (a few hundred terms each); the block and grid
-        // reductions are FP64.  The sums only set the gauge shift and the stopping norm.
-        const float d = (float)rv;
-        if (!isfinite(d)) {
-            fa[4] += 1.f;
-        } else {
-            fa[0] += d;
-            fa[2] += d * d;
-            if (!fl) {
-                fa[1] += d;
-                fa[3] += 1.f;
-            }
-        }
-    }
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x)
+        residual_cell<T, BG, WRITE_R, MIXED>(u, F, fscale, lam, kmask, bg, gap, n, lg, ih2, nu, kap, Df, lsat_c,
+                                             floor_piece, r, sat, rplain, chi32, gap32, c, fa);
     double acc[5];
 #pragma unroll
     for (int q = 0; q < 5; ++q) acc[q] = (double)fa[q];
@@ -161,9 +188,38 @@ __global__ void __launch_bounds__(256) k_residual(const T* __restrict__ u, const
 
 // ------------------------------------------------------------------ transfers
 
-// Coarse cell = average of its 8 children, for the iterate (-> ur and the coarse start
+// Coarse cell c = average of its 8 children, for the iterate (-> ur and the coarse start
 // value) and the gauge-projected residual r - gm * [unfloored]; the coarse screening mask
 // holds the children's mean unscreened fraction in eighths (floored children count 8).
+template <typename T>
+__device__ __forceinline__ void restrict_fas_cell(const T* __restrict__ uf, const T* __restrict__ rf,
+                                                  const uint8_t* __restrict__ satf, const uint8_t* __restrict__ kmf,
+                                                  T gm, int nc, int lgc, T* __restrict__ ur, T* __restrict__ uc,
+                                                  T* __restrict__ rc, uint8_t* __restrict__ kmc, size_t c)
+{
+    const int nf = 2 * nc;
+    const int I = (int)(c & (size_t)(nc - 1));  // nc is a power of two
+    const size_t row = c >> lgc;
+    const int J = (int)(row & (size_t)(nc - 1)), K = (int)(row >> lgc);
+    T su = T(0), sr = T(0);
+    int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int di = q & 1, dj = (q >> 1) & 1, dk = (q >> 2) & 1;
+        const size_t f = ((size_t)(2 * K + dk) * nf + (2 * J + dj)) * nf + (2 * I + di);
+        su += uf[f];
+        const bool fl = satf[f] != 0;
+        sr += fl ? rf[f] : rf[f] - gm;
+        const int kf = kmf ? (kmf[f] < 8 ? kmf[f] : 8) : 0;
+        cnt += fl ? 8 : kf;  // unscreened eighths of the child
+    }
+    su *= T(0.125);
+    ur[c] = su;
+    uc[c] = su;
+    rc[c] = sr * T(0.125);
+    kmc[c] = (uint8_t)((cnt + 4) >> 3);  // mean of the children, rounded to eighths
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_restrict_fas(const T* __restrict__ uf, const T* __restrict__ rf,
                                                       const uint8_t* __restrict__ satf,
@@ -171,32 +227,11 @@ __global__ void __launch_bounds__(256) k_restrict_fas(const T* __restrict__ uf, 
                                                       int nc, T* __restrict__ ur, T* __restrict__ uc,
                                                       T* __restrict__ rc, uint8_t* __restrict__ kmc)
 {
-    const int nf = 2 * nc;
     const size_t total = (size_t)nc * nc * nc;
     const T gm = gm_ptr ? (T)(*gm_ptr) : T(0);
     const int lgc = __ffs(nc) - 1;
-    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x) {
-        const int I = (int)(c & (size_t)(nc - 1));  // nc is a power of two
-        const size_t row = c >> lgc;
-        const int J = (int)(row & (size_t)(nc - 1)), K = (int)(row >> lgc);
-        T su = T(0), sr = T(0);
-        int cnt = 0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int di = q & 1, dj = (q >> 1) & 1, dk = (q >> 2) & 1;
-            const size_t f = ((size_t)(2 * K + dk) * nf + (2 * J + dj)) * nf + (2 * I + di);
-            su += uf[f];
-            const bool fl = satf[f] != 0;
-            sr += fl ? rf[f] : rf[f] - gm;
-            const int kf = kmf ? (kmf[f] < 8 ? kmf[f] : 8) : 0;
-            cnt += fl ? 8 : kf;  // unscreened eighths of the child
-        }
-        su *= T(0.125);
-        ur[c] = su;
-        uc[c] = su;
-        rc[c] = sr * T(0.125);
-        kmc[c] = (uint8_t)((cnt + 4) >> 3);  // mean of the children, rounded to eighths
-    }
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x)
+        restrict_fas_cell<T>(uf, rf, satf, kmf, gm, nc, lgc, ur, uc, rc, kmc, c);
 }
 
 // Plain 8-child average (background field of the correction form).
@@ -228,6 +263,39 @@ __global__ void k_restrict(const T* __restrict__ uf, int nc, T* __restrict__ uc)
 // children's raw mean residual and the mask byte carries the unfloored children in its high
 // nibble; the gauge term -gm * (unfloored children)/8 is applied here and the nibble cleared.
 template <typename T, bool BG>
+__device__ __forceinline__ void fas_rhs_cell(const T* __restrict__ uc, const T* __restrict__ rc,
+                                             uint8_t* __restrict__ kmask, const T* __restrict__ bg, int n, int lg,
+                                             T ih2, T nu, T kap, T* __restrict__ fc, uint32_t* __restrict__ coefo,
+                                             float* __restrict__ gapo, float lsat, bool apply_gm, T gm, size_t total,
+                                             size_t c)
+{
+    const int i = (int)(c & (size_t)(n - 1));  // n is a power of two
+    const size_t row = c >> lg;
+    const int j = (int)(row & (size_t)(n - 1)), k = (int)(row >> lg);
+    Stencil<T> s = load_stencil(uc, uc, i, j, k, n);
+    Stencil<T> b;
+    if (BG) b = load_stencil(bg, bg, i, j, k, n);
+    T rcv = rc[c];
+    if (apply_gm) {
+        const uint8_t kb = kmask[c];
+        rcv -= gm * (T)(kb >> 4) * T(0.125);
+        kmask[c] = kb & 15;
+    }
+    const T w = screen_w<T>(kmask, c);
+    const T kc = kap * w;
+    Local<T> o = local_eval<T, BG>(s, b, ih2, nu, kc, T(0), T(0));
+    fc[c] = o.G + rcv;
+    if (BG && coefo) {
+        const float Xb = (float)(b.ax - T(2) * b.c0), Yb = (float)(b.ay - T(2) * b.c0),
+                    Zb = (float)(b.az - T(2) * b.c0);
+        coefo[c] = pack_bf16x2(2.f * (Yb + Zb), 2.f * (Xb + Zb));
+        coefo[total + c] = pack_bf16x2(2.f * (Xb + Yb), -0.25f * (float)b.exy);
+        coefo[2 * total + c] = pack_bf16x2(-0.25f * (float)b.exz, -0.25f * (float)b.eyz);
+        gapo[c] = kc != T(0) ? lsat / (float)w - (float)ih2 * (Xb + Yb + Zb) : 0.f;
+    }
+}
+
+template <typename T, bool BG>
 __global__ void __launch_bounds__(256) k_fas_rhs(const T* __restrict__ uc, const T* __restrict__ rc,
                                                  uint8_t* __restrict__ kmask, const T* __restrict__ bg, int n,
                                                  T ih2, T nu, T kap, T* __restrict__ fc, uint32_t* __restrict__ coefo,
@@ -236,32 +304,9 @@ __global__ void __launch_bounds__(256) k_fas_rhs(const T* __restrict__ uc, const
     const T gm = gm_ptr ? (T)(*gm_ptr) : T(0);
     const size_t total = (size_t)n * n * n;
     const int lg = __ffs(n) - 1;
-    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(c & (size_t)(n - 1));  // n is a power of two
-        const size_t row = c >> lg;
-        const int j = (int)(row & (size_t)(n - 1)), k = (int)(row >> lg);
-        Stencil<T> s = load_stencil(uc, uc, i, j, k, n);
-        Stencil<T> b;
-        if (BG) b = load_stencil(bg, bg, i, j, k, n);
-        T rcv = rc[c];
-        if (gm_ptr) {
-            const uint8_t kb = kmask[c];
-            rcv -= gm * (T)(kb >> 4) * T(0.125);
-            kmask[c] = kb & 15;
-        }
-        const T w = screen_w<T>(kmask, c);
-        const T kc = kap * w;
-        Local<T> o = local_eval<T, BG>(s, b, ih2, nu, kc, T(0), T(0));
-        fc[c] = o.G + rcv;
-        if (BG && coefo) {
-            const float Xb = (float)(b.ax - T(2) * b.c0), Yb = (float)(b.ay - T(2) * b.c0),
-                        Zb = (float)(b.az - T(2) * b.c0);
-            coefo[c] = pack_bf16x2(2.f * (Yb + Zb), 2.f * (Xb + Zb));
-            coefo[total + c] = pack_bf16x2(2.f * (Xb + Yb), -0.25f * (float)b.exy);
-            coefo[2 * total + c] = pack_bf16x2(-0.25f * (float)b.exz, -0.25f * (float)b.eyz);
-            gapo[c] = kc != T(0) ? lsat / (float)w - (float)ih2 * (Xb + Yb + Zb) : 0.f;
-        }
-    }
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x)
+        fas_rhs_cell<T, BG>(uc, rc, kmask, bg, n, lg, ih2, nu, kap, fc, coefo, gapo, lsat, gm_ptr != nullptr, gm, total,
+                            c);
 }
 
 // k_fas_rhs for levels of at least 32^3, tiled: a block stages the iterate (and the
@@ -335,51 +380,57 @@ __global__ void __launch_bounds__(256) k_fas_rhs_tile(const T* __restrict__ uc, 
 // separably (weights 3/4 and 1/4 per axis, i.e. 27/64, 9/64, 3/64, 1/64 in 3D), and the
 // children are updated as pairs along x (8-byte / 16-byte accesses).
 template <typename T>
+__device__ __forceinline__ void prolong_add_cell(const T* __restrict__ uc, const T* __restrict__ ur, int nc, int lgc,
+                                                 T* __restrict__ uf, size_t c)
+{
+    const int nf = 2 * nc, mc = nc - 1;
+    const T a = T(0.75), b = T(0.25);
+    const int I = (int)(c & (size_t)mc);  // nc is a power of two
+    const size_t row = c >> lgc;
+    const int J = (int)(row & (size_t)mc), K = (int)(row >> lgc);
+    const int xs[3] = {(I - 1) & mc, I, (I + 1) & mc};
+    const int ys[3] = {(J - 1) & mc, J, (J + 1) & mc};
+    const int zs[3] = {(K - 1) & mc, K, (K + 1) & mc};
+    // along x: px[z][y][child]
+    T px[3][3][2];
+#pragma unroll
+    for (int kz = 0; kz < 3; ++kz)
+#pragma unroll
+        for (int jy = 0; jy < 3; ++jy) {
+            const size_t base = ((size_t)zs[kz] * nc + ys[jy]) * nc;
+            T v[3];
+#pragma unroll
+            for (int ix = 0; ix < 3; ++ix) v[ix] = ur ? uc[base + xs[ix]] - ur[base + xs[ix]] : uc[base + xs[ix]];
+            px[kz][jy][0] = a * v[1] + b * v[0];
+            px[kz][jy][1] = a * v[1] + b * v[2];
+        }
+    // along y, then z, then add to the children
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            T out[2];
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                T py[3];
+#pragma unroll
+                for (int kz = 0; kz < 3; ++kz) py[kz] = a * px[kz][1][dx] + b * px[kz][dy ? 2 : 0][dx];
+                out[dx] = a * py[1] + b * py[dz ? 2 : 0];
+            }
+            T* f = uf + ((size_t)(2 * K + dz) * nf + (2 * J + dy)) * nf + 2 * I;
+            f[0] += out[0];
+            f[1] += out[1];
+        }
+}
+
+template <typename T>
 __global__ void __launch_bounds__(256) k_prolong_add(const T* __restrict__ uc, const T* __restrict__ ur, int nc,
                                                      T* __restrict__ uf)
 {
-    const int nf = 2 * nc, mc = nc - 1;
     const int lgc = __ffs(nc) - 1;
     const size_t total = (size_t)nc * nc * nc;
-    const T a = T(0.75), b = T(0.25);
-    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x) {
-        const int I = (int)(c & (size_t)mc);  // nc is a power of two
-        const size_t row = c >> lgc;
-        const int J = (int)(row & (size_t)mc), K = (int)(row >> lgc);
-        const int xs[3] = {(I - 1) & mc, I, (I + 1) & mc};
-        const int ys[3] = {(J - 1) & mc, J, (J + 1) & mc};
-        const int zs[3] = {(K - 1) & mc, K, (K + 1) & mc};
-        // along x: px[z][y][child]
-        T px[3][3][2];
-#pragma unroll
-        for (int kz = 0; kz < 3; ++kz)
-#pragma unroll
-            for (int jy = 0; jy < 3; ++jy) {
-                const size_t base = ((size_t)zs[kz] * nc + ys[jy]) * nc;
-                T v[3];
-#pragma unroll
-                for (int ix = 0; ix < 3; ++ix) v[ix] = ur ? uc[base + xs[ix]] - ur[base + xs[ix]] : uc[base + xs[ix]];
-                px[kz][jy][0] = a * v[1] + b * v[0];
-                px[kz][jy][1] = a * v[1] + b * v[2];
-            }
-        // along y, then z, then add to the children
-#pragma unroll
-        for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-            for (int dy = 0; dy < 2; ++dy) {
-                T out[2];
-#pragma unroll
-                for (int dx = 0; dx < 2; ++dx) {
-                    T py[3];
-#pragma unroll
-                    for (int kz = 0; kz < 3; ++kz) py[kz] = a * px[kz][1][dx] + b * px[kz][dy ? 2 : 0][dx];
-                    out[dx] = a * py[1] + b * py[dz ? 2 : 0];
-                }
-                T* f = uf + ((size_t)(2 * K + dz) * nf + (2 * J + dy)) * nf + 2 * I;
-                f[0] += out[0];
-                f[1] += out[1];
-            }
-    }
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x)
+        prolong_add_cell<T>(uc, ur, nc, lgc, uf, c);
 }
 
 // The same prolongation for coarse grids of at least 32^3, tiled: a block stages the
@@ -441,15 +492,24 @@ __global__ void __launch_bounds__(256) k_prolong_add_tile(const T* __restrict__ 
 // storage type's arithmetic (FP64 for the FP64 cycle, FP32 inside the FP32 inner cycle):
 // `sweeps` red-black sweeps, each followed by the gauge update lambda -= sum r / #unfloored.
 // The block sums go through warp shuffles and one exchange between the warps.
+template <typename T>
+struct CoarsestSmem {
+    T su[512], ss[512], sf[512], sb[512];
+    uint8_t sk[512];
+    T red[2][8];
+};
+
+// The coarsest solve of one level (at most 8^3 cells) by the calling block, its arrays in sm.
 template <typename T, bool BG>
-__global__ void __launch_bounds__(256) k_coarsest(T* __restrict__ u, const T* __restrict__ F, T fscale,
-                                                  const uint8_t* __restrict__ kmask, const T* __restrict__ bg, int n,
-                                                  double ih2_d, double nu_d, double kap_d, double eta, int sweeps,
-                                                  bool floor_piece)
+__device__ void coarsest_block(T* __restrict__ u, const T* __restrict__ F, T fscale, const uint8_t* __restrict__ kmask,
+                               const T* __restrict__ bg, int n, double ih2_d, double nu_d, double kap_d, double eta,
+                               int sweeps, bool floor_piece, CoarsestSmem<T>& sm)
 {
-    __shared__ T su[512], ss[512], sf[512], sb[512];
-    __shared__ uint8_t sk[512];
-    __shared__ T red[2][8];
+    T* su = sm.su;
+    T* ss = sm.ss;
+    T* sf = sm.sf;
+    T* sb = sm.sb;
+    uint8_t* sk = sm.sk;
     const int cells = n * n * n, t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const T ih2 = (T)ih2_d, nu = (T)nu_d, kap = (T)kap_d;
     for (int c = t; c < cells; c += blockDim.x) {
@@ -500,19 +560,29 @@ __global__ void __launch_bounds__(256) k_coarsest(T* __restrict__ u, const T* __
             a1 += __shfl_down_sync(0xffffffffu, a1, o);
         }
         if (lane == 0) {
-            red[0][wid] = a0;
-            red[1][wid] = a1;
+            sm.red[0][wid] = a0;
+            sm.red[1][wid] = a1;
         }
         __syncthreads();
         T s0 = T(0), s1 = T(0);
         for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {  // every thread, the same order
-            s0 += red[0][q];
-            s1 += red[1][q];
+            s0 += sm.red[0][q];
+            s1 += sm.red[1][q];
         }
         if (s1 > T(0)) lam -= s0 / s1;
         __syncthreads();
     }
     for (int c = t; c < cells; c += blockDim.x) u[c] = su[c];
+}
+
+template <typename T, bool BG>
+__global__ void __launch_bounds__(256) k_coarsest(T* __restrict__ u, const T* __restrict__ F, T fscale,
+                                                  const uint8_t* __restrict__ kmask, const T* __restrict__ bg, int n,
+                                                  double ih2_d, double nu_d, double kap_d, double eta, int sweeps,
+                                                  bool floor_piece)
+{
+    __shared__ CoarsestSmem<T> sm;
+    coarsest_block<T, BG>(u, F, fscale, kmask, bg, n, ih2_d, nu_d, kap_d, eta, sweeps, floor_piece, sm);
 }
 
 // ------------------------------------------------------------------ exact coarsest solve
