@@ -69,6 +69,10 @@ typedef struct {
                               0: coarse_sweeps red-black sweeps with gauge updates (0) */
     int grad_order;        /* force_interp / pm_step gradient: 4 the five-point fourth-order difference of
                               Sec. 3.5.2, 2 the two-point central difference (4) */
+    int batch_persistent;  /* scalar_mg_solve_batched: 1 runs the inner V-cycle's levels 32^3 .. 4^3 of every box of
+                              at least 64^3 in one persistent cooperative launch per outer iteration, with grid
+                              barriers whose waits are bounded (PM_ERR_TIMEOUT when one gives up); 0 launches
+                              them per box (1; applies with coarse_exact = 0, coarsest_n = 4, inner_cycles = 1) */
 } pm_params;
 
 /* Report of one solve.  rel_res = |r|_2 / |f - <f>|_2 of the FP64 residual. */
@@ -156,6 +160,17 @@ pm_status scalar_mg_solve(pm_ctx* ctx, const double* delta, int n, double alpha_
 pm_status scalar_mg_solve_batched(pm_ctx* ctx, int nbox, const int* n, const double* const* delta,
                                   const double* alpha_B0, const double* alpha_M0, const double* a, double tol,
                                   double* const* phi_inout, pm_solve_info* infos);
+
+/*
+ * Test hook of the batched solve's bounded grid barrier (pm_params.batch_persistent).  With
+ * block >= 0, block `block` of the persistent coarse-level kernel leaves the kernel just
+ * before its `barrier`-th grid barrier (counted from 0) in every launch, so that the other
+ * blocks' bounded waits run out: the batched solve then returns PM_ERR_TIMEOUT with its
+ * results undefined, and the context stays usable.  Nothing faults: the blocks only stop
+ * early.  block < 0 restores normal operation.  wait_s (> 0) sets how long one barrier wait
+ * may take before it gives up (default 2 s); <= 0 keeps the current bound.
+ */
+pm_status pm_batch_barrier_test(pm_ctx* ctx, int block, int barrier, double wait_s);
 
 /*
  * Force interpolation (Eq. force, Eq. phipsi_mod, Sec. 3.5.2): acc = -grad Psi at the

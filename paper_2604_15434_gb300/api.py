@@ -33,7 +33,8 @@ class Params(ctypes.Structure):
                 ("npost", ctypes.c_int), ("max_cycles", ctypes.c_int), ("coarsest_n", ctypes.c_int),
                 ("coarse_sweeps", ctypes.c_int), ("precision", ctypes.c_int), ("include_dot_alphaB", ctypes.c_int),
                 ("inner_cycles", ctypes.c_int), ("autotune", ctypes.c_int), ("linear_eft", ctypes.c_int),
-                ("smoother", ctypes.c_int), ("coarse_exact", ctypes.c_int), ("grad_order", ctypes.c_int)]
+                ("smoother", ctypes.c_int), ("coarse_exact", ctypes.c_int), ("grad_order", ctypes.c_int),
+                ("batch_persistent", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -77,6 +78,7 @@ SIGNATURES = {
     "pm_mg_sweep": (_I, [_P, _P, _P, _D, _I, _D, _D, _D, _P]),
     "pm_mg_residual": (_I, [_P, _P, _P, _D, _I, _D, _D, _D, _P, _P, _P]),
     "pm_mg_coarse_exact": (_I, [_P, _P, _P, _I, _D, _D, _D, _P, _P]),
+    "pm_batch_barrier_test": (_I, [_P, _I, _I, _D]),
     "pm_mg_restrict": (_I, [_P, _P, _I, _P]),
     "pm_mg_prolong_add": (_I, [_P, _P, _I, _P]),
     "pm_trace_enable": (_I, [_P, _I]),
@@ -176,6 +178,12 @@ class Context:
         if st != PM_OK:
             msg = load().pm_last_error(self._h)
             raise PMError(st, msg.decode() if msg else "")
+
+    def batch_barrier_test(self, block: int, barrier: int = 0, wait_s: float = 0.0):
+        """Make block `block` of the batched solve's persistent kernel leave before barrier
+        `barrier`, so that the others' bounded waits (wait_s seconds) run out; block < 0 undoes it
+        (see pm_batch_barrier_test)."""
+        self._check(load().pm_batch_barrier_test(self._h, int(block), int(barrier), float(wait_s)))
 
     def trace(self, on: bool = True):
         """Per-launch CUDA-event tracing of the library's kernels (see pm_trace_enable)."""

@@ -87,6 +87,68 @@ static void box_iteration(Exec* x, BoxRun& B)
     box_residual(x, B);
 }
 
+// The same iteration split around the cooperative coarse kernel: box_down runs the levels
+// above level l32 (the 32^3 level) down, box_up the prolongations and post-smoothing back
+// up, the correction and the next residual; level l32's iterate is in u[cur32] after the
+// cooperative kernel.
+static void box_down(Exec* x, BoxRun& B, int l32)
+{
+    Workspace* w = B.w;
+    auto& s = w->s;
+    for (size_t l = 0; l + 1 < s.size(); ++l) {
+        x->begin(PM_K_TRANSFER);
+        k_restrict<float><<<grid_for(x, s[l + 1].cells), kThreads, 0, x->stream>>>(s[l].bg, s[l + 1].n, s[l + 1].bg);
+        x->end();
+    }
+    s[0].cur = 0;
+    s[0].lamp = w->shift;
+    cudaMemsetAsync(s[0].u[0], 0, B.cells * sizeof(float), x->stream);
+    vcycle_down<float>(x, s, l32, w->rplain, 1.0f, 0.0f, B.c);
+}
+
+static void box_up(Exec* x, BoxRun& B, int l32, int cur32)
+{
+    Workspace* w = B.w;
+    auto& s = w->s;
+    s[l32].cur = cur32;
+    vcycle_up<float>(x, s, l32, w->rplain, 1.0f, 0.0f, B.c);
+    add_correction_ff(x, ff_chi(w), s[0].u[s[0].cur], B.cells);
+    box_residual(x, B);
+}
+
+// level index of the 32^3 level of a box of size n
+static int coop_level(int n)
+{
+    int l = 0;
+    while ((n >> l) > kCoopTop) ++l;
+    return l;
+}
+
+static pm_status coop_alloc(pm_ctx* ctx, int nbox)
+{
+    if (ctx->coop_cap >= nbox) return PM_OK;
+    cudaFree(ctx->coop_boxes);
+    cudaFree(ctx->coop_active);
+    cudaFreeHost(ctx->coop_active_host);
+    cudaFree(ctx->coop_partials);
+    cudaFree(ctx->coop_gm);
+    ctx->coop_boxes = nullptr;
+    ctx->coop_active = nullptr;
+    ctx->coop_active_host = nullptr;
+    ctx->coop_partials = nullptr;
+    ctx->coop_gm = nullptr;
+    ctx->coop_cap = 0;
+    PM_CUDA(cudaMalloc(&ctx->coop_boxes, sizeof(CoopBox) * nbox));
+    PM_CUDA(cudaMalloc(&ctx->coop_active, sizeof(int) * nbox));
+    PM_CUDA(cudaMallocHost(&ctx->coop_active_host, sizeof(int) * nbox));
+    PM_CUDA(cudaMalloc(&ctx->coop_partials, sizeof(double) * 2 * kCoopMaxItems * nbox));
+    PM_CUDA(cudaMalloc(&ctx->coop_gm, sizeof(float) * nbox));
+    if (!ctx->coop_bar) PM_CUDA(cudaMalloc(&ctx->coop_bar, sizeof(unsigned) * 4));
+    if (!ctx->coop_err_host) PM_CUDA(cudaMallocHost(&ctx->coop_err_host, sizeof(int)));
+    ctx->coop_cap = nbox;
+    return PM_OK;
+}
+
 // FP64 result of a box and its FP64 residual (sums to pinned host memory), eager.
 static void box_confirm(Exec* x, BoxRun& B)
 {
@@ -241,11 +303,50 @@ pm_status mg_solve_batched(pm_ctx* ctx, int nbox, const int* nn, const double* c
     std::vector<std::vector<cudaGraphNode_t>> box_nodes(nbox);
     std::vector<pm_profile> box_prof(nbox);
     std::vector<char> enabled(nbox, 0);
+    // the boxes whose levels 32^3 .. 4^3 run in the cooperative kernel, and their table
+    std::vector<int> coop_idx(nbox, -1);
+    int ncoop = 0;
+    long long coop_launches = 0;
+    if (P.batch_persistent && !P.coarse_exact && P.coarsest_n == 4 && P.inner_cycles == 1) {
+        std::vector<CoopBox> tab;
+        for (int b = 0; b < nbox; ++b) {
+            if (!B[b].active || nn[b] < 2 * kCoopTop) continue;
+            Workspace* w = B[b].w;
+            const int l32 = coop_level(nn[b]);
+            if ((int)w->s.size() != l32 + kCoopLevels) continue;
+            CoopBox cb{};
+            for (int k = 0; k < kCoopLevels; ++k) {
+                Level<float>& L = w->s[l32 + k];
+                cb.lv[k] = CoopLevel{{L.u[0], L.u[1]}, L.f, L.r, L.ur, L.bg, L.kmask, L.sat, L.n};
+            }
+            cb.nu = (float)B[b].c.nu;
+            cb.kap = (float)B[b].c.kap;
+            cb.nu_d = B[b].c.nu;
+            cb.kap_d = B[b].c.kap;
+            coop_idx[b] = ncoop++;
+            tab.push_back(cb);
+        }
+        if (ncoop > 0) {
+            PM_TRY(coop_alloc(ctx, ncoop));
+            PM_CUDA(cudaMemcpy(ctx->coop_boxes, tab.data(), sizeof(CoopBox) * ncoop, cudaMemcpyHostToDevice));
+        }
+    }
     {
         std::vector<int> act;
         for (int b = 0; b < nbox; ++b)
             if (B[b].active) act.push_back(b);
-        if (!act.empty()) {
+        // if the cooperative launch cannot be captured, capture again without it
+        for (int attempt = 0; attempt < 2 && !act.empty() && !exec; ++attempt) {
+            if (attempt == 1) {
+                if (ncoop == 0) break;
+                ncoop = 0;
+                for (int b = 0; b < nbox; ++b) {
+                    coop_idx[b] = -1;
+                    box_nodes[b].clear();
+                    box_prof[b] = pm_profile{};
+                }
+                coop_launches = 0;
+            }
             const pm_profile before = ctx->prof;
             cudaStream_t ms = ctx->batch_stream;
             cudaEvent_t fork;
@@ -254,7 +355,7 @@ pm_status mg_solve_batched(pm_ctx* ctx, int nbox, const int* nn, const double* c
             cudaEventRecord(fork, ms);
             cudaGraph_t cg = nullptr;
             cudaStreamCaptureStatus cs;
-            PM_CUDA(cudaStreamGetCaptureInfo(ms, &cs, nullptr, &cg, nullptr, nullptr, nullptr));
+            cudaStreamGetCaptureInfo(ms, &cs, nullptr, &cg, nullptr, nullptr, nullptr);
             std::set<cudaGraphNode_t> seen;
             auto new_nodes = [&](std::vector<cudaGraphNode_t>& out) {
                 size_t nn = 0;
@@ -272,24 +373,87 @@ pm_status mg_solve_batched(pm_ctx* ctx, int nbox, const int* nn, const double* c
             std::vector<cudaGraphNode_t> dummy;
             new_nodes(dummy);  // the fork
             std::vector<cudaEvent_t> joins;
+            auto join_into_ms = [&](cudaStream_t st) {
+                cudaEvent_t join;
+                cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+                cudaEventRecord(join, st);
+                cudaStreamWaitEvent(ms, join, 0);
+                joins.push_back(join);
+            };
+            auto add_prof = [&](int b, const pm_profile& pb) {
+                for (int k = 0; k < PM_K_COUNT; ++k) {
+                    box_prof[b].launches[k] += ctx->prof.launches[k] - pb.launches[k];
+                    box_prof[b].fine_launches[k] += ctx->prof.fine_launches[k] - pb.fine_launches[k];
+                    box_prof[b].cells[k] += ctx->prof.cells[k] - pb.cells[k];
+                }
+            };
+            // down: the coarse-kernel boxes to their 32^3 level, every other box a whole iteration
             for (int b : act) {
                 Workspace* w = B[b].w;
                 const pm_profile pb = ctx->prof;
                 cudaStreamWaitEvent(w->stream, fork, 0);
                 Exec x(ctx, w->stream, w->partials, w->out, w->host, false);
-                box_iteration(&x, B[b]);
-                cudaEvent_t join;
-                cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
-                cudaEventRecord(join, w->stream);
-                cudaStreamWaitEvent(ms, join, 0);
-                joins.push_back(join);
+                if (coop_idx[b] >= 0) box_down(&x, B[b], coop_level(nn[b]));
+                else box_iteration(&x, B[b]);
+                join_into_ms(w->stream);
                 new_nodes(box_nodes[b]);
-                for (int k = 0; k < PM_K_COUNT; ++k) {
-                    box_prof[b].launches[k] = ctx->prof.launches[k] - pb.launches[k];
-                    box_prof[b].fine_launches[k] = ctx->prof.fine_launches[k] - pb.fine_launches[k];
-                    box_prof[b].cells[k] = ctx->prof.cells[k] - pb.cells[k];
-                }
+                add_prof(b, pb);
                 enabled[b] = 1;
+            }
+            if (ncoop > 0) {
+                // the coarse levels of every box in one cooperative launch
+                cudaMemsetAsync(ctx->coop_bar, 0, sizeof(unsigned) * 4, ms);  // errors surface at the end of capture
+                CoopParams cp{};
+                cp.boxes = reinterpret_cast<const CoopBox*>(ctx->coop_boxes);
+                cp.active = ctx->coop_active;
+                cp.nbox = ncoop;
+                cp.npre = P.npre;
+                cp.npost = P.npost;
+                cp.coarse_sweeps = P.coarse_sweeps;
+                cp.eta = P.eta;
+                cp.partials = ctx->coop_partials;
+                cp.gm = ctx->coop_gm;
+                cp.bar = ctx->coop_bar;
+                cp.err = reinterpret_cast<int*>(ctx->coop_bar + 2);
+                int khz = 0;
+                cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, ctx->device);
+                cp.spin_limit = (long long)(ctx->coop_wait_s * (double)(khz > 0 ? khz : 2000000) * 1e3);
+                cp.fail_block = ctx->coop_fail_block;
+                cp.fail_barrier = ctx->coop_fail_barrier;
+                int per_sm = 0;
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_coarse, kCoopThreads, 0);
+                int grid = ctx->num_sms * (per_sm < 2 ? per_sm : 2);
+                if (grid < 1) grid = 1;
+                cudaLaunchConfig_t lc{};
+                lc.gridDim = dim3(grid);
+                lc.blockDim = dim3(kCoopThreads);
+                lc.dynamicSmemBytes = 0;
+                lc.stream = ms;
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeCooperative;
+                at[0].val.cooperative = 1;
+                lc.attrs = at;
+                lc.numAttrs = 1;
+                ctx->prof.launches[PM_K_TRANSFER] += 1;
+                coop_launches += 1;
+                if (cudaLaunchKernelEx(&lc, k_batch_coarse, cp) != cudaSuccess) cudaGetLastError();
+                cudaMemcpyAsync(ctx->coop_err_host, ctx->coop_bar + 2, sizeof(int), cudaMemcpyDeviceToHost, ms);
+                cudaEvent_t fork2;
+                cudaEventCreateWithFlags(&fork2, cudaEventDisableTiming);
+                cudaEventRecord(fork2, ms);
+                joins.push_back(fork2);
+                const int cur32 = (P.npre + P.npost) & 1;
+                for (int b : act) {
+                    if (coop_idx[b] < 0) continue;
+                    Workspace* w = B[b].w;
+                    const pm_profile pb = ctx->prof;
+                    cudaStreamWaitEvent(w->stream, fork2, 0);
+                    Exec x(ctx, w->stream, w->partials, w->out, w->host, false);
+                    box_up(&x, B[b], coop_level(nn[b]), cur32);
+                    join_into_ms(w->stream);
+                    new_nodes(box_nodes[b]);
+                    add_prof(b, pb);
+                }
             }
             cudaGraph_t g = nullptr;
             cudaError_t ce = cudaStreamEndCapture(ms, &g);
@@ -297,6 +461,9 @@ pm_status mg_solve_batched(pm_ctx* ctx, int nbox, const int* nn, const double* c
             cudaEventDestroy(fork);
             ctx->prof = before;  // capture launched nothing; replays are counted below
             if (ce != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                cudaGetLastError();
+                if (attempt == 0 && ncoop > 0) continue;
                 ctx->set_error(std::string("graph capture failed: ") + cudaGetErrorString(ce));
                 return PM_ERR_CUDA;
             }
@@ -314,8 +481,21 @@ pm_status mg_solve_batched(pm_ctx* ctx, int nbox, const int* nn, const double* c
                 for (auto nd : box_nodes[b]) PM_CUDA(cudaGraphNodeSetEnabled(exec, nd, 0));
                 enabled[b] = 0;
             }
+        if (ncoop > 0) {
+            for (int b = 0; b < nbox; ++b)
+                if (coop_idx[b] >= 0) ctx->coop_active_host[coop_idx[b]] = B[b].active ? 1 : 0;
+            PM_CUDA(cudaMemcpyAsync(ctx->coop_active, ctx->coop_active_host, sizeof(int) * ncoop,
+                                    cudaMemcpyHostToDevice, ctx->batch_stream));
+        }
         PM_CUDA(cudaGraphLaunch(exec, ctx->batch_stream));
         PM_CUDA(cudaStreamSynchronize(ctx->batch_stream));
+        if (ncoop > 0) {
+            ctx->prof.launches[PM_K_TRANSFER] += coop_launches;
+            if (*ctx->coop_err_host != PM_OK) {
+                ctx->set_error("batched solve: a grid barrier wait of the persistent coarse-level kernel gave up");
+                return PM_ERR_TIMEOUT;
+            }
+        }
         for (int b : act) {
             for (int k = 0; k < PM_K_COUNT; ++k) {
                 ctx->prof.launches[k] += box_prof[b].launches[k];

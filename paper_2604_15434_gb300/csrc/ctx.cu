@@ -212,6 +212,7 @@ extern "C" void pm_default_params(pm_params* p)
     p->smoother = 0;
     p->coarse_exact = 0;
     p->grad_order = 4;
+    p->batch_persistent = 1;
 }
 
 static bool params_ok(const pm_params* p)
@@ -222,7 +223,8 @@ static bool params_ok(const pm_params* p)
            (p->precision >= 0 && p->precision <= 2) && p->inner_cycles >= 1 && p->inner_cycles <= 16 &&
            (p->autotune == 0 || p->autotune == 1) && (p->linear_eft == 0 || p->linear_eft == 1) &&
            (p->smoother == 0 || p->smoother == 1) && (p->coarse_exact == 0 || (p->coarse_exact == 1 &&
-           p->coarsest_n <= 4)) && (p->grad_order == 2 || p->grad_order == 4);
+           p->coarsest_n <= 4)) && (p->grad_order == 2 || p->grad_order == 4) &&
+           (p->batch_persistent == 0 || p->batch_persistent == 1);
 }
 
 extern "C" pm_status pm_coefficients(double aB0, double aM0, double a, double om0, int include_dot, pm_coeffs* out)
@@ -286,7 +288,23 @@ extern "C" void pm_destroy(pm_ctx* ctx)
     cudaFree(ctx->red_out);
     cudaFree(ctx->flag);
     cudaFreeHost(ctx->host_out);
+    cudaFree(ctx->coop_boxes);
+    cudaFree(ctx->coop_active);
+    cudaFreeHost(ctx->coop_active_host);
+    cudaFree(ctx->coop_partials);
+    cudaFree(ctx->coop_gm);
+    cudaFree(ctx->coop_bar);
+    cudaFreeHost(ctx->coop_err_host);
     delete ctx;
+}
+
+extern "C" pm_status pm_batch_barrier_test(pm_ctx* ctx, int block, int barrier, double wait_s)
+{
+    if (!ctx || barrier < 0) return PM_ERR_INVALID_ARG;
+    ctx->coop_fail_block = block < 0 ? -1 : block;
+    ctx->coop_fail_barrier = block < 0 ? -1 : barrier;
+    if (wait_s > 0.0) ctx->coop_wait_s = wait_s;
+    return PM_OK;
 }
 
 extern "C" const char* pm_last_error(const pm_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }

@@ -193,6 +193,18 @@ struct pm_ctx {
     double* host_out = nullptr;      // pinned host mirror (64 doubles)
     int* flag = nullptr;             // device error flag
     int num_sms = 152;
+    // the batched solve's persistent coarse-level kernel: box table, active flags, sums,
+    // barrier words (counter, generation, error) and its test knob
+    void* coop_boxes = nullptr;
+    int* coop_active = nullptr;
+    int* coop_active_host = nullptr;  // pinned
+    double* coop_partials = nullptr;
+    float* coop_gm = nullptr;
+    unsigned* coop_bar = nullptr;
+    int* coop_err_host = nullptr;     // pinned
+    int coop_cap = 0;
+    int coop_fail_block = -1, coop_fail_barrier = -1;
+    double coop_wait_s = 2.0;
     std::map<int, int> tuned;  // autotuned tile variant per (level size, inputs)
     std::string tune_log;
     // tracing (pm_trace_*): event pairs per launch, summed per class on read-out

@@ -1258,40 +1258,15 @@ static bool residual_restrict_f32(Exec* ctx, Level<float>& L, Level<float>& C, c
     return true;
 }
 
+// The first half of one level of the FAS V-cycle: pre-smoothing, residual, restriction
+// to level l+1 and its right-hand side.
 template <typename T>
-static void vcycle(Exec* ctx, std::vector<Level<T>>& lv, int l, const T* F0, T fs0, T lam0, const Coef& c)
+static void level_down(Exec* ctx, std::vector<Level<T>>& lv, int l, const T* F0, T fs0, T lam0, const Coef& c)
 {
     Level<T>& L = lv[l];
     const T* F = l == 0 ? F0 : L.f;
     const T fs = l == 0 ? fs0 : T(1);
     const T lam = l == 0 ? lam0 : T(0);
-    const int nlev = (int)lv.size();
-    if (l == nlev - 1) {
-        const double ih2 = (double)L.n * (double)L.n;
-        if (ctx->prm.coarse_exact && L.cells <= (size_t)kExactMaxCells) {
-            ctx->begin(PM_K_COARSEST, false, 0);
-            if (L.bg)
-                k_coarsest_exact<T, true><<<1, kExactThreads, 0, ctx->stream>>>(
-                    L.u[L.cur], F, fs, L.kmask, L.bg, L.n, ih2, c.nu, c.kap, c.eta, nullptr);
-            else
-                k_coarsest_exact<T, false><<<1, kExactThreads, 0, ctx->stream>>>(
-                    L.u[L.cur], F, fs, L.kmask, nullptr, L.n, ih2, c.nu, c.kap, c.eta, nullptr);
-            ctx->end();
-            return;
-        }
-        if (L.bg) {
-            ctx->begin(PM_K_COARSEST, false, 0);
-            k_coarsest<T, true><<<1, 256, 0, ctx->stream>>>(L.u[L.cur], F, fs, L.kmask, L.bg, L.n, ih2, c.nu, c.kap,
-                                                            c.eta, ctx->prm.coarse_sweeps, L.fine);
-            ctx->end();
-        } else {
-            ctx->begin(PM_K_COARSEST, false, 0);
-            k_coarsest<T, false><<<1, 256, 0, ctx->stream>>>(L.u[L.cur], F, fs, L.kmask, nullptr, L.n, ih2, c.nu,
-                                                             c.kap, c.eta, ctx->prm.coarse_sweeps, L.fine);
-            ctx->end();
-        }
-        return;
-    }
     for (int s = 0; s < ctx->prm.npre; ++s) sweep(ctx, L, F, fs, lam, c);
     Level<T>& C = lv[l + 1];
     C.cur = 0;
@@ -1331,7 +1306,17 @@ static void vcycle(Exec* ctx, std::vector<Level<T>>& lv, int l, const T* F0, T f
                                                                   (T)c.kap, C.f, nullptr, nullptr, 0.f, gmp);
         ctx->end();
     }
-    vcycle(ctx, lv, l + 1, F0, fs0, lam0, c);
+}
+
+// The second half: prolongation of level l+1's correction and post-smoothing.
+template <typename T>
+static void level_up(Exec* ctx, std::vector<Level<T>>& lv, int l, const T* F0, T fs0, T lam0, const Coef& c)
+{
+    Level<T>& L = lv[l];
+    const T* F = l == 0 ? F0 : L.f;
+    const T fs = l == 0 ? fs0 : T(1);
+    const T lam = l == 0 ? lam0 : T(0);
+    Level<T>& C = lv[l + 1];
     ctx->begin(PM_K_TRANSFER, false, 0);
     if (C.n >= 32)
         k_prolong_add_tile<T><<<dim3(C.n / 32, C.n / 4, C.n / 4), 256, 0, ctx->stream>>>(C.u[C.cur], C.ur, C.n,
@@ -1340,6 +1325,58 @@ static void vcycle(Exec* ctx, std::vector<Level<T>>& lv, int l, const T* F0, T f
         k_prolong_add<T><<<grid_for(ctx, C.cells), kThreads, 0, ctx->stream>>>(C.u[C.cur], C.ur, C.n, L.u[L.cur]);
     ctx->end();
     for (int s = 0; s < ctx->prm.npost; ++s) sweep(ctx, L, F, fs, lam, c);
+}
+
+template <typename T>
+static void vcycle(Exec* ctx, std::vector<Level<T>>& lv, int l, const T* F0, T fs0, T lam0, const Coef& c)
+{
+    Level<T>& L = lv[l];
+    const T* F = l == 0 ? F0 : L.f;
+    const T fs = l == 0 ? fs0 : T(1);
+    const T lam = l == 0 ? lam0 : T(0);
+    const int nlev = (int)lv.size();
+    if (l == nlev - 1) {
+        const double ih2 = (double)L.n * (double)L.n;
+        if (ctx->prm.coarse_exact && L.cells <= (size_t)kExactMaxCells) {
+            ctx->begin(PM_K_COARSEST, false, 0);
+            if (L.bg)
+                k_coarsest_exact<T, true><<<1, kExactThreads, 0, ctx->stream>>>(
+                    L.u[L.cur], F, fs, L.kmask, L.bg, L.n, ih2, c.nu, c.kap, c.eta, nullptr);
+            else
+                k_coarsest_exact<T, false><<<1, kExactThreads, 0, ctx->stream>>>(
+                    L.u[L.cur], F, fs, L.kmask, nullptr, L.n, ih2, c.nu, c.kap, c.eta, nullptr);
+            ctx->end();
+            return;
+        }
+        if (L.bg) {
+            ctx->begin(PM_K_COARSEST, false, 0);
+            k_coarsest<T, true><<<1, 256, 0, ctx->stream>>>(L.u[L.cur], F, fs, L.kmask, L.bg, L.n, ih2, c.nu, c.kap,
+                                                            c.eta, ctx->prm.coarse_sweeps, L.fine);
+            ctx->end();
+        } else {
+            ctx->begin(PM_K_COARSEST, false, 0);
+            k_coarsest<T, false><<<1, 256, 0, ctx->stream>>>(L.u[L.cur], F, fs, L.kmask, nullptr, L.n, ih2, c.nu,
+                                                             c.kap, c.eta, ctx->prm.coarse_sweeps, L.fine);
+            ctx->end();
+        }
+        return;
+    }
+    level_down(ctx, lv, l, F0, fs0, lam0, c);
+    vcycle(ctx, lv, l + 1, F0, fs0, lam0, c);
+    level_up(ctx, lv, l, F0, fs0, lam0, c);
+}
+
+// The levels above `stop` of a V-cycle, down and up; level `stop` and below are solved in
+// between by the caller (the batched solve's cooperative coarse kernel).
+template <typename T>
+static void vcycle_down(Exec* ctx, std::vector<Level<T>>& lv, int stop, const T* F0, T fs0, T lam0, const Coef& c)
+{
+    for (int l = 0; l < stop; ++l) level_down(ctx, lv, l, F0, fs0, lam0, c);
+}
+template <typename T>
+static void vcycle_up(Exec* ctx, std::vector<Level<T>>& lv, int stop, const T* F0, T fs0, T lam0, const Coef& c)
+{
+    for (int l = stop - 1; l >= 0; --l) level_up(ctx, lv, l, F0, fs0, lam0, c);
 }
 
 template <typename T>
@@ -1642,6 +1679,7 @@ pm_status mg_solve(pm_ctx* pctx, const double* delta, int n, const pm_coeffs& cf
 
 }  // namespace pmeft
 
+#include "batch_coop.cuh"
 #include "batch.cuh"
 
 using namespace pmeft;

@@ -447,15 +447,57 @@ def test_batched_solve_matches_oracle_per_box(gpu_lib):
 
 
 def test_batched_solve_equals_single_box_solves(gpu_lib):
+    """With every level launched per box (batch_persistent = 0) a batched box runs exactly the
+    single solve's kernels: the same cycle count and chi to 1e-7."""
     sizes = [32, 64, 32]
     boxes = _box_set(sizes, 777)
-    ctx = gpu_lib.Context(max_cycles=100)
+    ctx = gpu_lib.Context(max_cycles=100, batch_persistent=0)
     phis, infos = gpu_lib.scalar_mg_solve_batched([cu(d) for d, *_ in boxes], [b[1] for b in boxes],
                                                   [b[2] for b in boxes], [b[3] for b in boxes], 1e-9, ctx=ctx)
     for (d, aB, aM, a), phi, info in zip(boxes, phis, infos):
         single, sinfo = gpu_lib.scalar_mg_solve(cu(d), aB, aM, a, 1e-9, ctx=gpu_lib.Context(precision=1))
         assert info["cycles"] == sinfo["cycles"]
         assert float((phi - single).norm() / single.norm()) < 1e-7
+
+
+def test_persistent_coarse_kernel_matches_per_box_launches(gpu_lib):
+    """The batched solve with the coarse levels (32^3 .. 4^3) of all boxes of at least 64^3 in
+    one cooperative launch per outer iteration against the same boxes with those levels launched
+    per box: the same converged chi (1e-6; the kernel's gauge sums are added in another order)
+    within one outer iteration, and each box against the oracle."""
+    sizes = [64, 128, 32, 64, 128, 64]
+    boxes = _box_set(sizes, 2024)
+    args = ([cu(d) for d, *_ in boxes], [b[1] for b in boxes], [b[2] for b in boxes], [b[3] for b in boxes], 1e-8)
+    pa, ia = gpu_lib.scalar_mg_solve_batched(*args, ctx=gpu_lib.Context(max_cycles=100, batch_persistent=1))
+    pb, ib = gpu_lib.scalar_mg_solve_batched(*args, ctx=gpu_lib.Context(max_cycles=100, batch_persistent=0))
+    for (d, aB, aM, a), x, y, i, j in zip(boxes, pa, pb, ia, ib):
+        assert i["status"] == 0 and j["status"] == 0 and i["rel_res"] <= 1e-8
+        assert abs(i["cycles"] - j["cycles"]) <= 1
+        assert float((x - y).norm() / y.norm()) < 1e-6
+        want, _, st = O.scalar_solve(d, aB, aM, a, 1e-11)
+        assert rel(x.cpu().numpy(), want) < 1e-6
+
+
+def test_persistent_kernel_barrier_timeout_is_reported(gpu_lib):
+    """The grid barriers of the persistent coarse-level kernel wait a bounded time: when one block
+    leaves the kernel before a barrier (the test hook; nothing faults), the others' waits run out
+    after 0.2 s and the batched solve returns PM_ERR_TIMEOUT; with the hook off, the same
+    context solves the same boxes normally."""
+    sizes = [64, 64]
+    boxes = _box_set(sizes, 99)
+    args = ([cu(d) for d, *_ in boxes], [b[1] for b in boxes], [b[2] for b in boxes], [b[3] for b in boxes], 1e-8)
+    ctx = gpu_lib.Context(max_cycles=100, batch_persistent=1)
+    for barrier in (0, 5):
+        ctx.batch_barrier_test(0, barrier, 0.2)
+        with pytest.raises(gpu_lib.PMError) as e:
+            gpu_lib.scalar_mg_solve_batched(*args, ctx=ctx)
+        assert e.value.status == gpu_lib.PM_ERR_TIMEOUT
+    ctx.batch_barrier_test(-1)
+    phis, infos = gpu_lib.scalar_mg_solve_batched(*args, ctx=ctx)
+    assert all(i["status"] == 0 and i["rel_res"] <= 1e-8 for i in infos)
+    for (d, aB, aM, a), phi in zip(boxes, phis):
+        want, _, st = O.scalar_solve(d, aB, aM, a, 1e-11)
+        assert rel(phi.cpu().numpy(), want) < 1e-6
 
 
 def test_nonconvergent_parameters_report_an_error(gpu_lib):
