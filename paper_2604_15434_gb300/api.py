@@ -94,6 +94,7 @@ SIGNATURES = {
     "scalar_mg_solve_batched": (_I, [_P, _I, _P, _P, _P, _P, _P, _D, _P, _P]),
     "pm_unet_num_params": (_LL, []),
     "pm_unet_create": (_I, [_P, _P]),
+    "pm_unet_set_conv_path": (_I, [_P, _I]),
     "pm_unet_destroy": (None, [_P]),
     "pm_unet_set_params": (_I, [_P, _P, _LL]),
     "pm_unet_get_params": (_I, [_P, _P, _LL, _I]),
@@ -438,6 +439,10 @@ class UNet:
         self.ctx._check(load().pm_unet_create(self.ctx._h, ctypes.byref(h)))
         self._h = h
         self.num_params = int(load().pm_unet_num_params())
+
+    def set_conv_path(self, path: int):
+        """0: mma.sync convolutions, 1: tcgen05 tensor-core convolutions (see pm_unet_set_conv_path)."""
+        self.ctx._check(load().pm_unet_set_conv_path(self._h, int(path)))
 
     def set_params(self, p):
         import numpy as np

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "conv.cuh"
+#include "conv_umma.cuh"
 #include "internal.cuh"
 
 struct pm_unet;
@@ -363,6 +364,49 @@ static pm_status ensure_acts(pm_unet* u, int n, bool train)
 
 static int blocks_for(pm_ctx* ctx, size_t work) { return grid_for(ctx, work); }
 
+// The convolution on the tcgen05 tensor cores (conv_umma.cuh), in slices of NT output channels
+// whose resident weights fit next to the input patch in shared memory.  Returns false (nothing
+// launched) where it does not apply.
+template <int NT>
+static void launch_umma(pm_ctx* ctx, const __nv_bfloat16* in, int in_ld, int in_off, int ci, const __nv_bfloat16* w,
+                        int co, int co0, const float* bias, __nv_bfloat16* out, int out_ld, int out_off, int n, bool relu,
+                        const __nv_bfloat16* mask, int mask_ld, int mask_off)
+{
+    const size_t smem = umma_smem<NT>(ci);
+    auto k = k_conv3d_umma<NT>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kUmThreads, smem);
+    constexpr int cols = NT <= 32 ? 32 : (NT <= 64 ? 64 : (NT <= 128 ? 128 : 256));
+    per_sm = std::max(1, std::min(per_sm, 512 / cols));  // the blocks of an SM share its 512 TMEM columns
+    const long long tiles = (long long)(n / kUmTX) * (n / kUmTY) * n;
+    const long long g = std::min<long long>(tiles, (long long)ctx->num_sms * per_sm);
+    k<<<(int)g, kUmThreads, smem, ctx->stream>>>(in, in_ld, in_off, ci, w, co, co0, bias, out, out_ld, out_off, n,
+                                                  relu ? 1 : 0, mask, mask_ld, mask_off, ctx->flag + 2);
+}
+
+static bool conv_umma(pm_ctx* ctx, const __nv_bfloat16* in, int in_ld, int in_off, int ci, const __nv_bfloat16* w,
+                      int co, const float* bias, __nv_bfloat16* out, int out_ld, int out_off, int n, bool relu,
+                      const __nv_bfloat16* mask, int mask_ld, int mask_off)
+{
+    if (ctx->conv_path != 1 || n < kUmTY || n % kUmTY != 0 || ci % 16 != 0 || co % 16 != 0) return false;
+    auto bytes = [&](int nt) { return (size_t)27 * (ci / 16) * nt * 32 + (size_t)(ci / 16) * kUmPV * 32 + 64; };
+    int nt = co;  // the widest slice whose weights fit
+    while (bytes(nt) > (size_t)227 * 1024 && nt % 32 == 0) nt /= 2;
+    if (bytes(nt) > (size_t)227 * 1024) return false;
+    for (int co0 = 0; co0 < co; co0 += nt) {
+        switch (nt) {
+            case 16: launch_umma<16>(ctx, in, in_ld, in_off, ci, w, co, co0, bias, out, out_ld, out_off, n, relu, mask, mask_ld, mask_off); break;
+            case 32: launch_umma<32>(ctx, in, in_ld, in_off, ci, w, co, co0, bias, out, out_ld, out_off, n, relu, mask, mask_ld, mask_off); break;
+            case 48: launch_umma<48>(ctx, in, in_ld, in_off, ci, w, co, co0, bias, out, out_ld, out_off, n, relu, mask, mask_ld, mask_off); break;
+            case 64: launch_umma<64>(ctx, in, in_ld, in_off, ci, w, co, co0, bias, out, out_ld, out_off, n, relu, mask, mask_ld, mask_off); break;
+            case 96: launch_umma<96>(ctx, in, in_ld, in_off, ci, w, co, co0, bias, out, out_ld, out_off, n, relu, mask, mask_ld, mask_off); break;
+            default: return false;
+        }
+    }
+    return true;
+}
+
 // forward conv launcher (also the backward-data conv with a mask)
 static void conv_fwd(pm_ctx* ctx, const __nv_bfloat16* in, int in_ld, int in_off, int ci, const __nv_bfloat16* w,
                      int co, const float* bias, __nv_bfloat16* out, int out_ld, int out_off, int n, bool relu,
@@ -370,6 +414,10 @@ static void conv_fwd(pm_ctx* ctx, const __nv_bfloat16* in, int in_ld, int in_off
 {
     const int nvox = n * n * n, grid = (nvox + kConvM - 1) / kConvM;
     ctx->begin(PM_K_PM);
+    if (conv_umma(ctx, in, in_ld, in_off, ci, w, co, bias, out, out_ld, out_off, n, relu, mask, mask_ld, mask_off)) {
+        ctx->end();
+        return;
+    }
     // grids of 16^3 and up whose weights fit next to the patch in shared memory take the
     // persistent tiled kernel, the rest the per-128-voxel kernel
     bool tiled = false;
@@ -495,6 +543,16 @@ static pm_status unet_forward(pm_unet* u, const double* delta, int n, double aB0
     k_head<<<blocks_for(ctx, v0), 256, 0, ctx->stream>>>(A.y9, u->p + u->off[10], (int)v0, A.that);
     ctx->end();
     PM_CUDA(cudaGetLastError());
+    if (ctx->conv_path == 1) {
+        // an mbarrier wait of the tensor-core convolution that gave up (conv_umma.cuh)
+        PM_CUDA(cudaMemcpyAsync(ctx->host_out + 62, ctx->flag + 2, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        PM_CUDA(cudaStreamSynchronize(ctx->stream));
+        if (*reinterpret_cast<int*>(ctx->host_out + 62) != 0) {
+            cudaMemsetAsync(ctx->flag + 2, 0, sizeof(int), ctx->stream);
+            ctx->set_error("tensor-core convolution: an accumulator wait gave up");
+            return PM_ERR_TIMEOUT;
+        }
+    }
     return PM_OK;
 }
 
@@ -661,6 +719,13 @@ extern "C" pm_status pm_unet_get_params(pm_unet* u, float* host, long long count
     pm_ctx* ctx = u->ctx;
     PM_CUDA(cudaMemcpyAsync(host, which == 0 ? u->p : u->g, count * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
     PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    return PM_OK;
+}
+
+extern "C" pm_status pm_unet_set_conv_path(pm_unet* u, int path)
+{
+    if (!u || path < 0 || path > 1) return PM_ERR_INVALID_ARG;
+    u->ctx->conv_path = path;
     return PM_OK;
 }
 
