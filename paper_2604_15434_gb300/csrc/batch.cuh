@@ -315,10 +315,13 @@ pm_status mg_solve_batched(pm_ctx* ctx, int nbox, const int* nn, const double* c
             const int l32 = coop_level(nn[b]);
             if ((int)w->s.size() != l32 + kCoopLevels) continue;
             CoopBox cb{};
+            bool ok = true;
             for (int k = 0; k < kCoopLevels; ++k) {
                 Level<float>& L = w->s[l32 + k];
                 cb.lv[k] = CoopLevel{{L.u[0], L.u[1]}, L.f, L.r, L.ur, L.bg, L.kmask, L.sat, L.n};
+                ok = ok && L.u[0] && L.u[1] && L.f && L.r && L.ur && L.bg && L.kmask && L.sat && L.n == (kCoopTop >> k);
             }
+            if (!ok) continue;  // not the level set the kernel expects: this box keeps per-box launches
             cb.nu = (float)B[b].c.nu;
             cb.kap = (float)B[b].c.kap;
             cb.nu_d = B[b].c.nu;
@@ -438,6 +441,10 @@ pm_status mg_solve_batched(pm_ctx* ctx, int nbox, const int* nn, const double* c
                 coop_launches += 1;
                 if (cudaLaunchKernelEx(&lc, k_batch_coarse, cp) != cudaSuccess) cudaGetLastError();
                 cudaMemcpyAsync(ctx->coop_err_host, ctx->coop_bar + 2, sizeof(int), cudaMemcpyDeviceToHost, ms);
+                {
+                    std::vector<cudaGraphNode_t> shared;  // the memset, kernel and copy belong to no box
+                    new_nodes(shared);
+                }
                 cudaEvent_t fork2;
                 cudaEventCreateWithFlags(&fork2, cudaEventDisableTiming);
                 cudaEventRecord(fork2, ms);
@@ -491,9 +498,14 @@ pm_status mg_solve_batched(pm_ctx* ctx, int nbox, const int* nn, const double* c
         PM_CUDA(cudaStreamSynchronize(ctx->batch_stream));
         if (ncoop > 0) {
             ctx->prof.launches[PM_K_TRANSFER] += coop_launches;
-            if (*ctx->coop_err_host != PM_OK) {
+            const int e = *ctx->coop_err_host;
+            if (e == PM_ERR_TIMEOUT) {
                 ctx->set_error("batched solve: a grid barrier wait of the persistent coarse-level kernel gave up");
                 return PM_ERR_TIMEOUT;
+            }
+            if (e != PM_OK) {
+                ctx->set_error("batched solve: the persistent coarse-level kernel rejected its box table");
+                return PM_ERR_CUDA;
             }
         }
         for (int b : act) {

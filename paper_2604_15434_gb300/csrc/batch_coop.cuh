@@ -101,6 +101,26 @@ __global__ void __launch_bounds__(kCoopThreads) k_batch_coarse(CoopParams P)
     int nbar = 0;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const int nl = kCoopLevels;
+    // every block checks the box table first (the same checks everywhere, so all leave
+    // together): a null buffer or an unexpected level size is recorded and nothing is accessed
+    {
+        __shared__ int bad;
+        if (t == 0) {
+            bad = 0;
+            for (int b = 0; b < P.nbox && !bad; ++b)
+                for (int k = 0; k < nl; ++k) {
+                    const CoopLevel& L = P.boxes[b].lv[k];
+                    if (!L.u[0] || !L.u[1] || !L.f || !L.r || !L.ur || !L.bg || !L.kmask || !L.sat ||
+                        L.n != (kCoopTop >> k))
+                        bad = 1;
+                }
+        }
+        __syncthreads();
+        if (bad) {
+            if (t == 0) atomicCAS(P.err, PM_OK, (int)PM_ERR_INVALID_ARG);
+            return;
+        }
+    }
     // every box has the same level sizes here: 32, 16, 8, 4
     int cur[kCoopLevels] = {0, 0, 0, 0};
 

@@ -205,7 +205,7 @@ struct pm_ctx {
     int coop_cap = 0;
     int coop_fail_block = -1, coop_fail_barrier = -1;
     double coop_wait_s = 2.0;
-    int conv_path = 0;  // U-Net convolutions: 0 mma.sync kernels, 1 tcgen05 tensor-core kernels
+    int conv_path = 0;  // convolution kernels of the U-Net call in progress (its pm_unet::conv_path)
     std::map<int, int> tuned;  // autotuned tile variant per (level size, inputs)
     std::string tune_log;
     // tracing (pm_trace_*): event pairs per launch, summed per class on read-out

@@ -65,10 +65,10 @@ __device__ __forceinline__ T opsplit_update(const Stencil<T>& s, T ih2, T nu, T 
 // lam.  OPS: the local solve of Method II (opsplit_update; etanu = eta |nu|) instead of
 // Method I's.
 template <typename T, bool BG, bool OPS>
-__device__ __forceinline__ void half_sweep_cell(const T* __restrict__ own, const T* __restrict__ oth,
-                                                T* __restrict__ out, const T* __restrict__ F, T fscale, T lam,
-                                                const uint8_t* __restrict__ kmask, const T* __restrict__ bg,
-                                                const T* __restrict__ gap, int n, int lg, int colour, T ih2, T nu,
+__device__ __forceinline__ void half_sweep_cell(const T* own, const T* oth,
+                                                T* out, const T* F, T fscale, T lam,
+                                                const uint8_t* kmask, const T* bg,
+                                                const T* gap, int n, int lg, int colour, T ih2, T nu,
                                                 T kap, T sp, T Df, T lsat_c, T etanu, size_t t)
 {
     const int hn = n >> 1;
@@ -115,12 +115,12 @@ __global__ void __launch_bounds__(256) k_half_sweep(const T* __restrict__ own, c
 // defect-correction loop) also writes the FP32 copies: the plain residual -G for the inner
 // right-hand side, the iterate as the inner background, and the floored gap.
 template <typename T, bool BG, bool WRITE_R, bool MIXED>
-__device__ __forceinline__ void residual_cell(const T* __restrict__ u, const T* __restrict__ F, T fscale, T lam,
-                                              const uint8_t* __restrict__ kmask, const T* __restrict__ bg,
-                                              const T* __restrict__ gap, int n, int lg, T ih2, T nu, T kap, T Df,
-                                              T lsat_c, bool floor_piece, T* __restrict__ r,
-                                              uint8_t* __restrict__ sat, float* __restrict__ rplain,
-                                              float* __restrict__ chi32, float* __restrict__ gap32, size_t c,
+__device__ __forceinline__ void residual_cell(const T* u, const T* F, T fscale, T lam,
+                                              const uint8_t* kmask, const T* bg,
+                                              const T* gap, int n, int lg, T ih2, T nu, T kap, T Df,
+                                              T lsat_c, bool floor_piece, T* r,
+                                              uint8_t* sat, float* rplain,
+                                              float* chi32, float* gap32, size_t c,
                                               float (&fa)[5])
 {
     const int i = (int)(c & (size_t)(n - 1));  // n is a power of two
@@ -192,10 +192,10 @@ __global__ void __launch_bounds__(256) k_residual(const T* __restrict__ u, const
 // value) and the gauge-projected residual r - gm * [unfloored]; the coarse screening mask
 // holds the children's mean unscreened fraction in eighths (floored children count 8).
 template <typename T>
-__device__ __forceinline__ void restrict_fas_cell(const T* __restrict__ uf, const T* __restrict__ rf,
-                                                  const uint8_t* __restrict__ satf, const uint8_t* __restrict__ kmf,
-                                                  T gm, int nc, int lgc, T* __restrict__ ur, T* __restrict__ uc,
-                                                  T* __restrict__ rc, uint8_t* __restrict__ kmc, size_t c)
+__device__ __forceinline__ void restrict_fas_cell(const T* uf, const T* rf,
+                                                  const uint8_t* satf, const uint8_t* kmf,
+                                                  T gm, int nc, int lgc, T* ur, T* uc,
+                                                  T* rc, uint8_t* kmc, size_t c)
 {
     const int nf = 2 * nc;
     const int I = (int)(c & (size_t)(nc - 1));  // nc is a power of two
@@ -263,10 +263,10 @@ __global__ void k_restrict(const T* __restrict__ uf, int nc, T* __restrict__ uc)
 // children's raw mean residual and the mask byte carries the unfloored children in its high
 // nibble; the gauge term -gm * (unfloored children)/8 is applied here and the nibble cleared.
 template <typename T, bool BG>
-__device__ __forceinline__ void fas_rhs_cell(const T* __restrict__ uc, const T* __restrict__ rc,
-                                             uint8_t* __restrict__ kmask, const T* __restrict__ bg, int n, int lg,
-                                             T ih2, T nu, T kap, T* __restrict__ fc, uint32_t* __restrict__ coefo,
-                                             float* __restrict__ gapo, float lsat, bool apply_gm, T gm, size_t total,
+__device__ __forceinline__ void fas_rhs_cell(const T* uc, const T* rc,
+                                             uint8_t* kmask, const T* bg, int n, int lg,
+                                             T ih2, T nu, T kap, T* fc, uint32_t* coefo,
+                                             float* gapo, float lsat, bool apply_gm, T gm, size_t total,
                                              size_t c)
 {
     const int i = (int)(c & (size_t)(n - 1));  // n is a power of two
@@ -380,8 +380,8 @@ __global__ void __launch_bounds__(256) k_fas_rhs_tile(const T* __restrict__ uc, 
 // separably (weights 3/4 and 1/4 per axis, i.e. 27/64, 9/64, 3/64, 1/64 in 3D), and the
 // children are updated as pairs along x (8-byte / 16-byte accesses).
 template <typename T>
-__device__ __forceinline__ void prolong_add_cell(const T* __restrict__ uc, const T* __restrict__ ur, int nc, int lgc,
-                                                 T* __restrict__ uf, size_t c)
+__device__ __forceinline__ void prolong_add_cell(const T* uc, const T* ur, int nc, int lgc,
+                                                 T* uf, size_t c)
 {
     const int nf = 2 * nc, mc = nc - 1;
     const T a = T(0.75), b = T(0.25);
@@ -501,8 +501,8 @@ struct CoarsestSmem {
 
 // The coarsest solve of one level (at most 8^3 cells) by the calling block, its arrays in sm.
 template <typename T, bool BG>
-__device__ void coarsest_block(T* __restrict__ u, const T* __restrict__ F, T fscale, const uint8_t* __restrict__ kmask,
-                               const T* __restrict__ bg, int n, double ih2_d, double nu_d, double kap_d, double eta,
+__device__ void coarsest_block(T* u, const T* F, T fscale, const uint8_t* kmask,
+                               const T* bg, int n, double ih2_d, double nu_d, double kap_d, double eta,
                                int sweeps, bool floor_piece, CoarsestSmem<T>& sm)
 {
     T* su = sm.su;

@@ -285,6 +285,7 @@ struct pm_unet {
     long long off[11] = {};  // parameter offsets of each conv and of the head
     pmeft::Acts acts;
     int adam_t = 0;
+    int conv_path = 0;  // 0 mma.sync, 1 tcgen05 convolutions (pm_unet_set_conv_path)
 };
 
 namespace pmeft {
@@ -511,6 +512,7 @@ static const float* bias_of(pm_unet* u, int i)
 static pm_status unet_forward(pm_unet* u, const double* delta, int n, double aB0, double aM0, double a)
 {
     pm_ctx* ctx = u->ctx;
+    ctx->conv_path = u->conv_path;  // the convolution launcher reads it from the context
     Acts& A = u->acts;
     const int n1 = n / 2, n2 = n / 4;
     const size_t v0 = (size_t)n * n * n;
@@ -725,7 +727,7 @@ extern "C" pm_status pm_unet_get_params(pm_unet* u, float* host, long long count
 extern "C" pm_status pm_unet_set_conv_path(pm_unet* u, int path)
 {
     if (!u || path < 0 || path > 1) return PM_ERR_INVALID_ARG;
-    u->ctx->conv_path = path;
+    u->conv_path = path;
     return PM_OK;
 }
 

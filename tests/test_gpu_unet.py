@@ -28,22 +28,29 @@ def case():
     return n, delta, target, p
 
 
-def test_forward_matches_reference(gpu_lib, case):
+@pytest.mark.parametrize("path", [0, 1])
+def test_forward_matches_reference(gpu_lib, case, path):
+    """path 0: mma.sync convolutions; path 1: tcgen05 convolutions (the 16^3 level; the
+    smaller levels keep path 0)."""
     n, delta, target, p = case
     net = gpu_lib.UNet()
+    net.set_conv_path(path)
     net.set_params(p)
     got = net.forward(cu(delta), -0.8, 0.4, 0.9).cpu().numpy()
     want, _ = U.forward(p, delta, -0.8, 0.4, 0.9)
     assert np.linalg.norm(got - want) / np.linalg.norm(want) < 3e-2  # BF16 activations and weights
 
 
-def test_forward_matches_reference_64(gpu_lib):
-    """At 64^3 every level takes the tiled convolution kernel (levels 64, 32, 16)."""
+@pytest.mark.parametrize("path", [0, 1])
+def test_forward_matches_reference_64(gpu_lib, path):
+    """At 64^3 every level takes the tiled convolution kernel (levels 64, 32, 16), with path 1
+    the tcgen05 kernel on every level."""
     n = 64
     delta = synth.lognormal_delta(n, -2.0, 1.2, 21)
     p = U.init_params(9)
     p[-1] = 0.1
     net = gpu_lib.UNet()
+    net.set_conv_path(path)
     net.set_params(p)
     got = net.forward(cu(delta), -1.2, 0.3, 0.7).cpu().numpy()
     want, _ = U.forward(p, delta, -1.2, 0.3, 0.7)
@@ -51,7 +58,8 @@ def test_forward_matches_reference_64(gpu_lib):
 
 
 @pytest.mark.slow
-def test_forward_at_512_matches_reference_on_a_crop(gpu_lib):
+@pytest.mark.parametrize("path", [0, 1])
+def test_forward_at_512_matches_reference_on_a_crop(gpu_lib, path):
     """The network applied at 512^3 (the size the warm start runs at; some of its
     activation tensors hold more than 2^31 values) against the reference evaluated on a
     64^3 crop: outputs farther from the crop's faces than the receptive field (about 23
@@ -64,6 +72,7 @@ def test_forward_at_512_matches_reference_on_a_crop(gpu_lib):
     p = U.init_params(4)
     p[-1] = 0.1
     net = gpu_lib.UNet()
+    net.set_conv_path(path)
     net.set_params(p)
     got = net.forward(delta, -1.0, 0.2, 0.9)[s0 + 28:s0 + 36, s0 + 28:s0 + 36, s0 + 28:s0 + 36].cpu().numpy()
     crop = delta[s0:s0 + w, s0:s0 + w, s0:s0 + w].cpu().numpy()
@@ -72,9 +81,11 @@ def test_forward_at_512_matches_reference_on_a_crop(gpu_lib):
     assert np.linalg.norm(got - want) / np.linalg.norm(want) < 3e-2
 
 
-def test_gradients_match_reference(gpu_lib, case):
+@pytest.mark.parametrize("path", [0, 1])
+def test_gradients_match_reference(gpu_lib, case, path):
     n, delta, target, p = case
     net = gpu_lib.UNet()
+    net.set_conv_path(path)
     net.set_params(p)
     net.zero_grad()
     loss = net.loss_grad(cu(delta), cu(target, torch.float32), -0.8, 0.4, 0.9)
@@ -87,6 +98,24 @@ def test_gradients_match_reference(gpu_lib, case):
         cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-300)
         assert cos > 0.99, (k, cos)
         assert np.linalg.norm(a - b) / np.linalg.norm(b) < 0.1, k
+
+
+def test_tensor_core_paths_agree_at_128(gpu_lib):
+    """The tcgen05 and the mma.sync convolutions on the same network and field (128^3, every
+    level on the tensor-core path): the same BF16 products with FP32 sums in another order, so
+    the outputs agree to the BF16 rounding of the activations."""
+    n = 128
+    delta = synth.lognormal_delta(n, -2.0, 1.5, 31)
+    p = U.init_params(6)
+    p[-1] = 0.1
+    out = []
+    for path in (0, 1):
+        net = gpu_lib.UNet()
+        net.set_conv_path(path)
+        net.set_params(p)
+        out.append(net.forward(cu(delta), -2.0, 0.5, 1.0).cpu().numpy())
+        net.close()
+    assert np.linalg.norm(out[1] - out[0]) / np.linalg.norm(out[0]) < 1e-2
 
 
 def test_target_and_linear_start(gpu_lib):
