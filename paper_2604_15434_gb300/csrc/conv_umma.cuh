@@ -100,7 +100,7 @@ constexpr size_t umma_smem(int cin)
 }
 
 // out[v][out_off + co0 + c] = act(sum_tap sum_ci in[v + tap][ci] W[tap][ci][co0 + c] + bias[co0 + c]),
-// c < NT, optionally times (mask[v][mask_off + co0 + c] > 0).  wt: the packed weights
+// c < NT, optionally times (mask[v][mask_off + co0 + c] > 0); bias may be null (no bias term).  wt: the packed weights
 // [tap][Cin/16][Cout][16] of the whole layer (Cout outputs).  err (nullable): set to 1 if an
 // mbarrier wait gave up (the tile's output is then not written).
 template <int NT>
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(kUmThreads) k_conv3d_umma(const __nv_bfloat16*
             __align__(16) __nv_bfloat16 o[16];
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
-                float y = d[q] + bias[co0 + c0 + q];
+                float y = bias ? d[q] + bias[co0 + c0 + q] : d[q];  // no bias in the backward-data convolution
                 if (relu) y = fmaxf(y, 0.f);
                 if (mask && !(__bfloat162float(mask[v * mask_ld + mask_off + co0 + c0 + q]) > 0.f)) y = 0.f;
                 o[q] = __float2bfloat16(y);
