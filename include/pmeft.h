@@ -247,7 +247,8 @@ pm_status pm_unet_create(pm_ctx* ctx, pm_unet** net);   /* parameters start at z
 void pm_unet_destroy(pm_unet* net);
 /* The convolution kernels of the network's forward and backward-data passes: 0 the
  * mma.sync (m16n8k16) implicit GEMM, 1 the tcgen05 implicit GEMM with its accumulator in
- * tensor memory (grids of at least 16^3; smaller ones keep path 0).  Default 0. */
+ * tensor memory (grids of at least 16^3; smaller ones keep path 0).  Default 1.  With path
+ * 1 a pass returns PM_ERR_TIMEOUT if a bounded accumulator wait of a convolution gave up. */
 pm_status pm_unet_set_conv_path(pm_unet* net, int path);
 /* host <-> device copies of the FP32 parameters (which = 0) or accumulated gradients (which = 1) */
 pm_status pm_unet_set_params(pm_unet* net, const float* host, long long count);

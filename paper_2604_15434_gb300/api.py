@@ -441,7 +441,7 @@ class UNet:
         self.num_params = int(load().pm_unet_num_params())
 
     def set_conv_path(self, path: int):
-        """0: mma.sync convolutions, 1: tcgen05 tensor-core convolutions (see pm_unet_set_conv_path)."""
+        """0: mma.sync convolutions, 1 (default): tcgen05 tensor-core convolutions (see pm_unet_set_conv_path)."""
         self.ctx._check(load().pm_unet_set_conv_path(self._h, int(path)))
 
     def set_params(self, p):

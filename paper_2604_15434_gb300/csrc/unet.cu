@@ -285,7 +285,7 @@ struct pm_unet {
     long long off[11] = {};  // parameter offsets of each conv and of the head
     pmeft::Acts acts;
     int adam_t = 0;
-    int conv_path = 0;  // 0 mma.sync, 1 tcgen05 convolutions (pm_unet_set_conv_path)
+    int conv_path = 1;  // 0 mma.sync, 1 tcgen05 convolutions (pm_unet_set_conv_path)
 };
 
 namespace pmeft {
@@ -366,7 +366,7 @@ static pm_status ensure_acts(pm_unet* u, int n, bool train)
 static int blocks_for(pm_ctx* ctx, size_t work) { return grid_for(ctx, work); }
 
 // The convolution on the tcgen05 tensor cores (conv_umma.cuh), in slices of NT output channels
-// whose resident weights fit next to the input patch in shared memory.  Returns false (nothing
+// whose resident weights fit next to the patch planes in shared memory.  Returns false (nothing
 // launched) where it does not apply.
 template <int NT>
 static void launch_umma(pm_ctx* ctx, const __nv_bfloat16* in, int in_ld, int in_off, int ci, const __nv_bfloat16* w,
@@ -376,13 +376,22 @@ static void launch_umma(pm_ctx* ctx, const __nv_bfloat16* in, int in_ld, int in_
     const size_t smem = umma_smem<NT>(ci);
     auto k = k_conv3d_umma<NT>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kUmThreads, smem);
-    constexpr int cols = NT <= 32 ? 32 : (NT <= 64 ? 64 : (NT <= 128 ? 128 : 256));
-    per_sm = std::max(1, std::min(per_sm, 512 / cols));  // the blocks of an SM share its 512 TMEM columns
-    const long long tiles = (long long)(n / kUmTX) * (n / kUmTY) * n;
-    const long long g = std::min<long long>(tiles, (long long)ctx->num_sms * per_sm);
-    k<<<(int)g, kUmThreads, smem, ctx->stream>>>(in, in_ld, in_off, ci, w, co, co0, bias, out, out_ld, out_off, n,
+    // blocks per SM from the kernel's own limits: shared memory (plus the 1 KB the system
+    // reserves per block), registers, threads, and the SM's 512 tensor-memory columns
+    int smem_sm = 0, regs_sm = 0;
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, ctx->device);
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, k);
+    constexpr int cols = 2 * um_acc_stride<NT>() < 32 ? 32 : 2 * (int)um_acc_stride<NT>();
+    int per_sm = std::min(smem_sm / (int)(smem + 1024), 2048 / kUmThreads);
+    if (fa.numRegs > 0) per_sm = std::min(per_sm, regs_sm / (fa.numRegs * kUmThreads));
+    per_sm = std::max(1, std::min(per_sm, 512 / cols));
+    // z planes per work item: n / 8 within [4, 64] (a divisor of n), enough items for every SM
+    const int zl = std::max(4, std::min(64, n / 8));
+    const long long items = (long long)(n / kUmTX) * (n / kUmTY) * (n / zl);
+    const long long g = std::min<long long>(items, (long long)ctx->num_sms * per_sm);
+    k<<<(int)g, kUmThreads, smem, ctx->stream>>>(in, in_ld, in_off, ci, w, co, co0, bias, out, out_ld, out_off, n, zl,
                                                   relu ? 1 : 0, mask, mask_ld, mask_off, ctx->flag + 2);
 }
 
@@ -391,7 +400,7 @@ static bool conv_umma(pm_ctx* ctx, const __nv_bfloat16* in, int in_ld, int in_of
                       const __nv_bfloat16* mask, int mask_ld, int mask_off)
 {
     if (ctx->conv_path != 1 || n < kUmTY || n % kUmTY != 0 || ci % 16 != 0 || co % 16 != 0) return false;
-    auto bytes = [&](int nt) { return (size_t)27 * (ci / 16) * nt * 32 + (size_t)(ci / 16) * kUmPV * 32 + 64; };
+    auto bytes = [&](int nt) { return (size_t)27 * (ci / 16) * nt * 32 + (size_t)kUmSlots * (ci / 16) * kUmPP * 32 + 64; };
     int nt = co;  // the widest slice whose weights fit
     while (bytes(nt) > (size_t)227 * 1024 && nt % 32 == 0) nt /= 2;
     if (bytes(nt) > (size_t)227 * 1024) return false;
@@ -509,6 +518,21 @@ static const float* bias_of(pm_unet* u, int i)
     return u->p + u->off[i] + 27LL * kConvs[i].ci * kConvs[i].co;
 }
 
+// After a pass with the tcgen05 convolutions: PM_ERR_TIMEOUT if an accumulator wait of
+// k_conv3d_umma gave up (its error word is cleared for the next pass), else PM_OK.
+static pm_status umma_status(pm_ctx* ctx)
+{
+    if (ctx->conv_path != 1) return PM_OK;
+    PM_CUDA(cudaMemcpyAsync(ctx->host_out + 62, ctx->flag + 2, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (*reinterpret_cast<int*>(ctx->host_out + 62) != 0) {
+        cudaMemsetAsync(ctx->flag + 2, 0, sizeof(int), ctx->stream);
+        ctx->set_error("tensor-core convolution: an accumulator wait gave up");
+        return PM_ERR_TIMEOUT;
+    }
+    return PM_OK;
+}
+
 static pm_status unet_forward(pm_unet* u, const double* delta, int n, double aB0, double aM0, double a)
 {
     pm_ctx* ctx = u->ctx;
@@ -545,17 +569,7 @@ static pm_status unet_forward(pm_unet* u, const double* delta, int n, double aB0
     k_head<<<blocks_for(ctx, v0), 256, 0, ctx->stream>>>(A.y9, u->p + u->off[10], (int)v0, A.that);
     ctx->end();
     PM_CUDA(cudaGetLastError());
-    if (ctx->conv_path == 1) {
-        // an mbarrier wait of the tensor-core convolution that gave up (conv_umma.cuh)
-        PM_CUDA(cudaMemcpyAsync(ctx->host_out + 62, ctx->flag + 2, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-        PM_CUDA(cudaStreamSynchronize(ctx->stream));
-        if (*reinterpret_cast<int*>(ctx->host_out + 62) != 0) {
-            cudaMemsetAsync(ctx->flag + 2, 0, sizeof(int), ctx->stream);
-            ctx->set_error("tensor-core convolution: an accumulator wait gave up");
-            return PM_ERR_TIMEOUT;
-        }
-    }
-    return PM_OK;
+    return umma_status(ctx);
 }
 
 // backward of the loss 1/V sum (T_hat - T)^2 into u->g (accumulated); returns the loss
@@ -630,7 +644,7 @@ static pm_status unet_backward(pm_unet* u, const float* target, int n, double* l
     // c0: x = input, dy = d0 (no input gradient)
     conv_wgrad(u, 0, A.in, 16, 0, A.d0, 16, 0, n);
     PM_CUDA(cudaGetLastError());
-    return PM_OK;
+    return umma_status(ctx);
 }
 
 static pm_status repack(pm_unet* u)
