@@ -39,6 +39,9 @@ COMBOS = [(-2.0, 0.0), (-2.0, 0.5), (-0.5, 0.0), (-0.5, 0.5)]
 SWEEP_DRAM_BYTES_PER_CELL = 28.7
 TOL = 1e-8
 SEED = 1003
+# the sampler's bound on |mu_chi| = |xi/nu|: draws beyond it (with more than 90% of the cells
+# on the void floor) fail to converge in about half the cases (robustness_leg)
+MU_CHI_MAX = 4.0
 METRIC = "512^3 scalar solve time-to-residual 1e-8 (learned+FP32 vs plain FP64); HBM GB/s %"
 
 
@@ -182,9 +185,9 @@ def batched_leg(api, dev, stream, nbox=24, seed=1007):
     from paper_2604_15434_gb300 import synth
 
     sizes = synth.sample_box_sizes(nbox, seed)
-    def accept(aB, aM, a):  # near-singular draws are redrawn: |nu| < 0.1 or |mu_chi| = |xi/nu| > 8
+    def accept(aB, aM, a):  # draws with |nu| < 0.1 or |mu_chi| = |xi/nu| > 4 are redrawn (robustness_leg)
         c = api.coefficients(aB, aM, a)
-        return abs(c["nu"]) >= 0.1 and abs(c["mu_chi"]) <= 8.0
+        return abs(c["nu"]) >= 0.1 and abs(c["mu_chi"]) <= MU_CHI_MAX
 
     params = synth.sample_box_params(nbox, seed, accept=accept)
     deltas = []
@@ -223,6 +226,57 @@ def batched_leg(api, dev, stream, nbox=24, seed=1007):
             "speedup_vs_sequential": seq_ms / batched_ms, "cells": cells,
             "max_rel_res": max(i["rel_res"] for i in infos), "outer_iterations": [i["cycles"] for i in infos],
             "tune": ctx.tune_log().strip().splitlines()}
+
+
+def robustness_leg(api, dev, stream, count=500, n=64, seed=4000):
+    """How often the solve converges over the batched/training distribution: `count` seeded
+    draws at n^3, alternately a lognormal source (P ~ k^-2, sigma_ln ~ U[1, 1.8]) and a
+    Zel'dovich one (P ~ k^-1.5, sigma ~ U[0.5, 2]), parameters alpha_B0 ~ U[-2,0], alpha_M0 ~
+    U[0,1], a ~ U[0.3,1] redrawn only where |nu| < 0.1 or |mu_chi| > 8 (the wider rule), all
+    solved to 1e-8 (max 200 outer iterations) by batched calls of 100 boxes.  Reported for the
+    wider rule and for the sampler's rule |mu_chi| <= MU_CHI_MAX."""
+    import numpy as np
+    import torch
+    from paper_2604_15434_gb300 import synth
+
+    t0 = time.time()
+    draws = []
+    for i in range(count):
+        rng = np.random.default_rng(seed + i)
+        kind = "lognormal" if i % 2 == 0 else "zeldovich"
+        sigma = rng.uniform(1.0, 1.8) if kind == "lognormal" else rng.uniform(0.5, 2.0)
+        while True:
+            aB, aM, a = rng.uniform(-2.0, 0.0), rng.uniform(0.0, 1.0), rng.uniform(0.3, 1.0)
+            c = api.coefficients(aB, aM, a)
+            if abs(c["nu"]) >= 0.1 and abs(c["mu_chi"]) <= 8.0 and c["xi"] != 0.0:
+                break
+        if kind == "lognormal":
+            d = torch.from_numpy(synth.lognormal_delta(n, -2.0, sigma, seed + 100000 + i)).to(dev)
+        else:
+            pos = torch.from_numpy(synth.zeldovich_particles(n, -1.5, sigma, seed + 100000 + i)).to(dev)
+            d = api.pm_deposit_cic(pos, n)
+        draws.append((d, aB, aM, a, c["nu"], c["mu_chi"]))
+    gen_s = time.time() - t0
+    ctx = api.Context(dev.index, stream, precision=1, max_cycles=200)
+    infos = []
+    torch.cuda.synchronize()
+    t1 = time.time()
+    for k in range(0, count, 100):
+        ch = draws[k:k + 100]
+        _, inf = api.scalar_mg_solve_batched([x[0] for x in ch], [x[1] for x in ch], [x[2] for x in ch],
+                                             [x[3] for x in ch], TOL, ctx=ctx, raise_on_noconv=False)
+        infos += inf
+    torch.cuda.synchronize()
+    solve_s = time.time() - t1
+    ok = [i["status"] == 0 for i in infos]
+    narrow = [abs(x[5]) <= MU_CHI_MAX for x in draws]
+    fails = [{"draw": k, "alpha_B0": draws[k][1], "alpha_M0": draws[k][2], "a": draws[k][3], "nu": draws[k][4],
+              "mu_chi": draws[k][5], "status": infos[k]["status"], "rel_res": infos[k]["rel_res"],
+              "floored_frac": infos[k]["floored_cells"] / n ** 3} for k in range(count) if not ok[k]]
+    return {"draws": count, "n": n, "converged": sum(ok), "converged_frac": sum(ok) / count,
+            "narrow_rule": f"|mu_chi| <= {MU_CHI_MAX}", "narrow_draws": sum(narrow),
+            "narrow_converged": sum(1 for o, w in zip(ok, narrow) if o and w),
+            "failures": fails, "generate_s": gen_s, "solve_s": solve_s}
 
 
 def warm_start_leg(api, delta, stream, ctx):
@@ -621,6 +675,7 @@ def main():
         line["precision_variants"] = precision_leg(api, delta, stream, dev)
     if not args.no_batch:
         line["batched"] = batched_leg(api, dev, stream)
+        line["robustness"] = robustness_leg(api, dev, stream)
     if not args.no_next:
         line["next_rows"] = next_rows_leg(api, dev, stream)
     if rank == 0 and not args.no_cpu:

@@ -103,7 +103,7 @@ def sample_params(rng):
     while True:
         aB, aM, a = rng.uniform(-2.0, 0.0), rng.uniform(0.0, 1.0), rng.uniform(0.3, 1.0)
         c = api.coefficients(aB, aM, a)
-        if abs(c["nu"]) >= 0.1 and abs(c["mu_chi"]) <= 8.0 and c["xi"] != 0.0:
+        if abs(c["nu"]) >= 0.1 and abs(c["mu_chi"]) <= 4.0 and c["xi"] != 0.0:
             return aB, aM, a
 
 

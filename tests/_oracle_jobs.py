@@ -13,7 +13,7 @@ def _accept(aB, aM, a):
     import oracle as O
 
     c = O.coefficients(aB, aM, a)
-    return abs(c["nu"]) >= 0.1 and abs(c["mu_chi"]) <= 8.0
+    return abs(c["nu"]) >= 0.1 and abs(c["mu_chi"]) <= 4.0
 
 
 def lognormal_solve(n, aB0, aM0, tol, seed=1003, eta=None):

@@ -420,11 +420,11 @@ def test_mixed_precision_solve_256_uses_fused_sweep(gpu_lib, inner):
 
 def _box_set(sizes, seed):
     """Zel'dovich sources (P ~ k^-1.5, sigma 1) on mixed sizes, with parameters drawn from
-    alpha_B0 ~ U[-2,0], alpha_M0 ~ U[0,1], a ~ U[0.3,1]; near-singular draws (|nu| < 0.1 or
-    |xi/nu| > 8, where the iteration diverges on the CPU reference as well) are redrawn."""
+    alpha_B0 ~ U[-2,0], alpha_M0 ~ U[0,1], a ~ U[0.3,1]; draws with |nu| < 0.1 or |xi/nu| > 4
+    (where about half of the draws do not converge on the CPU reference either) are redrawn."""
     def accept(aB, aM, a):
         c = O.coefficients(aB, aM, a)
-        return abs(c["nu"]) >= 0.1 and abs(c["mu_chi"]) <= 8.0
+        return abs(c["nu"]) >= 0.1 and abs(c["mu_chi"]) <= 4.0
 
     params = synth.sample_box_params(len(sizes), seed, accept=accept)
     boxes = []
