@@ -31,12 +31,16 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 COMBOS = [(-2.0, 0.0), (-2.0, 0.5), (-0.5, 0.0), (-0.5, 0.5)]
-# DRAM bytes per cell of one finest-level sweep launch, from an ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum of one 512^3 launch of the coefficient
-# variant with one warp per red unit, over its cells).  It exceeds the 20 algorithmic bytes
-# by design: the kernel reads 12 bytes of background coefficients in place of the 4-byte
-# background and its 19-point stencil.
-SWEEP_DRAM_BYTES_PER_CELL = 28.7
+# DRAM bytes per cell of one finest-level sweep launch of the variant the autotuner keeps at
+# 512^3 (k_sweep_pair<16, 1, 1, 1, 1>: tile 64 x 16, 32 planes per block, background through
+# its BF16 coefficients, one warp per red unit), from one ncu capture of a 256^3 launch of the
+# same variant (dram__bytes_read.sum + dram__bytes_write.sum = 431.1 + 58.5 MB over 16.78 M
+# cells; `python -m paper_2604_15434_gb300.microbench sweep --n 256 --mode 115`), scaled by the
+# cell count.  It is reported only when the autotuner's choice is that variant.
+SWEEP_DRAM = {"tile 64x16 nz 32 pair bal": 29.2}
+SWEEP_DRAM_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one 256^3 launch of "
+                     "k_sweep_pair<16,1,1,1,1> (microbench sweep --n 256 --mode 115): 29.2 B/cell, "
+                     "times this launch's cells")
 TOL = 1e-8
 SEED = 1003
 # the sampler's bound on |mu_chi| = |xi/nu|: draws beyond it (with more than 90% of the cells
@@ -420,22 +424,34 @@ def void_floor_leg(api, delta, stream, dev, phis):
     """The literal void floor (eta = 0: only cells with a negative discriminant are floored, at
     the parabola's vertex; Sec. 3.3) against the default eta on the nu > 0 pairs of the 512^3
     workload: cycles, time, floored fraction and the relative change of chi (phis holds the
-    timed steps' solutions at the default eta)."""
+    timed steps' solutions at the default eta).  The mixed-precision solve is tried first; where
+    it stops with an error (its FP32 inner cycle does not handle the vertex floor's zero
+    discriminant), the plain FP64 solve is run instead, capped at 40 cycles (it stalls, as on the
+    oracle)."""
     import torch
 
     cells = delta.numel()
-    c = api.Context(dev.index, stream, precision=1, max_cycles=100, eta=0.0)
     out = {}
     phi = torch.zeros_like(delta)
     for i, (aB, aM) in enumerate(COMBOS):
         if api.coefficients(aB, aM, 1.0)["nu"] <= 0.0:
             continue
-        phi.zero_()
-        _, info = api.scalar_mg_solve(delta, aB, aM, 1.0, TOL, phi=phi, ctx=c, raise_on_noconv=False)
-        out[f"{aB},{aM}"] = {"ms": info["ms_total"], "cycles": info["cycles"], "rel_res": info["rel_res"],
-                             "status": info["status"], "floored_frac": info["floored_cells"] / cells,
-                             "rel_change_chi_vs_default_eta": float((phi - phis[i]).norm() / phis[i].norm())}
-    c.close()
+        row = {}
+        for prec, cap in ((1, 100), (0, 40)):
+            c = api.Context(dev.index, stream, precision=prec, max_cycles=cap, eta=0.0)
+            phi.zero_()
+            key = "mixed" if prec == 1 else "fp64"
+            try:
+                _, info = api.scalar_mg_solve(delta, aB, aM, 1.0, TOL, phi=phi, ctx=c, raise_on_noconv=False)
+                row[key] = {"ms": info["ms_total"], "cycles": info["cycles"], "rel_res": info["rel_res"],
+                            "status": info["status"], "floored_frac": info["floored_cells"] / cells,
+                            "rel_change_chi_vs_default_eta": float((phi - phis[i]).norm() / phis[i].norm())}
+            except api.PMError as e:
+                row[key] = {"status": e.status, "error": str(e)}
+            c.close()
+            if row[key].get("status") == 0:
+                break
+        out[f"{aB},{aM}"] = row
     return {"eta": 0.0, "per_pair": out}
 
 
@@ -597,19 +613,24 @@ def main():
     fine = prof["sweep32"]
     if fine["fine_launches"] > 0 and fine["fine_ms"] > 0:
         avg_ms = fine["fine_ms"] / fine["fine_launches"]
-        # algorithmic bytes of one finest-level launch of the single-pass FP32 sweep of the
-        # correction e (both colours): read e, the background, the right-hand side and the
-        # floored gap once (4 x 4 B), write e once (4 B): 20 B per cell
-        bytes_launch = cells * 20
+        # algorithmic bytes of one finest-level launch of the single-pass FP32 sweep (both
+        # colours): read the iterate and the right-hand side, write the iterate, 12 B per cell
+        # (the ideal FP32 sweep's figure).  The correction form also reads the background and
+        # the floored gap: 20 B per cell on that count (frac_20B).
+        bytes_launch = cells * 12
         ach = bytes_launch / (avg_ms * 1e-3) / 1e9
         tuned = [l for l in ctx.tune_log().splitlines() if f"n={n} bg gap" in l]
-        roof = {"kernel": "single-pass FP32 red-black sweep of the finest level (k_sweep_pair / k_sweep_fused, "
-                          "autotuned: " + (tuned[-1].split(": ", 1)[1].split(" (variants")[0] if tuned else "?") + ")", "bound": "hbm",
-                "achieved": ach, "peak": hbm,
-                "unit": "GB/s", "frac": ach / hbm, "traffic": SWEEP_DRAM_BYTES_PER_CELL * cells,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 512^3 launch of this kernel",
+        variant = tuned[-1].split(": ", 1)[1].split(" (variants")[0] if tuned else "?"
+        per_cell = next((v for k, v in SWEEP_DRAM.items() if variant.startswith(k)), None)
+        roof = {"kernel": "single-pass FP32 red-black sweep of the finest level (k_sweep_pair / k_sweep_col / "
+                          "k_sweep_fused, autotuned: " + variant + ")", "bound": "hbm",
+                "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": per_cell * cells if per_cell else None,
+                "traffic_source": SWEEP_DRAM_SOURCE if per_cell else "no capture of this variant",
                 "peak_source": src, "frac_of_nominal_8000": ach / 8000.0,
-                "bytes_per_launch": bytes_launch, "avg_launch_ms": avg_ms, "launches": fine["fine_launches"]}
+                "bytes_per_launch": bytes_launch, "bytes_per_cell": 12,
+                "frac_20B": cells * 20 / (avg_ms * 1e-3) / 1e9 / hbm,
+                "avg_launch_ms": avg_ms, "launches": fine["fine_launches"]}
     r64 = prof_all["resid64"]
     resid64 = None
     if r64["fine_launches"] > 0 and r64["fine_ms"] > 0:

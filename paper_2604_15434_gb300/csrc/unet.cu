@@ -368,13 +368,13 @@ static int blocks_for(pm_ctx* ctx, size_t work) { return grid_for(ctx, work); }
 // The convolution on the tcgen05 tensor cores (conv_umma.cuh), in slices of NT output channels
 // whose resident weights fit next to the patch planes in shared memory.  Returns false (nothing
 // launched) where it does not apply.
-template <int NT>
+template <int NT, int SLOTS>
 static void launch_umma(pm_ctx* ctx, const __nv_bfloat16* in, int in_ld, int in_off, int ci, const __nv_bfloat16* w,
                         int co, int co0, const float* bias, __nv_bfloat16* out, int out_ld, int out_off, int n, bool relu,
                         const __nv_bfloat16* mask, int mask_ld, int mask_off)
 {
-    const size_t smem = umma_smem<NT>(ci);
-    auto k = k_conv3d_umma<NT>;
+    const size_t smem = umma_smem<NT, SLOTS>(ci);
+    auto k = k_conv3d_umma<NT, SLOTS>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     // blocks per SM from the kernel's own limits: shared memory (plus the 1 KB the system
     // reserves per block), registers, threads, and the SM's 512 tensor-memory columns
@@ -383,7 +383,7 @@ static void launch_umma(pm_ctx* ctx, const __nv_bfloat16* in, int in_ld, int in_
     cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, ctx->device);
     cudaFuncAttributes fa{};
     cudaFuncGetAttributes(&fa, k);
-    constexpr int cols = 2 * um_acc_stride<NT>() < 32 ? 32 : 2 * (int)um_acc_stride<NT>();
+    constexpr int cols = (int)um_cols<NT>();
     int per_sm = std::min(smem_sm / (int)(smem + 1024), 2048 / kUmThreads);
     if (fa.numRegs > 0) per_sm = std::min(per_sm, regs_sm / (fa.numRegs * kUmThreads));
     per_sm = std::max(1, std::min(per_sm, 512 / cols));
@@ -395,22 +395,38 @@ static void launch_umma(pm_ctx* ctx, const __nv_bfloat16* in, int in_ld, int in_
                                                   relu ? 1 : 0, mask, mask_ld, mask_off, ctx->flag + 2);
 }
 
+// three plane slots (two planes loading ahead) where the block still fits twice per SM, else two
+template <int NT>
+static void launch_umma_slots(pm_ctx* ctx, const __nv_bfloat16* in, int in_ld, int in_off, int ci,
+                              const __nv_bfloat16* w, int co, int co0, const float* bias, __nv_bfloat16* out,
+                              int out_ld, int out_off, int n, bool relu, const __nv_bfloat16* mask, int mask_ld,
+                              int mask_off)
+{
+    if (umma_smem<NT, 3>(ci) <= (size_t)112 * 1024)
+        launch_umma<NT, 3>(ctx, in, in_ld, in_off, ci, w, co, co0, bias, out, out_ld, out_off, n, relu, mask, mask_ld,
+                           mask_off);
+    else
+        launch_umma<NT, 2>(ctx, in, in_ld, in_off, ci, w, co, co0, bias, out, out_ld, out_off, n, relu, mask, mask_ld,
+                           mask_off);
+}
+
 static bool conv_umma(pm_ctx* ctx, const __nv_bfloat16* in, int in_ld, int in_off, int ci, const __nv_bfloat16* w,
                       int co, const float* bias, __nv_bfloat16* out, int out_ld, int out_off, int n, bool relu,
                       const __nv_bfloat16* mask, int mask_ld, int mask_off)
 {
     if (ctx->conv_path != 1 || n < kUmTY || n % kUmTY != 0 || ci % 16 != 0 || co % 16 != 0) return false;
-    auto bytes = [&](int nt) { return (size_t)27 * (ci / 16) * nt * 32 + (size_t)kUmSlots * (ci / 16) * kUmPP * 32 + 64; };
-    int nt = co;  // the widest slice whose weights fit
-    while (bytes(nt) > (size_t)227 * 1024 && nt % 32 == 0) nt /= 2;
-    if (bytes(nt) > (size_t)227 * 1024) return false;
+    auto bytes = [&](int nt) {  // umma_smem<nt, 2>(ci)
+        return (size_t)9 * (ci / 16) * 2 * kUmWGroups * nt * 16 + (size_t)2 * (ci / 16) * kUmPP * 32 + 32 + (size_t)nt * 4;
+    };
+    int nt = co;  // the widest slice (at most 64 outputs) whose weights fit
+    while ((nt > 64 || bytes(nt) > (size_t)227 * 1024) && nt % 32 == 0) nt /= 2;
+    if (nt > 64 || bytes(nt) > (size_t)227 * 1024) return false;
     for (int co0 = 0; co0 < co; co0 += nt) {
         switch (nt) {
-            case 16: launch_umma<16>(ctx, in, in_ld, in_off, ci, w, co, co0, bias, out, out_ld, out_off, n, relu, mask, mask_ld, mask_off); break;
-            case 32: launch_umma<32>(ctx, in, in_ld, in_off, ci, w, co, co0, bias, out, out_ld, out_off, n, relu, mask, mask_ld, mask_off); break;
-            case 48: launch_umma<48>(ctx, in, in_ld, in_off, ci, w, co, co0, bias, out, out_ld, out_off, n, relu, mask, mask_ld, mask_off); break;
-            case 64: launch_umma<64>(ctx, in, in_ld, in_off, ci, w, co, co0, bias, out, out_ld, out_off, n, relu, mask, mask_ld, mask_off); break;
-            case 96: launch_umma<96>(ctx, in, in_ld, in_off, ci, w, co, co0, bias, out, out_ld, out_off, n, relu, mask, mask_ld, mask_off); break;
+            case 16: launch_umma_slots<16>(ctx, in, in_ld, in_off, ci, w, co, co0, bias, out, out_ld, out_off, n, relu, mask, mask_ld, mask_off); break;
+            case 32: launch_umma_slots<32>(ctx, in, in_ld, in_off, ci, w, co, co0, bias, out, out_ld, out_off, n, relu, mask, mask_ld, mask_off); break;
+            case 48: launch_umma_slots<48>(ctx, in, in_ld, in_off, ci, w, co, co0, bias, out, out_ld, out_off, n, relu, mask, mask_ld, mask_off); break;
+            case 64: launch_umma_slots<64>(ctx, in, in_ld, in_off, ci, w, co, co0, bias, out, out_ld, out_off, n, relu, mask, mask_ld, mask_off); break;
             default: return false;
         }
     }

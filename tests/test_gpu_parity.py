@@ -236,6 +236,22 @@ def test_fp64_solve_with_exact_coarsest_matches_oracle(gpu_lib, aB0, aM0):
     assert abs(info["cycles"] - info_o["cycles"]) <= 1
 
 
+@pytest.mark.parametrize("n", [32, 128])
+def test_literal_void_floor_fp64_solve_matches_oracle(gpu_lib, n):
+    """The literal floor (eta = 0: only cells with a negative discriminant floored, at the
+    vertex; Sec. 3.3) on the nu > 0 pair (-0.5, 0.5) of the benchmark recipe, where the oracle
+    converges at every eta: the GPU's FP64 cycle reaches the oracle's chi to 1e-9 in the same
+    number of cycles give or take one."""
+    d = synth.lognormal_delta(n, -2.0, 1.5, 1003)
+    want, info_o, st = O.scalar_solve(d, -0.5, 0.5, 1.0, 1e-10, eta=0.0, max_cycles=60)
+    assert st == 0
+    ctx = gpu_lib.Context(precision=0, max_cycles=60, eta=0.0)
+    got, info = gpu_lib.scalar_mg_solve(cu(d), -0.5, 0.5, 1.0, 1e-10, ctx=ctx)
+    assert info["rel_res"] <= 1e-10
+    assert rel(got.cpu().numpy(), want) < 1e-9
+    assert abs(info["cycles"] - info_o["cycles"]) <= 1
+
+
 @pytest.mark.parametrize("precision", [1, 2])
 @pytest.mark.parametrize("aB0,aM0", [(-0.5, 0.0), (-2.0, 0.5)])
 def test_mixed_solves_with_exact_coarsest_and_fp64_outer_loop(gpu_lib, precision, aB0, aM0):
