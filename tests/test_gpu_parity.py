@@ -516,6 +516,38 @@ def test_persistent_kernel_barrier_timeout_is_reported(gpu_lib):
         assert rel(phi.cpu().numpy(), want) < 1e-6
 
 
+def test_sampler_draws_converge_batched(gpu_lib):
+    """200 seeded draws of the batched/training distribution at 32^3 (alternately lognormal,
+    P ~ k^-2, sigma_ln ~ U[1, 1.8], and Zel'dovich, P ~ k^-1.5, sigma ~ U[0.5, 2]) under the
+    sampler's rule |nu| >= 0.1, |xi/nu| <= 4: every one converges to 1e-8 in batched calls of
+    50 boxes, and a sample of them matches the oracle's chi to 1e-6."""
+    rng = np.random.default_rng(515)
+    boxes = []
+    while len(boxes) < 200:
+        i = len(boxes)
+        aB, aM, a = rng.uniform(-2.0, 0.0), rng.uniform(0.0, 1.0), rng.uniform(0.3, 1.0)
+        c = O.coefficients(aB, aM, a)
+        if not (abs(c["nu"]) >= 0.1 and abs(c["mu_chi"]) <= 4.0 and c["xi"] != 0.0):
+            continue
+        if i % 2 == 0:
+            d = synth.lognormal_delta(32, -2.0, rng.uniform(1.0, 1.8), 9000 + i)
+        else:
+            pos = synth.zeldovich_particles(32, -1.5, rng.uniform(0.5, 2.0), 9000 + i)
+            d = O.density(O.deposit_cic(pos, 32), pos.shape[1])
+        boxes.append((d, aB, aM, a))
+    ctx = gpu_lib.Context(max_cycles=200)
+    for k in range(0, 200, 50):
+        ch = boxes[k:k + 50]
+        phis, infos = gpu_lib.scalar_mg_solve_batched([cu(b[0]) for b in ch], [b[1] for b in ch],
+                                                      [b[2] for b in ch], [b[3] for b in ch], 1e-8, ctx=ctx)
+        assert all(i["status"] == 0 and i["rel_res"] <= 1e-8 for i in infos)
+        for j in (0, 17, 33):
+            d, aB, aM, a = ch[j]
+            want, _, st = O.scalar_solve(d, aB, aM, a, 1e-11)
+            assert st == 0
+            assert rel(phis[j].cpu().numpy(), want) < 1e-6
+
+
 def test_nonconvergent_parameters_report_an_error(gpu_lib):
     """A near-singular draw (nu = 0.114, xi/nu = -18.6) has no convergent iteration on the CPU
     reference either (it stalls near 4e-2); the GPU solve must stop with an error status

@@ -157,9 +157,10 @@ WEIGHTS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__)
 def test_trained_warm_start(gpu_lib):
     """On held-out fields (seeds outside the training range) the learned initial guess has a
     smaller residual than chi = 0 and than the paper's linear start, and the solve from it
-    converges to the same chi as the cold start.  (Outer-iteration counts from the three
-    starts are a performance figure, measured by the benchmark, not asserted here: a
-    smaller first residual does not always mean fewer iterations of the nonlinear loop.)"""
+    converges to the same chi as the cold start.  At 128^3, the resolution the network was
+    trained at, the learned start also takes fewer outer iterations in total over the four
+    fields than the cold start.  (At 256^3 and 512^3 this does not hold for the nu < 0 pairs:
+    their iteration counts are a performance figure measured by the benchmark.)"""
     from paper_2604_15434_gb300 import learned
 
     ctx = gpu_lib.Context(precision=1, max_cycles=100)
@@ -167,6 +168,7 @@ def test_trained_warm_start(gpu_lib):
     net.set_params(learned.load_params(WEIGHTS))
     gen = torch.Generator(device="cuda")
     gen.manual_seed(77777)
+    cycles_cold = cycles_warm = 0
     for kind, aB, aM, a in (("lognormal", -0.5, 0.0, 1.0), ("lognormal", -2.0, 0.0, 1.0),
                             ("zeldovich", -1.0, 0.2, 1.0), ("zeldovich", -0.8, 0.6, 0.7)):
         d = learned.gpu_field(128, kind, 1.5, gen, torch.device("cuda"), ctx)
@@ -180,3 +182,6 @@ def test_trained_warm_start(gpu_lib):
         assert warm["guess_rel_res"] < lin["guess_rel_res"]
         err = (chi_warm - chi_cold).norm() / chi_cold.norm()
         assert err < 1e-6, (kind, aB, aM, a, float(err))
+        cycles_cold += cold["cycles"]
+        cycles_warm += warm["cycles"]
+    assert cycles_warm < cycles_cold, (cycles_warm, cycles_cold)
