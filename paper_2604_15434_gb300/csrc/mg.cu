@@ -133,10 +133,12 @@ __device__ __forceinline__ void residual_cell(const T* u, const T* F, T fscale, 
     const T kc = kap * w;
     const T lsat = kc != T(0) ? lsat_c / w : T(0);
     Local<T> o = local_eval<T, BG>(s, b, ih2, nu, kc, fscale * F[c] + lam, lsat, gap != nullptr, gap ? gap[c] : T(0));
-    // the floored piece exists on the finest level only; coarse levels take their
-    // pieces from the restricted mask (linear where masked, quadratic elsewhere), so
-    // their right-hand side and their smoother solve the same equation (FAS consistency)
-    const bool fl = floor_piece && (o.P != T(0)) && (o.D < Df);
+    // the floored piece exists on the finest level; coarse levels take their pieces from
+    // the restricted mask (linear where masked, quadratic elsewhere), so their right-hand
+    // side and their smoother solve the same equation (FAS consistency), except where a
+    // coarse cell's quadratic has no real root (D < 0): the smoother's safeguard puts such a
+    // cell at the floored update, and its residual is the floored piece as well
+    const bool fl = (o.P != T(0)) && (o.D < (floor_piece ? Df : T(0)));
     // floored piece nu (L_sat - L) = nu g
     const T rv = fl ? nu * o.g : -o.G;
     if (WRITE_R) r[c] = rv;
@@ -551,7 +553,7 @@ __device__ void coarsest_block(T* u, const T* F, T fscale, const uint8_t* kmask,
             const T w = sk[c] >= 8 ? T(0) : (T)(8 - sk[c]) * T(0.125);
             const T kc = kap * w;
             Local<T> o = local_eval<T, BG>(s, b, ih2, nu, kc, sf[c] + lam, kc != T(0) ? lsat_c / w : T(0));
-            const bool fl = floor_piece && (o.P != T(0)) && (o.D < Df);
+            const bool fl = (o.P != T(0)) && (o.D < (floor_piece ? Df : T(0)));
             a0 += fl ? nu * o.g : -o.G;
             a1 += fl ? T(0) : T(1);
         }

@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(256) k_residual_zm(const float* __restrict__ u
             const float oG = h ? o2.G.y : o2.G.x, oP = h ? o2.P.y : o2.P.x, oD = h ? o2.D.y : o2.D.x,
                         og = h ? o2.g.y : o2.g.x;
             // the floored piece exists on the finest level only (see k_residual)
-            const bool fl = floor_piece && (oP != 0.f) && (oD < Df);
+            const bool fl = (oP != 0.f) && (oD < (floor_piece ? Df : 0.f));
             const float rv = fl ? nu * og : -oG;
             if (RESTRICT) {
                 const int kf = kmask ? (kmask[os + gxy[h]] < 8 ? kmask[os + gxy[h]] : 8) : 0;

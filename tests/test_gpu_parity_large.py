@@ -52,6 +52,7 @@ def refs():
     jobs["boxes"] = pool.apply_async(J.box_set, (BOX_SIZES, BOX_SEED, ORACLE_TOL))
     for aB, aM in ((-2.0, 0.0), (-0.5, 0.5)):
         jobs[("logn", 128, aB, aM)] = pool.apply_async(J.lognormal_solve, (128, aB, aM, ORACLE_TOL))
+    jobs["literal"] = pool.apply_async(J.lognormal_solve, (256, -0.5, 0.5, ORACLE_TOL, 1003, 0.0))
     pool.close()
     assert here  # the workers import _oracle_jobs from this directory (on sys.path)
     yield {k: v for k, v in jobs.items()}
@@ -151,3 +152,19 @@ def test_learned_start_128_matches_oracle_chi(gpu_lib, refs, aB0, aM0):
     ref = _get(refs, ("logn", 128, aB0, aM0))
     assert info["rel_res"] <= 1e-8 and not info["guess_rejected"]
     assert rel(got.cpu().numpy(), ref["chi"]) < 1e-6
+
+
+def test_literal_void_floor_256_matches_oracle(gpu_lib, refs, delta_256):
+    """The literal floor (eta = 0) on the nu > 0 pair (-0.5, 0.5) at 256^3, where coarse levels
+    meet cells whose quadratic has no real root: the FP64 cycle follows the oracle's cycle count
+    (give or take one) to its chi within 1e-9, and the mixed-precision path reaches 1e-8 with chi
+    within 1e-6."""
+    want = _get(refs, "literal")
+    assert want["status"] == 0
+    for precision, tol, bound in ((0, ORACLE_TOL, 1e-9), (1, 1e-8, 1e-6)):
+        ctx = gpu_lib.Context(precision=precision, max_cycles=60, eta=0.0)
+        got, info = gpu_lib.scalar_mg_solve(cu(delta_256), -0.5, 0.5, 1.0, tol, ctx=ctx)
+        assert info["rel_res"] <= tol
+        assert rel(got.cpu().numpy(), want["chi"]) < bound, precision
+        if precision == 0:
+            assert abs(info["cycles"] - want["cycles"]) <= 1
