@@ -932,7 +932,8 @@ static const FusedCfg kFusedCfgs[] = {
     {64, 8, 64, true, false, false},   {64, 16, 32, true, false, false}, {64, 16, 64, true, false, false},
     {64, 4, 64, true, false, false},   {64, 8, 16, true, false, false},  {64, 16, 32, true, true, false},
     {64, 8, 32, true, true, false},    {64, 8, 32, false, false, true},  {64, 8, 64, false, false, true},
-    {64, 16, 32, false, false, true},  {64, 16, 64, false, false, true}};
+    {64, 16, 32, false, false, true},  {64, 16, 64, false, false, true},  {64, 16, 16, true, true, false},
+    {64, 8, 16, true, true, false}};
 constexpr int kNumFusedCfgs = sizeof(kFusedCfgs) / sizeof(kFusedCfgs[0]);
 
 template <int TX, int TY, bool BG, bool GAP>

@@ -396,11 +396,13 @@ PAIR_COEF_MODE = 100 + 9  # pair kernel, tile 64 x 8, 32 planes, background thro
 
 
 @pytest.mark.parametrize("n", [64, 128, 256])
-@pytest.mark.parametrize("mode", [17, 18, 19, 20])
+@pytest.mark.parametrize("mode", [15, 16, 17, 18, 19, 20, 21, 22])
 def test_column_sweep_equals_pair_coefficient_sweep(gpu_lib, n, mode):
-    """The column-resident sweep (k_sweep_col, tiles 64 x 8 / 64 x 16, 32 / 64 planes per block)
-    against the pair kernel on the same BF16 background coefficients and gap: the same formulas
-    in FP32 up to rounding order, on grids that give one and several blocks in every direction."""
+    """The coefficient-level variants (the balanced pair kernel with 32 or 16 planes per block,
+    modes 15, 16, 21, 22; the column-resident k_sweep_col, tiles 64 x 8 / 64 x 16, 32 / 64 planes
+    per block, modes 17-20) against the pair kernel on the same BF16 background coefficients and
+    gap: the same formulas in FP32 up to rounding order, on grids that give one and several
+    blocks in every direction."""
     u, f, c = _sweep_inputs(n, 700 + n, 0.5)
     rng = np.random.default_rng(n + mode)
     bg = cu(2.0 * rng.standard_normal((n, n, n)) / n ** 2, torch.float32)
