@@ -519,8 +519,8 @@ __device__ __forceinline__ T local_update(const Local<T>& o, T sp, T Df, T ih2)
 
 // FP32 variant for the inner cycle of the defect-correction loop: the same branches with
 // the approximate hardware reciprocal and square root (relative error ~1e-7), and the
-// constant divisions folded into multiplications.  The FP64 outer residual is the judge
-// of accuracy, so the inner update only has to be a good correction.
+// constant divisions folded into multiplications.  The outer residual decides the accuracy
+// of the result, so the inner update only has to be a good correction.
 __device__ __forceinline__ float local_update_fast(const Local<float>& o, float sp, float Df, float h2over6,
                                                    float inv2P)
 {

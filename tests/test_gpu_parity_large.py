@@ -4,7 +4,7 @@ At 256^3 the mixed-precision solve uses the kernels that smaller grids never rea
 float-float z-marching outer residual (n >= 64), the FP32 residual that restricts in its
 own pass (n >= 128) and the single-pass pair sweep with BF16 background coefficients
 (n >= 256).  Here their results are compared element by element with the FP64 oracle,
-driven to relative residual 1e-10 on the same seeded inputs, at the north-star
+driven to relative residual 1e-10 on the same seeded inputs, at the target
 tolerances: chi within 1e-6 relative L2, accelerations within 1e-5 of the largest one.
 The oracle references are computed at the start of the module in spawned worker processes
 (single-threaded FP64 solves of a few minutes each at 256^3), concurrently.
