@@ -321,8 +321,32 @@ def warm_start_leg(api, delta, stream, ctx):
                          "rel_res": info["rel_res"], "status": info["status"]}
         out[f"{aB},{aM}"] = row
     mean = {k: sum(r[k]["total_ms"] for r in out.values()) / len(out) for k in ("cold", "linear", "learned")}
+    # the network's forward alone (its tensor-core convolutions and the pooling, upsampling and
+    # head kernels): 2 x 27 x sum(Cin Cout per voxel of each level) flop per voxel of the grid
+    reps = 3
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        net.forward(delta, *COMBOS[0], 1.0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / reps
+    n = delta.shape[0]
+    macs = 27 * (16 * 16 + 16 * 16 + 48 * 16 + 16 * 16 + (16 * 32 + 32 * 32 + 96 * 32 + 32 * 32) / 8.0 +
+                 (32 * 64 + 64 * 64) / 64.0)
+    flop = 2.0 * macs * n ** 3
+    bf16 = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16 = json.load(f).get("bf16_tflops")
+    except Exception:
+        pass
+    tflops = flop / (fwd_ms * 1e-3) / 1e12
     net.close()
     return {"per_pair": out, "mean_total_ms": mean,
+            "unet_forward": {"ms": fwd_ms, "tflop": flop / 1e12, "tflops": tflops,
+                             "frac_of_bf16_peak": tflops / bf16 if bf16 else None,
+                             "conv_path": "tcgen05 (k_conv3d_umma)"},
             "note": "total_ms = initial guess + solve; guess_rel_res = relative residual of the guess"}
 
 
@@ -377,6 +401,25 @@ def next_rows_leg(api, dev, stream):
     psi = api.poisson_solve(torch.from_numpy(synth.lognormal_delta(n, -2.0, 1.5, SEED)).to(dev), 1.0, 0.2, ctx=cr)
     ms, _ = timed(lambda: api.lensing_potential(psi, phi, -1.0, 0.2, 1.0, ctx=cr), 5)
     out["lensing_potential"] = {"ms": ms, "gbs": 3 * 8 * n ** 3 / (ms * 1e-3) / 1e9}
+    # the PM step's own kernels on their own, with their algorithmic bytes: the deposit reads
+    # the positions (24 B per particle) and adds 8 int64 weights per particle in L2, clears the
+    # int64 grid and converts it to delta (24 B per cell); the Poisson solve is two FP64 cuFFT
+    # passes and the Green's function (timed, no byte model); the force kernel reads the two
+    # potentials' 5-point stencils at the 8 CIC corners (2 x 8 B per cell from DRAM, the rest
+    # from L2) and the positions, and writes the accelerations (24 + 24 B per particle)
+    hbm, _ = _peaks()
+    cp = api.Context(dev.index, stream, precision=1)
+    ms, dlt = timed(lambda: api.pm_deposit_cic(pos0, n, ctx=cp), 5)
+    byt = 24 * n ** 3 + 24 * n ** 3
+    out["deposit"] = {"ms": ms, "particles_per_s": n ** 3 / (ms * 1e-3), "gbs": byt / (ms * 1e-3) / 1e9,
+                      "frac_of_hbm": byt / (ms * 1e-3) / 1e9 / hbm, "bound": "L2 atomics"}
+    ms, psn = timed(lambda: api.poisson_solve(dlt, 1.0, 0.2, ctx=cp), 5)
+    out["poisson_fft"] = {"ms": ms}
+    acc = torch.empty_like(pos0)
+    ms, _ = timed(lambda: api.force_interp(psn, phi, -1.0, 0.2, 1.0, pos0, acc=acc, ctx=cp), 5)
+    byt = 16 * n ** 3 + 48 * n ** 3
+    out["force_interp"] = {"ms": ms, "particles_per_s": n ** 3 / (ms * 1e-3), "gbs": byt / (ms * 1e-3) / 1e9,
+                           "frac_of_hbm": byt / (ms * 1e-3) / 1e9 / hbm}
     m2 = {}
     d128 = torch.from_numpy(synth.lognormal_delta(128, -2.0, 1.5, SEED)).to(dev)
     p128 = torch.zeros_like(d128)
