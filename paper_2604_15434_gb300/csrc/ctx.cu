@@ -170,6 +170,7 @@ void delete_workspace(Workspace* w)
     cudaFree(w->rplain);
     cudaFree(w->ff_alt);
     cudaFree(w->coef_test);
+    cudaFree(w->grad);
     cudaFree(w->psi);
     cudaFree(w->delta);
     cudaFree(w->acc);

@@ -159,6 +159,7 @@ struct Workspace {
                                    // iterate out of place)
     uint32_t* coef_test = nullptr; // coefficients of a caller's background (pm_mg_sweep_f32, mode > 100)
     double* psi = nullptr;         // scratch n^3 (Poisson output / total potential)
+    double* grad = nullptr;        // scratch 4 n^3: total potential and its gradient (force kernels)
     double* delta = nullptr;       // scratch n^3 (pm_step)
     long long* acc = nullptr;      // int64 fixed-point deposit grid
     cufftHandle plan_r2c = 0, plan_c2r = 0;

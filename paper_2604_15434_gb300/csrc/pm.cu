@@ -120,46 +120,66 @@ __global__ void k_f2d(const float* __restrict__ x, size_t total, double* __restr
         y[c] = (double)x[c];
 }
 
-// g = -grad(psiN + xi chi) at each particle: for every one of the 8 CIC corners (in the
-// deposit's corner order) the five-point difference (-f+2 + 8 f+1 - 8 f-1 + f-2)/(12 h) per
-// axis (FOUR; else the two-point (f+1 - f-1)/(2 h)), weighted by the corner's CIC weight.
-// No force grid is written.
+// Psi = psiN + xi chi on the grid (psiN alone when chi is null), rounded as written.
+__global__ void k_psi_total(const double* __restrict__ psiN, const double* __restrict__ chi, double xi,
+                            size_t total, double* __restrict__ psi)
+{
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x)
+        psi[c] = chi ? __dadd_rn(psiN[c], __dmul_rn(xi, chi[c])) : psiN[c];
+}
+
+// g = -grad Psi on the grid, one cell per thread: the five-point difference
+// (-f+2 + 8 f+1 - 8 f-1 + f-2)/(12 h) per axis (FOUR; else the two-point (f+1 - f-1)/(2 h)),
+// periodic.  g holds the three components one after the other ([3][n^3]).
 template <bool FOUR>
-__global__ void __launch_bounds__(256) k_force(const double* __restrict__ psiN, const double* __restrict__ chi,
-                                               double xi, int n, const double* __restrict__ pos, long long np,
-                                               double* __restrict__ acc)
+__global__ void __launch_bounds__(256) k_grad(const double* __restrict__ psi, int n, double* __restrict__ g)
 {
     const int m = n - 1;
+    const size_t total = (size_t)n * n * n;
     const double inv12h = (double)n / 12.0, inv2h = (double)n * 0.5;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(c & (size_t)m);  // n is a power of two
+        const int j = (int)((c / n) & (size_t)m), k = (int)(c / ((size_t)n * n));
+        auto at = [&](int x, int y, int z) { return psi[((size_t)(z & m) * n + (y & m)) * n + (x & m)]; };
+        double gx, gy, gz;
+        if (FOUR) {
+            gx = (-at(i + 2, j, k) + 8.0 * at(i + 1, j, k) - 8.0 * at(i - 1, j, k) + at(i - 2, j, k)) * inv12h;
+            gy = (-at(i, j + 2, k) + 8.0 * at(i, j + 1, k) - 8.0 * at(i, j - 1, k) + at(i, j - 2, k)) * inv12h;
+            gz = (-at(i, j, k + 2) + 8.0 * at(i, j, k + 1) - 8.0 * at(i, j, k - 1) + at(i, j, k - 2)) * inv12h;
+        } else {
+            gx = (at(i + 1, j, k) - at(i - 1, j, k)) * inv2h;
+            gy = (at(i, j + 1, k) - at(i, j - 1, k)) * inv2h;
+            gz = (at(i, j, k + 1) - at(i, j, k - 1)) * inv2h;
+        }
+        g[c] = -gx;
+        g[total + c] = -gy;
+        g[2 * total + c] = -gz;
+    }
+}
+
+// the force at each particle: the grid force g ([3][n^3]) at the 8 CIC corners (in the
+// deposit's corner order), weighted by the corner's CIC weight (the deposit's adjoint)
+__global__ void __launch_bounds__(256) k_interp_force(const double* __restrict__ g, int n,
+                                                      const double* __restrict__ pos, long long np,
+                                                      double* __restrict__ acc)
+{
+    const int m = n - 1;
+    const size_t total = (size_t)n * n * n;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (long long)gridDim.x * blockDim.x) {
         int ix[2], iy[2], iz[2];
         double wx[2], wy[2], wz[2];
         cic_1d(pos[p], n, ix[0], ix[1], wx[0], wx[1]);
         cic_1d(pos[np + p], n, iy[0], iy[1], wy[0], wy[1]);
         cic_1d(pos[2 * np + p], n, iz[0], iz[1], wz[0], wz[1]);
-        auto psi = [&](int i, int j, int k) {
-            const size_t c = ((size_t)(k & m) * n + (j & m)) * n + (i & m);
-            return chi ? __dadd_rn(psiN[c], __dmul_rn(xi, chi[c])) : psiN[c];
-        };
         double s0 = 0.0, s1 = 0.0, s2 = 0.0;
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             const int a = c & 1, b = (c >> 1) & 1, e = (c >> 2) & 1;
-            const int i = ix[a], j = iy[b], k = iz[e];
+            const size_t cell = ((size_t)(iz[e] & m) * n + (iy[b] & m)) * n + (ix[a] & m);
             const double w = __dmul_rn(__dmul_rn(wx[a], wy[b]), wz[e]);
-            double gx, gy, gz;
-            if (FOUR) {
-                gx = (-psi(i + 2, j, k) + 8.0 * psi(i + 1, j, k) - 8.0 * psi(i - 1, j, k) + psi(i - 2, j, k)) * inv12h;
-                gy = (-psi(i, j + 2, k) + 8.0 * psi(i, j + 1, k) - 8.0 * psi(i, j - 1, k) + psi(i, j - 2, k)) * inv12h;
-                gz = (-psi(i, j, k + 2) + 8.0 * psi(i, j, k + 1) - 8.0 * psi(i, j, k - 1) + psi(i, j, k - 2)) * inv12h;
-            } else {
-                gx = (psi(i + 1, j, k) - psi(i - 1, j, k)) * inv2h;
-                gy = (psi(i, j + 1, k) - psi(i, j - 1, k)) * inv2h;
-                gz = (psi(i, j, k + 1) - psi(i, j, k - 1)) * inv2h;
-            }
-            s0 += w * -gx;
-            s1 += w * -gy;
-            s2 += w * -gz;
+            s0 += w * g[cell];
+            s1 += w * g[total + cell];
+            s2 += w * g[2 * total + cell];
         }
         acc[p] = s0;
         acc[np + p] = s1;
@@ -276,14 +296,29 @@ pm_status poisson32(pm_ctx* ctx, const double* delta, int n, double fac, double*
     return PM_OK;
 }
 
+// g = -grad(psiN + xi chi) at each particle (Eq. force, Sec. 3.5.2): the total potential and
+// its gradient on the grid (workspace [4][n^3]: Psi, then the three components), then the
+// CIC interpolation of the grid force.
 pm_status interp_force(pm_ctx* ctx, const double* psiN, const double* chi, double xi, int n, const double* pos,
                        long long np, double* acc)
 {
+    Workspace* w = nullptr;
+    PM_TRY(get_workspace(ctx, n, &w));
+    const size_t cells = (size_t)n * n * n;
+    if (!w->grad) PM_CUDA(cudaMalloc(&w->grad, 4 * cells * sizeof(double)));
+    double* psi = w->grad;
+    double* g = w->grad + cells;
+    ctx->begin(PM_K_PM, false, 0);
+    k_psi_total<<<grid_for(ctx, cells), kThreads, 0, ctx->stream>>>(psiN, chi, xi, cells, psi);
+    ctx->end();
     ctx->begin(PM_K_PM, false, 0);
     if (ctx->prm.grad_order == 2)
-        k_force<false><<<grid_for(ctx, (size_t)np), kThreads, 0, ctx->stream>>>(psiN, chi, xi, n, pos, np, acc);
+        k_grad<false><<<grid_for(ctx, cells), kThreads, 0, ctx->stream>>>(psi, n, g);
     else
-        k_force<true><<<grid_for(ctx, (size_t)np), kThreads, 0, ctx->stream>>>(psiN, chi, xi, n, pos, np, acc);
+        k_grad<true><<<grid_for(ctx, cells), kThreads, 0, ctx->stream>>>(psi, n, g);
+    ctx->end();
+    ctx->begin(PM_K_PM, false, 0);
+    k_interp_force<<<grid_for(ctx, (size_t)np), kThreads, 0, ctx->stream>>>(g, n, pos, np, acc);
     ctx->end();
     PM_CUDA(cudaGetLastError());
     return PM_OK;
