@@ -599,6 +599,41 @@ def main():
     solves = len(COMBOS)
     value = job_value(ms_step, solves, ws)  # ms per 512^3 solve, whole job
 
+    # end to end through the C ABI with host buffers: H2D delta, solve, D2H chi (headline pair),
+    # measured right after the timed steps, before the comparison legs allocate their own fields;
+    # with events between the three parts
+    host_in = torch.from_numpy(delta_h).pin_memory()
+    host_out = torch.empty((n, n, n), dtype=torch.float64).pin_memory()
+    dev_in = torch.empty_like(delta)
+    e2e_ms, e2e_parts = [], []
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # one untimed round trip first: the first copies through freshly pinned buffers pay for
+    # their mapping (about ten times the steady copy time on this machine)
+    dev_in.copy_(host_in, non_blocking=True)
+    host_out.copy_(phis[0], non_blocking=True)
+    torch.cuda.synchronize()
+    # the same two copies alone, for the host link's rate at this point of the run
+    e0.record(stream)
+    dev_in.copy_(host_in, non_blocking=True)
+    ea.record(stream)
+    host_out.copy_(phis[0], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    link = (cells_h := n ** 3 * 8) / (e0.elapsed_time(ea) * 1e-3) / 1e9, cells_h / (ea.elapsed_time(e1) * 1e-3) / 1e9
+    for _ in range(max(1, args.steps)):
+        phis[0].zero_()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        dev_in.copy_(host_in, non_blocking=True)
+        ea.record(stream)
+        api.scalar_mg_solve(dev_in, COMBOS[0][0], COMBOS[0][1], 1.0, TOL, phi=phis[0], ctx=ctx)
+        eb.record(stream)
+        host_out.copy_(phis[0], non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+        e2e_parts.append((e0.elapsed_time(ea), ea.elapsed_time(eb), eb.elapsed_time(e1)))
+
     # one more step with every launch traced, outside the timed region: the per-class breakdown
     ctx.trace(True)
     torch.cuda.synchronize()
@@ -621,32 +656,6 @@ def main():
             e1.record(stream)
             torch.cuda.synchronize()
             fp64[f"{aB},{aM}"] = {"ms": e0.elapsed_time(e1), "cycles": info["cycles"], "rel_res": info["rel_res"]}
-
-    # end to end through the C ABI with host buffers: H2D delta, solve, D2H chi (headline pair),
-    # with events between the three parts
-    host_in = torch.from_numpy(delta_h).pin_memory()
-    host_out = torch.empty((n, n, n), dtype=torch.float64).pin_memory()
-    dev_in = torch.empty_like(delta)
-    e2e_ms, e2e_parts = [], []
-    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    # one untimed round trip first: the first copies through freshly pinned buffers pay for
-    # their mapping (about ten times the steady copy time on this machine)
-    dev_in.copy_(host_in, non_blocking=True)
-    host_out.copy_(phis[0], non_blocking=True)
-    torch.cuda.synchronize()
-    for _ in range(max(1, args.steps)):
-        phis[0].zero_()
-        torch.cuda.synchronize()
-        e0.record(stream)
-        dev_in.copy_(host_in, non_blocking=True)
-        ea.record(stream)
-        api.scalar_mg_solve(dev_in, COMBOS[0][0], COMBOS[0][1], 1.0, TOL, phi=phis[0], ctx=ctx)
-        eb.record(stream)
-        host_out.copy_(phis[0], non_blocking=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        e2e_ms.append(e0.elapsed_time(e1))
-        e2e_parts.append((e0.elapsed_time(ea), ea.elapsed_time(eb), eb.elapsed_time(e1)))
 
     # roofline of the dominant kernel class, finest-level launches
     hbm, src = _peaks()
@@ -700,7 +709,8 @@ def main():
                 "solve_ms": sum(p[1] for p in e2e_parts) / len(e2e_parts),
                 "d2h_ms": sum(p[2] for p in e2e_parts) / len(e2e_parts),
                 "h2d_gbs": cells * 8 / (sum(p[0] for p in e2e_parts) / len(e2e_parts) * 1e-3) / 1e9,
-                "d2h_gbs": cells * 8 / (sum(p[2] for p in e2e_parts) / len(e2e_parts) * 1e-3) / 1e9},
+                "d2h_gbs": cells * 8 / (sum(p[2] for p in e2e_parts) / len(e2e_parts) * 1e-3) / 1e9,
+                "copies_alone_gbs": {"h2d": link[0], "d2h": link[1]}},
         "roofline": roof,
         "gpu_launches": launches,
         "clocks": clk.summary(),
