@@ -57,9 +57,17 @@ __global__ void k_density(const long long* __restrict__ acc, size_t cells, doubl
 }
 
 // Multiply the spectrum by fac / lambda_k with lambda_k = -(4/h^2) sum sin^2(pi m/n), the
-// 7-point Laplacian's eigenvalues; the zero mode is set to 0.  Also folds in 1/n^3.
+// 7-point Laplacian's eigenvalues; the zero mode is set to 0.  Also folds in 1/n^3.  Each
+// block first tabulates sin^2(pi m/n), m < n, in shared memory (n doubles), so the FP64 sines
+// are evaluated n times per block instead of three times per mode.
 __global__ void k_green(double2* __restrict__ spec, int n, double fac)
 {
+    extern __shared__ double s2[];  // [n]
+    for (int m = threadIdx.x; m < n; m += blockDim.x) {
+        const double sm = sinpi((double)m / n);
+        s2[m] = sm * sm;
+    }
+    __syncthreads();
     const int nh = n / 2 + 1;
     const size_t total = (size_t)n * n * nh;
     const double h2inv = (double)n * (double)n;
@@ -68,8 +76,7 @@ __global__ void k_green(double2* __restrict__ spec, int n, double fac)
         const int mx = (int)(t % nh);
         const size_t row = t / nh;
         const int my = (int)(row % n), mz = (int)(row / n);
-        const double sx = sinpi((double)mx / n), sy = sinpi((double)my / n), sz = sinpi((double)mz / n);
-        const double lam = -4.0 * h2inv * (sx * sx + sy * sy + sz * sz);
+        const double lam = -4.0 * h2inv * (s2[mx] + s2[my] + s2[mz]);
         double2 v = spec[t];
         if (t == 0) {
             v.x = 0.0;
@@ -258,7 +265,8 @@ pm_status poisson(pm_ctx* ctx, const double* delta, int n, double fac, double* p
         return PM_ERR_CUDA;
     }
     ctx->begin(PM_K_PM, false, 0);
-    k_green<<<grid_for(ctx, (size_t)n * n * (n / 2 + 1)), kThreads, 0, ctx->stream>>>(w->spec, n, fac);
+    k_green<<<grid_for(ctx, (size_t)n * n * (n / 2 + 1)), kThreads, (size_t)n * sizeof(double), ctx->stream>>>(w->spec, n,
+                                                                                                         fac);
     ctx->end();
     if (cufftExecZ2D(w->plan_c2r, (cufftDoubleComplex*)w->spec, (cufftDoubleReal*)psi) != CUFFT_SUCCESS) {
         ctx->set_error("cufftExecZ2D failed");
