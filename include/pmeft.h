@@ -333,7 +333,8 @@ pm_status pm_mg_sweep(pm_ctx* ctx, double* u, const double* f, double lambda, in
                       double eta, const unsigned char* kmask);
 /* The same sweep on an FP32 grid: mode 0 runs the two half-sweep kernels, mode k >= 1
  * the single-pass fused kernel with tile variant k-1 (pm_tune_log lists the variants the
- * autotuner chose; the inner FP32 cycle uses the fused kernel for grids >= 256^3), and
+ * autotuner chose; on FP32 levels of 64^3 and up the inner cycle takes whichever of these
+ * kernels and the two half-sweep launches the autotuner timed fastest), and
  * mode 100 + k variant k-1 with the background entering through its six bilinear
  * coefficients rounded to BF16 (the form in which the finest inner level of grids >= 256^3
  * receives it; needs bg and gap and no kmask).  A variant that does not tile n or cannot

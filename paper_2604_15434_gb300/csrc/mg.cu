@@ -915,7 +915,7 @@ struct Coef {
     double nu, kap, eta, src;
 };
 
-constexpr int kFusedMinN = 256;
+constexpr int kFusedMinN = 64;  // single-pass candidates from this size up (the autotuner chooses)
 constexpr int kResidZmMinN = 128;  // FP32 residual: z-marching kernel from this size up
 
 // Tile variants of the single-pass FP32 sweep: (TX, TY) x-y tile, NZ planes per block.
@@ -1053,6 +1053,9 @@ static void sweep_fused_f32(Exec* ctx, Level<float>& L, const float* F, float fs
     L.cur = 1 - L.cur;
 }
 
+template <typename T>
+static void sweep_halves(Exec* ctx, Level<T>& L, const T* F, T fscale, T lam, const Coef& c);
+
 // Autotuner: the first time a level of size n (with a given input set) is swept, every
 // fitting tile variant runs once on the real data (out of place, A -> B, so the state is
 // unchanged whichever runs last) and the fastest is kept for that key.
@@ -1073,14 +1076,15 @@ static int tuned_cfg(Exec* ctx, Level<float>& L, const float* F, float fscale, f
         cudaEventCreate(&e1);
         const bool was = ctx->c->tracing;
         ctx->c->tracing = false;
-        for (int cfg = 0; cfg < kNumFusedCfgs; ++cfg) {
-            if (!fused_cfg_usable(cfg, L)) continue;
+        for (int cfg = -1; cfg < kNumFusedCfgs; ++cfg) {  // -1: the two half-sweep launches
+            if (cfg >= 0 && !fused_cfg_usable(cfg, L)) continue;
             // one untimed launch, then three timed back to back
             for (int rep = 0; rep < 2; ++rep) {
                 const int launches = rep == 0 ? 1 : 3;
                 cudaEventRecord(e0, ctx->stream);
                 for (int q = 0; q < launches; ++q) {
-                    sweep_fused_f32(ctx, L, F, fscale, lam, c, cfg);
+                    if (cfg < 0) sweep_halves(ctx, L, F, fscale, lam, c);
+                    else sweep_fused_f32(ctx, L, F, fscale, lam, c, cfg);
                     L.cur = 1 - L.cur;  // keep A as the input of every trial
                 }
                 cudaEventRecord(e1, ctx->stream);
@@ -1100,34 +1104,27 @@ static int tuned_cfg(Exec* ctx, Level<float>& L, const float* F, float fscale, f
         ctx->c->tracing = was;
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        std::string choice = "two half-sweep launches";
+        if (best >= 0) {
+            const FusedCfg& g = kFusedCfgs[best];
+            choice = "tile " + std::to_string(g.tx) + "x" + std::to_string(g.ty) + " nz " + std::to_string(g.nz) +
+                     (g.col ? " col" : g.pair ? (g.bal ? " pair bal" : " pair") : " single");
+        }
         ctx->tune_log += "sweep32 n=" + std::to_string(L.n) + (L.bg ? " bg" : "") + (L.gap ? " gap" : "") +
-                         (L.kmask ? " mask" : "") +
-                         (cf ? " coef" : "") +
-                         ": tile " + std::to_string(kFusedCfgs[best].tx) + "x" + std::to_string(kFusedCfgs[best].ty) +
-                         " nz " + std::to_string(kFusedCfgs[best].nz) +
-                         (kFusedCfgs[best].col ? " col" : kFusedCfgs[best].pair ? (kFusedCfgs[best].bal ? " pair bal" : " pair") : " single") +
-                         " " + std::to_string(best_ms) + " ms (variants tried, ms:" + trials + ")\n";
+                         (L.kmask ? " mask" : "") + (cf ? " coef" : "") + ": " + choice + " " +
+                         std::to_string(best_ms) + " ms (variants tried, ms:" + trials + ")\n";
+    } else if (L.n < kCoefMinN) {
+        best = -1;  // without timing, the levels below the coefficient levels keep the half-sweeps
     }
     ctx->tuned[key] = best;
     return best;
 }
 
+// One red-black sweep as two half-sweep launches (one per colour), out of place: A = u[cur]
+// is read, B = u[1 - cur] receives the new values, then cur flips.
 template <typename T>
-static void sweep(Exec* ctx, Level<T>& L, const T* F, T fscale, T lam, const Coef& c, int force_mode = -1)
+static void sweep_halves(Exec* ctx, Level<T>& L, const T* F, T fscale, T lam, const Coef& c)
 {
-    // FP32 levels of at least 256^3 take the single-pass kernel (force_mode 0: two
-    // half-sweep launches, 1: single pass, -1: choose by size)
-    if constexpr (sizeof(T) == 4) {
-        // force_mode >= 1 selects tile variant force_mode - 1
-        if (force_mode >= 1 && force_mode <= kNumFusedCfgs && fused_cfg_usable(force_mode - 1, L)) {
-            sweep_fused_f32(ctx, L, F, fscale, lam, c, force_mode - 1);
-            return;
-        }
-        if (force_mode < 0 && L.n >= kFusedMinN && fused_cfg_fits(0, L.n)) {
-            sweep_fused_f32(ctx, L, F, fscale, lam, c, tuned_cfg(ctx, L, F, fscale, lam, c));
-            return;
-        }
-    }
     const int n = L.n;
     const T h2inv = (T)((double)n * (double)n);
     const T sp = c.nu >= 0.0 ? T(-1) : T(1);
@@ -1163,6 +1160,29 @@ static void sweep(Exec* ctx, Level<T>& L, const T* F, T fscale, T lam, const Coe
         }
     }
     L.cur = 1 - L.cur;
+}
+
+
+template <typename T>
+static void sweep(Exec* ctx, Level<T>& L, const T* F, T fscale, T lam, const Coef& c, int force_mode = -1)
+{
+    // FP32 levels of at least kFusedMinN^3: the autotuner's choice among the single-pass
+    // kernels and the two half-sweep launches (force_mode 0: the half-sweeps, k >= 1: tile
+    // variant k - 1, -1: the autotuner's choice)
+    if constexpr (sizeof(T) == 4) {
+        if (force_mode >= 1 && force_mode <= kNumFusedCfgs && fused_cfg_usable(force_mode - 1, L)) {
+            sweep_fused_f32(ctx, L, F, fscale, lam, c, force_mode - 1);
+            return;
+        }
+        if (force_mode < 0 && L.n >= kFusedMinN && fused_cfg_fits(0, L.n)) {
+            const int cfg = tuned_cfg(ctx, L, F, fscale, lam, c);
+            if (cfg >= 0) {
+                sweep_fused_f32(ctx, L, F, fscale, lam, c, cfg);
+                return;
+            }
+        }
+    }
+    sweep_halves(ctx, L, F, fscale, lam, c);
 }
 
 template <typename T, bool WRITE_R, bool MIXED>
