@@ -104,6 +104,7 @@ def _pmstep(args):
         torch.cuda.synchronize()
         print(json.dumps({"kernel": "pm_step", "n": n, "rep": rep, "ms": e0.elapsed_time(e1),
                           "cycles": info["cycles"]}), flush=True)
+    print(json.dumps({"tune": ctx.tune_log().strip().splitlines()}), flush=True)
 
 
 def main(argv=None):
