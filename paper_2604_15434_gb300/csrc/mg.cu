@@ -115,6 +115,12 @@ __global__ void __launch_bounds__(256) k_half_sweep(const T* __restrict__ own, c
 // defect-correction loop) also writes the FP32 copies: the plain residual -G for the inner
 // right-hand side, the iterate as the inner background, and the floored gap.
 template <typename T, bool BG, bool WRITE_R, bool MIXED>
+__device__ __forceinline__ void residual_cell_s(const Stencil<T>& s, const Stencil<T>& b, const T* F, T fscale,
+                                                T lam, const uint8_t* kmask, const T* gap, T ih2, T nu, T kap, T Df,
+                                                T lsat_c, bool floor_piece, T* r, uint8_t* sat, float* rplain,
+                                                float* chi32, float* gap32, size_t c, float (&fa)[5]);
+
+template <typename T, bool BG, bool WRITE_R, bool MIXED>
 __device__ __forceinline__ void residual_cell(const T* u, const T* F, T fscale, T lam,
                                               const uint8_t* kmask, const T* bg,
                                               const T* gap, int n, int lg, T ih2, T nu, T kap, T Df,
@@ -129,6 +135,17 @@ __device__ __forceinline__ void residual_cell(const T* u, const T* F, T fscale, 
     Stencil<T> s = load_stencil(u, u, i, j, k, n);
     Stencil<T> b;
     if (BG) b = load_stencil(bg, bg, i, j, k, n);
+    residual_cell_s<T, BG, WRITE_R, MIXED>(s, b, F, fscale, lam, kmask, gap, ih2, nu, kap, Df, lsat_c, floor_piece, r,
+                                           sat, rplain, chi32, gap32, c, fa);
+}
+
+// The residual of one cell from its stencil (residual_cell, or a tiled kernel's shared copy).
+template <typename T, bool BG, bool WRITE_R, bool MIXED>
+__device__ __forceinline__ void residual_cell_s(const Stencil<T>& s, const Stencil<T>& b, const T* F, T fscale,
+                                                T lam, const uint8_t* kmask, const T* gap, T ih2, T nu, T kap, T Df,
+                                                T lsat_c, bool floor_piece, T* r, uint8_t* sat, float* rplain,
+                                                float* chi32, float* gap32, size_t c, float (&fa)[5])
+{
     const T w = screen_w<T>(kmask, c);
     const T kc = kap * w;
     const T lsat = kc != T(0) ? lsat_c / w : T(0);
@@ -186,6 +203,66 @@ __global__ void __launch_bounds__(256) k_residual(const T* __restrict__ u, const
 #pragma unroll
     for (int q = 0; q < 5; ++q) acc[q] = (double)fa[q];
     block_sums<5>(acc, partials, fin_out);
+}
+
+// The FP64 residual of a level without a background (the FP64 cycle's levels, the mixed
+// loops' confirming residual and the FP64 outer loop), marching up z: a block of 32 x 8
+// threads keeps three planes of its 32 x 8 tile and their one-cell halo in a shared ring, so
+// each iterate value is read from global memory once per block instead of once per stencil
+// point.  Arithmetic and sums as k_residual (residual_cell_s); grid (n/32, n/8, n/nz).
+constexpr int kR64TX = 32, kR64TY = 8;
+template <bool WRITE_R, bool MIXED>
+__global__ void __launch_bounds__(256) k_residual64_zm(const double* __restrict__ u, const double* __restrict__ F,
+                                                       double fscale, double lam, const uint8_t* __restrict__ kmask,
+                                                       int n, int nz, double ih2, double nu, double kap, double Df,
+                                                       double lsat_c, bool floor_piece, double* __restrict__ r,
+                                                       uint8_t* __restrict__ sat, double* __restrict__ partials,
+                                                       float* __restrict__ rplain, float* __restrict__ chi32,
+                                                       float* __restrict__ gap32, const double* __restrict__ lamp,
+                                                       double* __restrict__ fin_out)
+{
+    constexpr int WX = kR64TX + 2, WY = kR64TY + 2, PL = WX * WY;
+    __shared__ double ring[3][PL];
+    if (lamp) lam += *lamp;
+    const int m = n - 1;
+    const int x0 = blockIdx.x * kR64TX, y0 = blockIdx.y * kR64TY, z0 = blockIdx.z * nz;
+    const int t = threadIdx.x, tx = t & (kR64TX - 1), ty = t / kR64TX;
+    const size_t plane = (size_t)n * n;
+    auto load = [&](int z, int slot) {
+        const size_t zo = (size_t)(z & m) * plane;
+        for (int e = t; e < PL; e += 256) {
+            const int xx = e % WX, yy = e / WX;
+            ring[slot][e] = u[zo + (size_t)((y0 - 1 + yy) & m) * n + ((x0 - 1 + xx) & m)];
+        }
+    };
+    float fa[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    load(z0 - 1, 0);
+    load(z0, 1);
+    const int cl = (ty + 1) * WX + tx + 1;
+    for (int s = 0; s < nz; ++s) {
+        const int z = z0 + s;
+        load(z + 1, (s + 2) % 3);
+        __syncthreads();
+        const double* pm = ring[s % 3];        // plane z - 1
+        const double* pc = ring[(s + 1) % 3];  // plane z
+        const double* pp = ring[(s + 2) % 3];  // plane z + 1
+        Stencil<double> st, b;
+        st.c0 = pc[cl];
+        st.ax = pc[cl + 1] + pc[cl - 1];
+        st.ay = pc[cl + WX] + pc[cl - WX];
+        st.az = pp[cl] + pm[cl];
+        st.exy = pc[cl + 1 + WX] - pc[cl + 1 - WX] - pc[cl - 1 + WX] + pc[cl - 1 - WX];
+        st.exz = pp[cl + 1] - pm[cl + 1] - pp[cl - 1] + pm[cl - 1];
+        st.eyz = pp[cl + WX] - pm[cl + WX] - pp[cl - WX] + pm[cl - WX];
+        const size_t c = (size_t)z * plane + (size_t)(y0 + ty) * n + (x0 + tx);
+        residual_cell_s<double, false, WRITE_R, MIXED>(st, b, F, fscale, lam, kmask, nullptr, ih2, nu, kap, Df, lsat_c,
+                                                       floor_piece, r, sat, rplain, chi32, gap32, c, fa);
+        __syncthreads();  // the slot of plane z - 1 is refilled next step
+    }
+    double acc[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) acc[q] = (double)fa[q];
+    block_sums<5>(acc, partials, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z), fin_out);
 }
 
 // ------------------------------------------------------------------ transfers
@@ -1226,6 +1303,20 @@ static int residual(Exec* ctx, Level<T>& L, const T* u, const T* F, T fscale, T 
             }
             ctx->end();
             return nb;
+        }
+    }
+    if constexpr (sizeof(T) == 8) {
+        // FP64 levels from 64^3 up without a background: the z-marching kernel
+        if (!L.bg && !L.gap && n >= 64) {
+            int nz = 8;
+            while ((size_t)(n / kR64TX) * (n / kR64TY) * (n / nz) > (size_t)kMaxPartials) nz *= 2;
+            const dim3 g3(n / kR64TX, n / kR64TY, n / nz);
+            ctx->begin(PM_K_RESID64, L.fine, (long long)L.cells);
+            k_residual64_zm<WRITE_R, MIXED><<<g3, 256, 0, ctx->stream>>>(
+                u, F, fscale, lam, L.kmask, n, nz, h2inv, c.nu, c.kap, sqDf * sqDf, (double)lsn, L.fine, L.r, L.sat,
+                ctx->red_partials, rplain, chi32, gap32, L.lamp, ctx->red_out);
+            ctx->end();
+            return (int)(g3.x * g3.y * g3.z);
         }
     }
     if (L.bg) {
