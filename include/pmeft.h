@@ -73,6 +73,10 @@ typedef struct {
                               at least 64^3 in one persistent cooperative launch per outer iteration, with grid
                               barriers whose waits are bounded (PM_ERR_TIMEOUT when one gives up); 0 launches
                               them per box (1; applies with coarse_exact = 0, coarsest_n = 4, inner_cycles = 1) */
+    int zero_start;        /* precision 1: the first sweep of each inner cycle on the finest inner level of grids
+                              >= 256^3 (the level that receives the background's coefficients) runs the
+                              zero-start kernel, which exploits that the correction starts at zero (same
+                              result as clearing it and sweeping; npre >= 1); 0 clears it and sweeps (1) */
 } pm_params;
 
 /* Report of one solve.  rel_res = |r|_2 / |f - <f>|_2 of the FP64 residual. */
@@ -337,7 +341,9 @@ pm_status pm_mg_sweep(pm_ctx* ctx, double* u, const double* f, double lambda, in
  * kernels and the two half-sweep launches the autotuner timed fastest), and
  * mode 100 + k variant k-1 with the background entering through its six bilinear
  * coefficients rounded to BF16 (the form in which the finest inner level of grids >= 256^3
- * receives it; needs bg and gap and no kmask).  A variant that does not tile n or cannot
+ * receives it; needs bg and gap and no kmask), and mode 200 the zero-start kernel on those
+ * coefficients: the sweep of u = 0 (the values passed in are ignored; n >= 64), which is the
+ * first sweep of each inner cycle when pm_params.zero_start is on.  A variant that does not tile n or cannot
  * take these inputs falls back to mode 0.  u, f: device n^3 float.
  * bg (nullable): the correction form of the mixed-precision inner cycle, where u is the
  * correction to the background bg and the operator is N(bg + u) - N(bg); gap (nullable,

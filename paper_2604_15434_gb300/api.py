@@ -34,7 +34,7 @@ class Params(ctypes.Structure):
                 ("coarse_sweeps", ctypes.c_int), ("precision", ctypes.c_int), ("include_dot_alphaB", ctypes.c_int),
                 ("inner_cycles", ctypes.c_int), ("autotune", ctypes.c_int), ("linear_eft", ctypes.c_int),
                 ("smoother", ctypes.c_int), ("coarse_exact", ctypes.c_int), ("grad_order", ctypes.c_int),
-                ("batch_persistent", ctypes.c_int)]
+                ("batch_persistent", ctypes.c_int), ("zero_start", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -379,7 +379,9 @@ def pm_mg_coarse_exact(u, f, nu, kappa, eta, kmask=None, ctx=None):
 
 def pm_mg_sweep_f32(u, f, lam, nu, kappa, eta, kmask=None, mode=1, bg=None, gap=None, ctx=None):
     """One red-black sweep of an FP32 grid in place; mode 0: two half-sweep launches, k >= 1: the
-    single-pass kernel with tile variant k-1.  bg / gap: the correction form (see pmeft.h)."""
+    single-pass kernel with tile variant k-1, 100 + k the same through the background's BF16
+    coefficients, 200 the zero-start kernel (u taken as zero).  bg / gap: the correction form
+    (see pmeft.h)."""
     ctx = ctx or default_context()
     n = u.shape[0]
     ctx._check(load().pm_mg_sweep_f32(ctx._h, _ptr(u, torch.float32, (n, n, n)), _ptr(f, torch.float32, (n, n, n)),

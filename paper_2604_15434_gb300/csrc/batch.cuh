@@ -79,9 +79,8 @@ static void box_iteration(Exec* x, BoxRun& B)
         k_restrict<float><<<grid_for(x, s[l + 1].cells), kThreads, 0, x->stream>>>(s[l].bg, s[l + 1].n, s[l + 1].bg);
         x->end();
     }
-    s[0].cur = 0;
     s[0].lamp = w->shift;
-    cudaMemsetAsync(s[0].u[0], 0, B.cells * sizeof(float), x->stream);
+    start_at_zero(x, s[0]);
     for (int k = 0; k < x->prm.inner_cycles; ++k) vcycle<float>(x, s, 0, w->rplain, 1.0f, 0.0f, B.c);
     add_correction_ff(x, ff_chi(w), s[0].u[s[0].cur], B.cells);
     box_residual(x, B);
@@ -100,9 +99,8 @@ static void box_down(Exec* x, BoxRun& B, int l32)
         k_restrict<float><<<grid_for(x, s[l + 1].cells), kThreads, 0, x->stream>>>(s[l].bg, s[l + 1].n, s[l + 1].bg);
         x->end();
     }
-    s[0].cur = 0;
     s[0].lamp = w->shift;
-    cudaMemsetAsync(s[0].u[0], 0, B.cells * sizeof(float), x->stream);
+    start_at_zero(x, s[0]);
     vcycle_down<float>(x, s, l32, w->rplain, 1.0f, 0.0f, B.c);
 }
 

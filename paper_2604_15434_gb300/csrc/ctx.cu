@@ -214,6 +214,7 @@ extern "C" void pm_default_params(pm_params* p)
     p->coarse_exact = 0;
     p->grad_order = 4;
     p->batch_persistent = 1;
+    p->zero_start = 1;
 }
 
 static bool params_ok(const pm_params* p)
@@ -225,7 +226,7 @@ static bool params_ok(const pm_params* p)
            (p->autotune == 0 || p->autotune == 1) && (p->linear_eft == 0 || p->linear_eft == 1) &&
            (p->smoother == 0 || p->smoother == 1) && (p->coarse_exact == 0 || (p->coarse_exact == 1 &&
            p->coarsest_n <= 4)) && (p->grad_order == 2 || p->grad_order == 4) &&
-           (p->batch_persistent == 0 || p->batch_persistent == 1);
+           (p->batch_persistent == 0 || p->batch_persistent == 1) && (p->zero_start == 0 || p->zero_start == 1);
 }
 
 extern "C" pm_status pm_coefficients(double aB0, double aM0, double a, double om0, int include_dot, pm_coeffs* out)

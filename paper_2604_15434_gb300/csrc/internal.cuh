@@ -147,6 +147,7 @@ struct Level {
     uint8_t* kmask = nullptr;  // 1: screening term off (coarse levels)
     uint8_t* sat = nullptr;    // 1: floored piece used by the last residual
     bool fine = false;         // finest level of its hierarchy (for tracing)
+    bool zero = false;         // the iterate is zero and not stored: the next sweep is the zero-start kernel
 };
 
 struct Workspace {

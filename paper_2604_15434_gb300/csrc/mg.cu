@@ -17,6 +17,7 @@
 #include "sweep_fused.cuh"
 #include "sweep_pair.cuh"
 #include "sweep_col.cuh"
+#include "sweep_zero.cuh"
 #include "outer_ff.cuh"
 #include "resid_fused.cuh"
 
@@ -1239,10 +1240,55 @@ static void sweep_halves(Exec* ctx, Level<T>& L, const T* F, T fscale, T lam, co
     L.cur = 1 - L.cur;
 }
 
+// The first sweep of a coefficient level whose iterate is zero (L.zero): the zero-start kernel
+// writes the swept field into the other buffer; the zero iterate itself was never stored.
+constexpr int kZeroTY = 8;
+static bool zero_start_level(const Level<float>& L) { return col_level(L) && L.n >= 64; }
+static void sweep_zero_f32(Exec* ctx, Level<float>& L, const float* F, float fscale, float lam, const Coef& c)
+{
+    const int n = L.n;
+    const float h2inv = (float)((double)n * (double)n);
+    const float sp = c.nu >= 0.0 ? -1.f : 1.f;
+    const double sqDf = c.eta * 6.0 * std::fabs(c.nu) * (double)n * (double)n;
+    const float lsn = c.kap != 0.0 ? (float)(0.75 * c.nu * (1.0 - c.eta) / c.kap) : 0.f;  // L_sat
+    const int nz = n < 32 ? n : 32;
+    const dim3 grid(n / 64, n / kZeroTY, n / nz);
+    // traced as an FP32 sweep but not as a finest-level launch: the finest-level class times
+    // the general sweep kernel
+    ctx->begin(PM_K_SWEEP32, false, 0);
+    k_sweep_zero<kZeroTY><<<grid, ZeroGeom<kZeroTY>::NT, 0, ctx->stream>>>(
+        L.u[1 - L.cur], F, fscale, lam, L.gap, n, nz, h2inv, (float)c.nu, (float)c.kap, sp, (float)(sqDf * sqDf), lsn,
+        L.lamp, L.coef);
+    ctx->end();
+    L.cur = 1 - L.cur;
+    L.zero = false;
+}
+
+// Start level L's iterate at zero: either mark it for the zero-start sweep (FP32 coefficient
+// levels, when the first thing to touch the iterate is a sweep) or clear it.
+template <typename T>
+static void start_at_zero(Exec* ctx, Level<T>& L)
+{
+    L.cur = 0;
+    L.zero = false;
+    if constexpr (sizeof(T) == 4) {
+        if (ctx->prm.zero_start && ctx->prm.npre >= 1 && zero_start_level(L)) {
+            L.zero = true;
+            return;
+        }
+    }
+    cudaMemsetAsync(L.u[0], 0, L.cells * sizeof(T), ctx->stream);
+}
 
 template <typename T>
 static void sweep(Exec* ctx, Level<T>& L, const T* F, T fscale, T lam, const Coef& c, int force_mode = -1)
 {
+    if constexpr (sizeof(T) == 4) {
+        if (L.zero) {
+            sweep_zero_f32(ctx, L, F, fscale, lam, c);
+            return;
+        }
+    }
     // FP32 levels of at least kFusedMinN^3: the autotuner's choice among the single-pass
     // kernels and the two half-sweep launches (force_mode 0: the half-sweeps, k >= 1: tile
     // variant k - 1, -1: the autotuner's choice)
@@ -1739,8 +1785,8 @@ pm_status mg_solve(pm_ctx* pctx, const double* delta, int n, const pm_coeffs& cf
                                                                                                s[l + 1].bg);
                 ctx->end();
             }
-            s[0].cur = 0;
-            PM_CUDA(cudaMemsetAsync(s[0].u[0], 0, cells * sizeof(float), ctx->stream));
+            start_at_zero(ctx, s[0]);
+            PM_CUDA(cudaGetLastError());
             for (int k = 0; k < P.inner_cycles; ++k) {
                 vcycle<float>(ctx, s, 0, w->rplain, 1.0f, (float)(-gm), c);
                 ++vcyc;
@@ -1837,10 +1883,14 @@ extern "C" pm_status pm_mg_sweep_f32(pm_ctx* ctx, float* u, const float* f, floa
                                      const float* gap, int mode)
 {
     PM_TRY(check_mg_args(ctx, n));
-    // mode 100 + k: variant k - 1 with the background entering through its BF16 coefficients
+    // mode 100 + k: variant k - 1 with the background entering through its BF16 coefficients;
+    // mode 200: the zero-start kernel (u taken as zero)
+    const bool from_zero = mode == 200;
+    if (from_zero) mode = 101;
     const bool via_coef = mode > 100;
     if (via_coef) mode -= 100;
-    if (!u || !f || mode < 0 || mode > kNumFusedCfgs || (gap && !bg) || (via_coef && (!bg || !gap || kmask)))
+    if (!u || !f || mode < 0 || mode > kNumFusedCfgs || (gap && !bg) || (via_coef && (!bg || !gap || kmask)) ||
+        (from_zero && n < 64))
         return PM_ERR_INVALID_ARG;
     Workspace* w = nullptr;
     PM_TRY(get_workspace(ctx, n, &w));
@@ -1861,6 +1911,7 @@ extern "C" pm_status pm_mg_sweep_f32(pm_ctx* ctx, float* u, const float* f, floa
     PM_CUDA(cudaMemcpyAsync(L.u[0], u, cells * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
     Coef c{nu, kappa, eta, 1.0};
     Exec ex(ctx);
+    L.zero = from_zero;
     sweep<float>(&ex, L, f, 1.0f, lambda, c, mode);
     PM_CUDA(cudaMemcpyAsync(u, L.u[L.cur], cells * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
     PM_CUDA(cudaGetLastError());

@@ -1,0 +1,180 @@
+// sweep_zero.cuh -- the first red-black sweep of the finest inner level, from a zero start.
+//
+// Every outer iteration of the mixed-precision loop starts the FP32 inner V-cycle on the
+// correction e = 0 (Sec. 3.4 FAS, in the correction form of the defect-correction loop).  The
+// first pre-smoothing sweep then needs almost nothing of the general kernels' 19-point
+// stencils:
+//   - red cells see only zeros: X = Y = Z = 0, no cross differences, so q2 = 0 and the local
+//     quadratic of Sec. 3.2.1 has E = -(f + lambda), E' = (8 kappa (L_sat - gap) - 6 nu)/h^2;
+//     the update depends on the cell's own right-hand side and gap alone;
+//   - black cells see the six new red faces and zeros elsewhere (their centre and the 12
+//     same-colour edge neighbours are still zero at the half-sweep's start), so only the
+//     background coefficients of X, Y and Z enter (the first two coefficient words).
+// The arithmetic is that of the general kernels (local_eval2_cf and pick_update of
+// sweep_pair.cuh) with those zeros put in, so the result is the general sweep's on e = 0.
+// The kernel replaces the clearing of e and the first general sweep: it reads the right-hand
+// side, the gap and two of the three coefficient words and writes e, 20 bytes per cell
+// instead of 4 + 29.
+//
+// Layout: a block owns a 64 x TY tile of x-y rows and marches NZ planes up z.  A thread owns
+// the column pair (x, x + 1), x even, of one row; on every plane one of the two is red and the
+// other black.  Step s computes the red cell of plane s (rows -1 .. TY of the tile, so the
+// black cells on the tile's y edges have their faces) and the black cell of plane s - 2, the
+// two as the lanes of paired FP32 instructions.  The black cell's z-faces are the red values
+// of planes s - 1 and s - 3 in its column, which this thread computed itself; its in-plane
+// faces are the red values of plane s - 2 of the pair and of the neighbouring pairs and rows,
+// from a three-slot shared ring (one value per pair: the red one).  One more warp computes the
+// red cells just outside the tile in x (x = -1 and x = 64).  Fields are loaded one plane
+// ahead into registers (8-byte loads of the pair, coalesced per row).
+#pragma once
+
+#include "sweep_pair.cuh"
+
+namespace pmeft {
+
+template <int TY>
+struct ZeroGeom {
+    static constexpr int RW = 34;                   // ring row: x = -1, pairs 0..31, x = 64
+    static constexpr int RH = TY + 2;               // ring rows: y = -1 .. TY
+    static constexpr int NXH = 2 * RH;              // x-halo lanes
+    static constexpr int NXW = (NXH + 31) / 32;     // x-halo warps
+    static constexpr int NW = RH + NXW;             // row warps + x-halo warps
+    static constexpr int NT = 32 * NW;
+};
+
+// The red and black updates of two cells, one per lane of the paired arithmetic.  Red lane:
+// all stencil values zero.  Black lane: faces bax, bay, baz, the rest zero.
+__device__ __forceinline__ float2 zero_start_update(float bax, float bay, float baz, const BgCoef& cb, float2 rhs,
+                                                    float2 gapx, float ih2, float nu, float kap, float sp, float Df,
+                                                    float lsat, float h2over6, float inv2P)
+{
+    Stencil2 st;
+    st.c0 = make_float2(0.f, 0.f);
+    st.ax = make_float2(0.f, bax);
+    st.ay = make_float2(0.f, bay);
+    st.az = make_float2(0.f, baz);
+    st.exy = st.exz = st.eyz = make_float2(0.f, 0.f);
+    const BgCoef ca{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const Local2 o = local_eval2_cf(st, ca, cb, ih2, nu, f2(kap), rhs, f2(lsat), gapx);
+    float2 e;
+    if (kap == 0.f) {
+        e.x = __fdividef(-o.G.x, o.Ep.x);
+        e.y = __fdividef(-o.G.y, o.Ep.y);
+    } else {
+        e.x = pick_update(o.G.x, o.Ep.x, o.P.x, o.D.x, o.g.x, sp, Df, h2over6, inv2P);
+        e.y = pick_update(o.G.y, o.Ep.y, o.P.y, o.D.y, o.g.y, sp, Df, h2over6, inv2P);
+    }
+    return make_float2(0.f + e.x, 0.f + e.y);  // the new value c0 + e, as the general kernels form it
+}
+
+// One sweep from e = 0 into V (n^3).  F: right-hand side (fscale F + lam [+ *lamp]); gap:
+// L_sat - L(background); coef: the three BF16-pair planes of the background coefficients
+// (only the first two are read).  Grid (n / 64, n / TY, n / NZ), n >= 64.
+template <int TY>
+__global__ void __launch_bounds__(ZeroGeom<TY>::NT, 3) k_sweep_zero(float* __restrict__ V, const float* __restrict__ F,
+                                                                 float fscale, float lam, const float* __restrict__ gap,
+                                                                 int n, int NZ, float ih2, float nu, float kap, float sp,
+                                                                 float Df, float lsat, const float* __restrict__ lamp,
+                                                                 const uint32_t* __restrict__ coef)
+{
+    using G = ZeroGeom<TY>;
+    constexpr int RW = G::RW, RH = G::RH;
+    __shared__ float ring[3][RH][RW];  // red values of three planes, slot (p - z0 + 1) mod 3
+    if (lamp) lam += *lamp;
+    const int m = n - 1;
+    const int x0 = blockIdx.x * 64, y0 = blockIdx.y * TY, z0 = blockIdx.z * NZ;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const size_t plane = (size_t)n * n, cells = plane * (size_t)n;
+    const float h2over6 = 1.f / (6.f * ih2), inv2P = kap != 0.f ? 1.f / (-48.f * kap * ih2 * ih2) : 0.f;
+    const BgCoef nocoef{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    auto slot = [&](int p) { return (p - z0 + 1) % 3; };  // p >= z0 - 1
+    const int zred = z0 + NZ;                            // red planes z0 - 1 .. zred
+
+    if (warp < RH) {
+        // ---------------------------------------------------------------- row warps
+        const int y = warp - 1;  // -1 .. TY
+        const bool interior = y >= 0 && y < TY;
+        const int q = lane;
+        const size_t rowoff = (size_t)((y0 + y) & m) * n + x0 + 2 * q;  // x0 + 2q + 1 < n: no wrap in x
+        float2 fN = make_float2(0.f, 0.f), gN = fN;  // fields of the next plane
+        uint2 c0N = make_uint2(0u, 0u), c1N = c0N;
+        auto load = [&](int p) {
+            const size_t o = (size_t)(p & m) * plane + rowoff;
+            fN = *reinterpret_cast<const float2*>(F + o);
+            gN = *reinterpret_cast<const float2*>(gap + o);
+            if (interior) {
+                c0N = *reinterpret_cast<const uint2*>(coef + o);
+                c1N = *reinterpret_cast<const uint2*>(coef + cells + o);
+            }
+        };
+        // fields of the black cells of planes s - 1 (b1) and s - 2 (b2)
+        float b1F = 0.f, b1G = 0.f, b2F = 0.f, b2G = 0.f;
+        uint32_t b1C0 = 0u, b1C1 = 0u, b2C0 = 0u, b2C1 = 0u;
+        // red values of planes s - 1 (column 1 - C), s - 2 (column C), s - 3 (column 1 - C)
+        float r1 = 0.f, r2 = 0.f, r3 = 0.f;
+        load(z0 - 1);
+        for (int s = z0 - 1; s <= zred + 1; ++s) {
+            const float2 fc = fN, gc = gN;
+            const uint2 c0c = c0N, c1c = c1N;
+            if (s + 1 <= zred) load(s + 1);
+            const int C = (y0 + y + s) & 1;  // the column of the pair that is red on planes s, s - 2
+            const bool blk = interior && s - 2 >= z0;
+            // black cell of plane s - 2 (column 1 - C): in-plane faces from the ring
+            float bax = 0.f, bay = 0.f;
+            if (blk) {
+                const float(*r)[RW] = ring[slot(s - 2)];
+                // its x-neighbour outside the pair: the red cell of pair q + 1 (black column 1) or of
+                // pair q - 1 (black column 0)
+                const float rout = C ? r[y + 1][q] : r[y + 1][q + 2];
+                bax = r2 + rout;
+                bay = r[y + 2][q + 1] + r[y][q + 1];
+            }
+            const float2 rhs = f2fma(f2(fscale), make_float2(C ? fc.y : fc.x, b2F), f2(lam));
+            const BgCoef cb = blk ? unpack_bg_coef(b2C0, b2C1, 0u) : nocoef;
+            // .x: the red cell of plane s; .y: the black cell of plane s - 2
+            const float2 v = zero_start_update(bax, bay, r1 + r3, cb, rhs, make_float2(C ? gc.y : gc.x, b2G), ih2, nu,
+                                               kap, sp, Df, lsat, h2over6, inv2P);
+            if (s <= zred) ring[slot(s)][y + 1][q + 1] = v.x;
+            if (blk) {
+                const float2 out = C ? make_float2(v.y, r2) : make_float2(r2, v.y);
+                *reinterpret_cast<float2*>(V + (size_t)(s - 2) * plane + rowoff) = out;
+            }
+            // the black cell of plane s is column 1 - C
+            b2F = b1F;
+            b2G = b1G;
+            b2C0 = b1C0;
+            b2C1 = b1C1;
+            b1F = C ? fc.x : fc.y;
+            b1G = C ? gc.x : gc.y;
+            b1C0 = C ? c0c.x : c0c.y;
+            b1C1 = C ? c1c.x : c1c.y;
+            r3 = r2;
+            r2 = r1;
+            r1 = v.x;
+            __syncthreads();
+        }
+    } else {
+        // ---------------------------------------------------------------- x-halo lanes
+        const int idx = (warp - RH) * 32 + lane;
+        const bool active = idx < G::NXH;
+        const int side = idx < RH ? 0 : 1;  // 0: x = -1, 1: x = 64
+        const int y = (active ? idx % RH : 0) - 1;
+        const int xg = side ? ((x0 + 64) & m) : ((x0 - 1) & m);
+        const int col = side ? RW - 1 : 0;
+        const size_t rowoff = (size_t)((y0 + y) & m) * n + xg;
+        for (int s = z0 - 1; s <= zred + 1; ++s) {
+            // red on plane s when x + y + s is even (x = x0 - 1 or x0 + 64, x0 even)
+            const bool red = active && s <= zred && ((1 - side + y0 + y + s) & 1) == 0;
+            if (red) {
+                const size_t o = (size_t)(s & m) * plane + rowoff;
+                const float2 rhs = f2fma(f2(fscale), make_float2(F[o], 0.f), f2(lam));
+                const float2 v = zero_start_update(0.f, 0.f, 0.f, nocoef, rhs, make_float2(gap[o], 0.f), ih2, nu, kap,
+                                                   sp, Df, lsat, h2over6, inv2P);
+                ring[slot(s)][y + 1][col] = v.x;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+}  // namespace pmeft

@@ -420,6 +420,48 @@ def test_column_sweep_equals_pair_coefficient_sweep(gpu_lib, n, mode):
     assert np.sqrt(np.mean((got - ref) ** 2)) <= 1e-2 * np.sqrt(np.mean((ref - u) ** 2))
 
 
+ZERO_START_MODE = 200  # the zero-start kernel: the first sweep of an inner cycle, from u = 0
+
+
+@pytest.mark.parametrize("n", [64, 128, 256])
+@pytest.mark.parametrize("pair", [(-0.5, 0.0), (-2.0, 0.0), (-0.5, 0.5)])
+def test_zero_start_sweep_equals_general_sweep_from_zero(gpu_lib, n, pair):
+    """The zero-start kernel gives the general coefficient sweep's result on u = 0 (the same
+    formulas with the zeros put in, so equal up to the sign of zero), for both signs of nu and
+    with floored cells, on grids of one and several blocks in every direction; the field passed
+    in is ignored."""
+    c = O.coefficients(pair[0], pair[1], 1.0)
+    f = O.source(synth.lognormal_delta(n, -2.0, 1.5, 500 + n), c)
+    rng = np.random.default_rng(n)
+    bg = cu(2.0 * rng.standard_normal((n, n, n)) / n ** 2, torch.float32)
+    lsat = 0.75 * c["nu"] * (1 - 0.35) / c["kappa"]
+    gap = cu(lsat * (1.0 + 0.5 * rng.standard_normal((n, n, n))), torch.float32)
+    args = (cu(f, torch.float32), 0.01, c["nu"], c["kappa"], 0.35)
+    zeros = torch.zeros((n, n, n), dtype=torch.float32, device=DEV)
+    want = gpu_lib.pm_mg_sweep_f32(zeros, *args, mode=PAIR_COEF_MODE, bg=bg, gap=gap).cpu().numpy()
+    junk = cu(rng.standard_normal((n, n, n)), torch.float32)
+    got = gpu_lib.pm_mg_sweep_f32(junk, *args, mode=ZERO_START_MODE, bg=bg, gap=gap).cpu().numpy()
+    assert np.isfinite(got).all() and np.abs(want).max() > 0
+    assert np.array_equal(got, want), np.abs(got - want).max() / np.abs(want).max()
+
+
+@pytest.mark.parametrize("pair", [(-2.0, 0.0), (-0.5, 0.0)])
+def test_zero_start_solve_equals_cleared_start_256(gpu_lib, pair):
+    """Inside the mixed solve at 256^3 (the size where the finest inner level receives the
+    background's coefficients) the zero-start sweep changes nothing: the same outer iterations
+    and chi to FP32 rounding of the inner cycle, as with the correction cleared and swept."""
+    n = 256
+    d = cu(synth.lognormal_delta(n, -2.0, 1.5, 1003))
+    out = []
+    for zs in (0, 1):
+        phi, info = gpu_lib.scalar_mg_solve(d, pair[0], pair[1], 1.0, 1e-8,
+                                            ctx=gpu_lib.Context(precision=1, zero_start=zs, max_cycles=100))
+        assert info["status"] == 0 and info["rel_res"] <= 1e-8
+        out.append((phi, info))
+    assert out[0][1]["cycles"] == out[1][1]["cycles"]
+    assert float((out[0][0] - out[1][0]).norm() / out[0][0].norm()) < 1e-7
+
+
 @pytest.mark.parametrize("inner", [1, 2, 3])
 def test_mixed_precision_solve_256_uses_fused_sweep(gpu_lib, inner):
     """At 256^3 the inner cycle runs the fused sweep on its finest level; the mixed solve
