@@ -343,7 +343,10 @@ pm_status pm_mg_sweep(pm_ctx* ctx, double* u, const double* f, double lambda, in
  * coefficients rounded to BF16 (the form in which the finest inner level of grids >= 256^3
  * receives it; needs bg and gap and no kmask), and mode 200 the zero-start kernel on those
  * coefficients: the sweep of u = 0 (the values passed in are ignored; n >= 64), which is the
- * first sweep of each inner cycle when pm_params.zero_start is on.  A variant that does not tile n or cannot
+ * first sweep of each inner cycle when pm_params.zero_start is on (200 + k: its variant k - 1,
+ * k = 1..6: tiles 64 x 8 and 64 x 16 with fields loaded one or two planes ahead, 128 x 4,
+ * 128 x 8; a variant whose tile does not divide n returns PM_ERR_INVALID_ARG).  A variant that
+ * does not tile n or cannot
  * take these inputs falls back to mode 0.  u, f: device n^3 float.
  * bg (nullable): the correction form of the mixed-precision inner cycle, where u is the
  * correction to the background bg and the operator is N(bg + u) - N(bg); gap (nullable,

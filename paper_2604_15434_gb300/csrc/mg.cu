@@ -1242,23 +1242,99 @@ static void sweep_halves(Exec* ctx, Level<T>& L, const T* F, T fscale, T lam, co
 
 // The first sweep of a coefficient level whose iterate is zero (L.zero): the zero-start kernel
 // writes the swept field into the other buffer; the zero iterate itself was never stored.
-constexpr int kZeroTY = 8;
+// Variants (rows per block, planes of fields loaded ahead); the autotuner times them on the
+// first use of each size, as it does the general sweep's tiles.
+struct ZeroCfg {
+    int tx, ty, pf;
+};
+static const ZeroCfg kZeroCfgs[] = {{64, 8, 1}, {64, 8, 2}, {64, 16, 1}, {64, 16, 2}, {128, 4, 1}, {128, 8, 1}};
+constexpr int kNumZeroCfgs = sizeof(kZeroCfgs) / sizeof(kZeroCfgs[0]);
 static bool zero_start_level(const Level<float>& L) { return col_level(L) && L.n >= 64; }
-static void sweep_zero_f32(Exec* ctx, Level<float>& L, const float* F, float fscale, float lam, const Coef& c)
+
+template <int TX, int TY, int PF>
+static void launch_zero(Exec* ctx, float* V, const float* F, float fscale, float lam, const Level<float>& L,
+                        float h2inv, const Coef& c, float sp, float Df, float lsn)
+{
+    const int n = L.n;
+    const int nz = n < 32 ? n : 32;
+    const dim3 grid(n / TX, n / TY, n / nz);
+    k_sweep_zero<TX, TY, PF><<<grid, ZeroGeom<TX, TY>::NT, 0, ctx->stream>>>(V, F, fscale, lam, L.gap, n, nz, h2inv,
+                                                                     (float)c.nu, (float)c.kap, sp, Df, lsn, L.lamp,
+                                                                     L.coef);
+}
+
+static void launch_zero_cfg(Exec* ctx, int cfg, const float* F, float fscale, float lam, Level<float>& L,
+                            const Coef& c)
 {
     const int n = L.n;
     const float h2inv = (float)((double)n * (double)n);
     const float sp = c.nu >= 0.0 ? -1.f : 1.f;
     const double sqDf = c.eta * 6.0 * std::fabs(c.nu) * (double)n * (double)n;
+    const float Df = (float)(sqDf * sqDf);
     const float lsn = c.kap != 0.0 ? (float)(0.75 * c.nu * (1.0 - c.eta) / c.kap) : 0.f;  // L_sat
-    const int nz = n < 32 ? n : 32;
-    const dim3 grid(n / 64, n / kZeroTY, n / nz);
+    float* V = L.u[1 - L.cur];
+    switch (cfg) {
+    case 0: launch_zero<64, 8, 1>(ctx, V, F, fscale, lam, L, h2inv, c, sp, Df, lsn); break;
+    case 1: launch_zero<64, 8, 2>(ctx, V, F, fscale, lam, L, h2inv, c, sp, Df, lsn); break;
+    case 2: launch_zero<64, 16, 1>(ctx, V, F, fscale, lam, L, h2inv, c, sp, Df, lsn); break;
+    case 3: launch_zero<64, 16, 2>(ctx, V, F, fscale, lam, L, h2inv, c, sp, Df, lsn); break;
+    case 4: launch_zero<128, 4, 1>(ctx, V, F, fscale, lam, L, h2inv, c, sp, Df, lsn); break;
+    default: launch_zero<128, 8, 1>(ctx, V, F, fscale, lam, L, h2inv, c, sp, Df, lsn); break;
+    }
+}
+
+static bool zero_cfg_fits(int cfg, int n) { return n % kZeroCfgs[cfg].tx == 0 && n % kZeroCfgs[cfg].ty == 0; }
+
+// force_cfg >= 0: that variant instead of the autotuner's choice
+static void sweep_zero_f32(Exec* ctx, Level<float>& L, const float* F, float fscale, float lam, const Coef& c,
+                           int force_cfg = -1)
+{
+    const int key = -L.n;  // the general sweep's keys are positive
+    auto it = ctx->tuned.find(key);
+    int best = 0;
+    if (force_cfg >= 0) {
+        best = force_cfg;
+    } else if (it != ctx->tuned.end()) {
+        best = it->second;
+    } else {
+        if (ctx->prm.autotune) {
+            float best_ms = 1e30f;
+            std::string trials;
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            for (int cfg = 0; cfg < kNumZeroCfgs; ++cfg) {
+                if (!zero_cfg_fits(cfg, L.n)) continue;
+                for (int rep = 0; rep < 2; ++rep) {  // one untimed launch, then three timed
+                    const int launches = rep == 0 ? 1 : 3;
+                    cudaEventRecord(e0, ctx->stream);
+                    for (int q = 0; q < launches; ++q) launch_zero_cfg(ctx, cfg, F, fscale, lam, L, c);
+                    cudaEventRecord(e1, ctx->stream);
+                    cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    ms /= (float)launches;
+                    if (rep == 1) {
+                        trials += " " + std::to_string(cfg) + ":" + std::to_string(ms).substr(0, 6);
+                        if (ms < best_ms) {
+                            best_ms = ms;
+                            best = cfg;
+                        }
+                    }
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            ctx->tune_log += "sweep32 zero-start n=" + std::to_string(L.n) + ": tile " +
+                             std::to_string(kZeroCfgs[best].tx) + "x" + std::to_string(kZeroCfgs[best].ty) + " ahead " + std::to_string(kZeroCfgs[best].pf) +
+                             " " + std::to_string(best_ms) + " ms (variants tried, ms:" + trials + ")\n";
+        }
+        ctx->tuned[key] = best;
+    }
     // traced as an FP32 sweep but not as a finest-level launch: the finest-level class times
     // the general sweep kernel
     ctx->begin(PM_K_SWEEP32, false, 0);
-    k_sweep_zero<kZeroTY><<<grid, ZeroGeom<kZeroTY>::NT, 0, ctx->stream>>>(
-        L.u[1 - L.cur], F, fscale, lam, L.gap, n, nz, h2inv, (float)c.nu, (float)c.kap, sp, (float)(sqDf * sqDf), lsn,
-        L.lamp, L.coef);
+    launch_zero_cfg(ctx, best, F, fscale, lam, L, c);
     ctx->end();
     L.cur = 1 - L.cur;
     L.zero = false;
@@ -1884,13 +1960,14 @@ extern "C" pm_status pm_mg_sweep_f32(pm_ctx* ctx, float* u, const float* f, floa
 {
     PM_TRY(check_mg_args(ctx, n));
     // mode 100 + k: variant k - 1 with the background entering through its BF16 coefficients;
-    // mode 200: the zero-start kernel (u taken as zero)
-    const bool from_zero = mode == 200;
+    // mode 200: the zero-start kernel (u taken as zero), 200 + k its variant k - 1
+    const bool from_zero = mode >= 200 && mode <= 200 + kNumZeroCfgs;
+    const int zero_cfg = from_zero ? mode - 201 : -1;
     if (from_zero) mode = 101;
     const bool via_coef = mode > 100;
     if (via_coef) mode -= 100;
     if (!u || !f || mode < 0 || mode > kNumFusedCfgs || (gap && !bg) || (via_coef && (!bg || !gap || kmask)) ||
-        (from_zero && n < 64))
+        (from_zero && (n < 64 || (zero_cfg >= 0 && !zero_cfg_fits(zero_cfg, n)))))
         return PM_ERR_INVALID_ARG;
     Workspace* w = nullptr;
     PM_TRY(get_workspace(ctx, n, &w));
@@ -1911,8 +1988,8 @@ extern "C" pm_status pm_mg_sweep_f32(pm_ctx* ctx, float* u, const float* f, floa
     PM_CUDA(cudaMemcpyAsync(L.u[0], u, cells * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
     Coef c{nu, kappa, eta, 1.0};
     Exec ex(ctx);
-    L.zero = from_zero;
-    sweep<float>(&ex, L, f, 1.0f, lambda, c, mode);
+    if (from_zero) sweep_zero_f32(&ex, L, f, 1.0f, lambda, c, zero_cfg);
+    else sweep<float>(&ex, L, f, 1.0f, lambda, c, mode);
     PM_CUDA(cudaMemcpyAsync(u, L.u[L.cur], cells * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
     PM_CUDA(cudaGetLastError());
     return PM_OK;

@@ -86,7 +86,7 @@ __device__ __forceinline__ float cmp(float2 v)
 __device__ __forceinline__ float col_update1(const Local<float>& o, float kap, float sp, float Df, float h2over6,
                                              float inv2P)
 {
-    if (kap == 0.f) return __fdividef(-o.G, o.Ep);
+    if (kap == 0.f) return div_ftz(-o.G, o.Ep);
     return pick_update(o.G, o.Ep, o.P, o.D, o.g, sp, Df, h2over6, inv2P);
 }
 
@@ -265,8 +265,8 @@ __global__ void __launch_bounds__(ColGeom<TY>::NT, TY <= 8 ? 2 : 1)
                                             make_float2(fr[1], bf[1]));
             float er, eb;
             if (kap == 0.f) {
-                er = __fdividef(-o.G.x, o.Ep.x);
-                eb = __fdividef(-o.G.y, o.Ep.y);
+                er = div_ftz(-o.G.x, o.Ep.x);
+                eb = div_ftz(-o.G.y, o.Ep.y);
             } else {
                 er = pick_update(o.G.x, o.Ep.x, o.P.x, o.D.x, o.g.x, sp, Df, h2over6, inv2P);
                 eb = pick_update(o.G.y, o.Ep.y, o.P.y, o.D.y, o.g.y, sp, Df, h2over6, inv2P);

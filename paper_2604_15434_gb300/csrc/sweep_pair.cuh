@@ -146,13 +146,29 @@ __device__ __forceinline__ Local2 local_eval2_cf(const Stencil2& s, const BgCoef
     return o;
 }
 
+// Approximate reciprocal square root and quotient of the special-function unit with subnormal
+// inputs and results flushed to zero: for the normal operands of the sweeps they return what
+// rsqrtf and __fdividef return, without the instructions that rescale subnormal operands.
+__device__ __forceinline__ float rsqrt_ftz(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float div_ftz(float a, float b)
+{
+    float r;
+    asm("div.approx.ftz.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+
 // local_update_fast for one cell, without branches
 __device__ __forceinline__ float pick_update(float G, float Ep, float P, float D, float g, float sp, float Df,
                                              float h2over6, float inv2P)
 {
     const float Dc = fmaxf(D, Df);
-    const float sq = Dc * rsqrtf(Dc);
-    const float r1 = __fdividef(-2.f * G, Ep + sp * sq);
+    const float sq = Dc * rsqrt_ftz(Dc);
+    const float r1 = div_ftz(-2.f * G, Ep + sp * sq);
     const float r2 = (sp * sq - Ep) * inv2P;
     float e = (Ep * sp > 0.f) ? r1 : r2;
     e = (D < Df) ? -g * h2over6 : e;
@@ -271,8 +287,8 @@ __global__ void __launch_bounds__(PairGeom<TY, BAL>::NT, TY >= 16 ? (BAL ? 2 : 3
         e.x = pick_update(o.G.x, o.Ep.x, o.P.x, o.D.x, o.g.x, sp, Df, h2over6, inv2P * iw.x);
         e.y = pick_update(o.G.y, o.Ep.y, o.P.y, o.D.y, o.g.y, sp, Df, h2over6, inv2P * iw.y);
         if (kc.x == 0.f || kc.y == 0.f) {  // unscreened cells: the linear (Newton) step
-            if (kc.x == 0.f) e.x = __fdividef(-o.G.x, o.Ep.x);
-            if (kc.y == 0.f) e.y = __fdividef(-o.G.y, o.Ep.y);
+            if (kc.x == 0.f) e.x = div_ftz(-o.G.x, o.Ep.x);
+            if (kc.y == 0.f) e.y = div_ftz(-o.G.y, o.Ep.y);
         }
         return e;
     };
@@ -347,8 +363,8 @@ __global__ void __launch_bounds__(PairGeom<TY, BAL>::NT, TY >= 16 ? (BAL ? 2 : 3
                 const int ca = r_cuA[it] + pa, cb = r_cuB[it] + pbb;
                 const Stencil2 a = stencil2(up, uc, un, ca, cb);
                 const float2 kc = f2mul(f2(kap), rW[it]);
-                const float2 iw = kmask ? make_float2(rW[it].x > 0.f ? 1.f / rW[it].x : 1.f,
-                                                      rW[it].y > 0.f ? 1.f / rW[it].y : 1.f)
+                const float2 iw = kmask ? make_float2(rW[it].x > 0.f ? __frcp_rn(rW[it].x) : 1.f,
+                                                      rW[it].y > 0.f ? __frcp_rn(rW[it].y) : 1.f)
                                         : f2(1.f);
                 Local2 o;
                 if (COEF) {
@@ -400,8 +416,8 @@ __global__ void __launch_bounds__(PairGeom<TY, BAL>::NT, TY >= 16 ? (BAL ? 2 : 3
                 a.eyz = f2sub(f2sub(make_float2(un[ca + WU], un[cb + WU]), make_float2(up[ca + WU], up[cb + WU])),
                               f2sub(make_float2(un[ca - WU], un[cb - WU]), make_float2(up[ca - WU], up[cb - WU])));
                 const float2 kc = f2mul(f2(kap), bW[it]);
-                const float2 iw = kmask ? make_float2(bW[it].x > 0.f ? 1.f / bW[it].x : 1.f,
-                                                      bW[it].y > 0.f ? 1.f / bW[it].y : 1.f)
+                const float2 iw = kmask ? make_float2(bW[it].x > 0.f ? __frcp_rn(bW[it].x) : 1.f,
+                                                      bW[it].y > 0.f ? __frcp_rn(bW[it].y) : 1.f)
                                         : f2(1.f);
                 Local2 o;
                 if (COEF) {

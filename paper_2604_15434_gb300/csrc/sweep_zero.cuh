@@ -16,7 +16,7 @@
 // side, the gap and two of the three coefficient words and writes e, 20 bytes per cell
 // instead of 4 + 29.
 //
-// Layout: a block owns a 64 x TY tile of x-y rows and marches NZ planes up z.  A thread owns
+// Layout: a block owns a TX x TY tile of x-y rows and marches NZ planes up z.  A thread owns
 // the column pair (x, x + 1), x even, of one row; on every plane one of the two is red and the
 // other black.  Step s computes the red cell of plane s (rows -1 .. TY of the tile, so the
 // black cells on the tile's y edges have their faces) and the black cell of plane s - 2, the
@@ -24,21 +24,23 @@
 // of planes s - 1 and s - 3 in its column, which this thread computed itself; its in-plane
 // faces are the red values of plane s - 2 of the pair and of the neighbouring pairs and rows,
 // from a three-slot shared ring (one value per pair: the red one).  One more warp computes the
-// red cells just outside the tile in x (x = -1 and x = 64).  Fields are loaded one plane
-// ahead into registers (8-byte loads of the pair, coalesced per row).
+// red cells just outside the tile in x (x = -1 and x = TX).  Fields are loaded one plane
+// ahead into registers (8-byte loads of the pair, coalesced per row), PF planes ahead.
 #pragma once
 
 #include "sweep_pair.cuh"
 
 namespace pmeft {
 
-template <int TY>
+template <int TX, int TY>
 struct ZeroGeom {
-    static constexpr int RW = 34;                   // ring row: x = -1, pairs 0..31, x = 64
+    static constexpr int WPR = TX / 64;             // warps per row (32 column pairs each)
+    static constexpr int RW = TX / 2 + 2;           // ring row: x = -1, the pairs, x = TX
     static constexpr int RH = TY + 2;               // ring rows: y = -1 .. TY
     static constexpr int NXH = 2 * RH;              // x-halo lanes
     static constexpr int NXW = (NXH + 31) / 32;     // x-halo warps
-    static constexpr int NW = RH + NXW;             // row warps + x-halo warps
+    static constexpr int NRW = RH * WPR;            // row warps
+    static constexpr int NW = NRW + NXW;            // row warps + x-halo warps
     static constexpr int NT = 32 * NW;
 };
 
@@ -58,8 +60,8 @@ __device__ __forceinline__ float2 zero_start_update(float bax, float bay, float 
     const Local2 o = local_eval2_cf(st, ca, cb, ih2, nu, f2(kap), rhs, f2(lsat), gapx);
     float2 e;
     if (kap == 0.f) {
-        e.x = __fdividef(-o.G.x, o.Ep.x);
-        e.y = __fdividef(-o.G.y, o.Ep.y);
+        e.x = div_ftz(-o.G.x, o.Ep.x);
+        e.y = div_ftz(-o.G.y, o.Ep.y);
     } else {
         e.x = pick_update(o.G.x, o.Ep.x, o.P.x, o.D.x, o.g.x, sp, Df, h2over6, inv2P);
         e.y = pick_update(o.G.y, o.Ep.y, o.P.y, o.D.y, o.g.y, sp, Df, h2over6, inv2P);
@@ -69,20 +71,21 @@ __device__ __forceinline__ float2 zero_start_update(float bax, float bay, float 
 
 // One sweep from e = 0 into V (n^3).  F: right-hand side (fscale F + lam [+ *lamp]); gap:
 // L_sat - L(background); coef: the three BF16-pair planes of the background coefficients
-// (only the first two are read).  Grid (n / 64, n / TY, n / NZ), n >= 64.
-template <int TY>
-__global__ void __launch_bounds__(ZeroGeom<TY>::NT, 3) k_sweep_zero(float* __restrict__ V, const float* __restrict__ F,
+// (only the first two are read).  Tile TX x TY (TX = 64 or 128), PF: planes of fields loaded
+// ahead.  Grid (n / TX, n / TY, n / NZ), n >= TX.
+template <int TX, int TY, int PF>
+__global__ void __launch_bounds__(ZeroGeom<TX, TY>::NT, ZeroGeom<TX, TY>::NT <= 512 ? 2 : 1) k_sweep_zero(float* __restrict__ V, const float* __restrict__ F,
                                                                  float fscale, float lam, const float* __restrict__ gap,
                                                                  int n, int NZ, float ih2, float nu, float kap, float sp,
                                                                  float Df, float lsat, const float* __restrict__ lamp,
                                                                  const uint32_t* __restrict__ coef)
 {
-    using G = ZeroGeom<TY>;
+    using G = ZeroGeom<TX, TY>;
     constexpr int RW = G::RW, RH = G::RH;
     __shared__ float ring[3][RH][RW];  // red values of three planes, slot (p - z0 + 1) mod 3
     if (lamp) lam += *lamp;
     const int m = n - 1;
-    const int x0 = blockIdx.x * 64, y0 = blockIdx.y * TY, z0 = blockIdx.z * NZ;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * NZ;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const size_t plane = (size_t)n * n, cells = plane * (size_t)n;
     const float h2over6 = 1.f / (6.f * ih2), inv2P = kap != 0.f ? 1.f / (-48.f * kap * ih2 * ih2) : 0.f;
@@ -90,21 +93,27 @@ __global__ void __launch_bounds__(ZeroGeom<TY>::NT, 3) k_sweep_zero(float* __res
     auto slot = [&](int p) { return (p - z0 + 1) % 3; };  // p >= z0 - 1
     const int zred = z0 + NZ;                            // red planes z0 - 1 .. zred
 
-    if (warp < RH) {
+    if (warp < G::NRW) {
         // ---------------------------------------------------------------- row warps
-        const int y = warp - 1;  // -1 .. TY
+        const int y = warp / G::WPR - 1;  // -1 .. TY
         const bool interior = y >= 0 && y < TY;
-        const int q = lane;
+        const int q = (warp % G::WPR) * 32 + lane;  // column pair
         const size_t rowoff = (size_t)((y0 + y) & m) * n + x0 + 2 * q;  // x0 + 2q + 1 < n: no wrap in x
-        float2 fN = make_float2(0.f, 0.f), gN = fN;  // fields of the next plane
-        uint2 c0N = make_uint2(0u, 0u), c1N = c0N;
-        auto load = [&](int p) {
+        // fields of the next PF planes: k = 0 the next, PF - 1 the last loaded
+        float2 fN[PF], gN[PF];
+        uint2 c0N[PF], c1N[PF];
+#pragma unroll
+        for (int k = 0; k < PF; ++k) {
+            fN[k] = gN[k] = make_float2(0.f, 0.f);
+            c0N[k] = c1N[k] = make_uint2(0u, 0u);
+        }
+        auto load = [&](int p, int k) {
             const size_t o = (size_t)(p & m) * plane + rowoff;
-            fN = *reinterpret_cast<const float2*>(F + o);
-            gN = *reinterpret_cast<const float2*>(gap + o);
+            fN[k] = *reinterpret_cast<const float2*>(F + o);
+            gN[k] = *reinterpret_cast<const float2*>(gap + o);
             if (interior) {
-                c0N = *reinterpret_cast<const uint2*>(coef + o);
-                c1N = *reinterpret_cast<const uint2*>(coef + cells + o);
+                c0N[k] = *reinterpret_cast<const uint2*>(coef + o);
+                c1N[k] = *reinterpret_cast<const uint2*>(coef + cells + o);
             }
         };
         // fields of the black cells of planes s - 1 (b1) and s - 2 (b2)
@@ -112,11 +121,20 @@ __global__ void __launch_bounds__(ZeroGeom<TY>::NT, 3) k_sweep_zero(float* __res
         uint32_t b1C0 = 0u, b1C1 = 0u, b2C0 = 0u, b2C1 = 0u;
         // red values of planes s - 1 (column 1 - C), s - 2 (column C), s - 3 (column 1 - C)
         float r1 = 0.f, r2 = 0.f, r3 = 0.f;
-        load(z0 - 1);
+#pragma unroll
+        for (int k = 0; k < PF; ++k)
+            if (z0 - 1 + k <= zred) load(z0 - 1 + k, k);
         for (int s = z0 - 1; s <= zred + 1; ++s) {
-            const float2 fc = fN, gc = gN;
-            const uint2 c0c = c0N, c1c = c1N;
-            if (s + 1 <= zred) load(s + 1);
+            const float2 fc = fN[0], gc = gN[0];
+            const uint2 c0c = c0N[0], c1c = c1N[0];
+#pragma unroll
+            for (int k = 0; k + 1 < PF; ++k) {
+                fN[k] = fN[k + 1];
+                gN[k] = gN[k + 1];
+                c0N[k] = c0N[k + 1];
+                c1N[k] = c1N[k + 1];
+            }
+            if (s + PF <= zred) load(s + PF, PF - 1);
             const int C = (y0 + y + s) & 1;  // the column of the pair that is red on planes s, s - 2
             const bool blk = interior && s - 2 >= z0;
             // black cell of plane s - 2 (column 1 - C): in-plane faces from the ring
@@ -155,15 +173,15 @@ __global__ void __launch_bounds__(ZeroGeom<TY>::NT, 3) k_sweep_zero(float* __res
         }
     } else {
         // ---------------------------------------------------------------- x-halo lanes
-        const int idx = (warp - RH) * 32 + lane;
+        const int idx = (warp - G::NRW) * 32 + lane;
         const bool active = idx < G::NXH;
-        const int side = idx < RH ? 0 : 1;  // 0: x = -1, 1: x = 64
+        const int side = idx < RH ? 0 : 1;  // 0: x = -1, 1: x = TX
         const int y = (active ? idx % RH : 0) - 1;
-        const int xg = side ? ((x0 + 64) & m) : ((x0 - 1) & m);
+        const int xg = side ? ((x0 + TX) & m) : ((x0 - 1) & m);
         const int col = side ? RW - 1 : 0;
         const size_t rowoff = (size_t)((y0 + y) & m) * n + xg;
         for (int s = z0 - 1; s <= zred + 1; ++s) {
-            // red on plane s when x + y + s is even (x = x0 - 1 or x0 + 64, x0 even)
+            // red on plane s when x + y + s is even (x = x0 - 1 or x0 + TX, x0 even)
             const bool red = active && s <= zred && ((1 - side + y0 + y + s) & 1) == 0;
             if (red) {
                 const size_t o = (size_t)(s & m) * plane + rowoff;
