@@ -230,7 +230,8 @@ pm_status pm_run(pm_ctx* ctx, double* pos, double* vel, long long np, int n, dou
  *   other bad arguments PM_ERR_INVALID_ARG; PM_ERR_OVERFLOW as for pm_deposit_cic.
  * The current device must be the one that holds pos and delta.  The first call on
  * each device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current and keeps it for later calls.  Every call uses
+ * device current and keeps it for later calls; make that first call before any stream
+ * capture is begun on the device.  Every call uses
  * the same array and clears the part it needs, so calls whose work overlaps on the
  * GPU (other streams, other threads) race with each other.  The call synchronises
  * the stream to read the overflow flag.
