@@ -22,6 +22,7 @@ import argparse
 import json
 import math
 import os
+import re
 import subprocess
 import sys
 import time
@@ -31,16 +32,17 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 COMBOS = [(-2.0, 0.0), (-2.0, 0.5), (-0.5, 0.0), (-0.5, 0.5)]
-# DRAM bytes per cell of one finest-level sweep launch of the variant the autotuner keeps at
-# 512^3 (k_sweep_pair<16, 1, 1, 1, 1>: tile 64 x 16, 32 planes per block, background through
-# its BF16 coefficients, one warp per red unit), from one ncu capture of a 256^3 launch of the
-# same variant (dram__bytes_read.sum + dram__bytes_write.sum = 431.1 + 58.5 MB over 16.78 M
-# cells; `python -m paper_2604_15434_gb300.microbench sweep --n 256 --mode 115`), scaled by the
-# cell count.  It is reported only when the autotuner's choice is that variant.
-SWEEP_DRAM = {"tile 64x16 nz 32 pair bal": 29.2}
-SWEEP_DRAM_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one 256^3 launch of "
-                     "k_sweep_pair<16,1,1,1,1> (microbench sweep --n 256 --mode 115): 29.2 B/cell, "
-                     "times this launch's cells")
+# DRAM bytes per cell of one finest-level sweep launch of the coefficient-level variants the
+# autotuner keeps at 512^3, each from one ncu capture of a 256^3 launch of that variant
+# (dram__bytes_read.sum + dram__bytes_write.sum over 16.78 M cells;
+# `python -m paper_2604_15434_gb300.microbench sweep --n 256 --mode <mode>`), scaled by the cell
+# count.  Keyed by the autotuner's description of its choice; a variant without a capture
+# reports no traffic.
+SWEEP_DRAM = {
+    "tile 64x16 nz 32 pair": (29.1, "k_sweep_pair<16,1,1,1,0>", 111),
+    "tile 64x16 nz 32 pair bal": (29.2, "k_sweep_pair<16,1,1,1,1>", 115),
+    "tile 64x16 nz 32 col": (29.9, "k_sweep_col<16>", 119),
+}
 TOL = 1e-8
 SEED = 1003
 # the sampler's bound on |mu_chi| = |xi/nu|: draws beyond it (with more than 90% of the cells
@@ -673,12 +675,16 @@ def main():
         ach = bytes_launch / (avg_ms * 1e-3) / 1e9
         tuned = [l for l in ctx.tune_log().splitlines() if f"n={n} bg gap" in l]
         variant = tuned[-1].split(": ", 1)[1].split(" (variants")[0] if tuned else "?"
-        per_cell = next((v for k, v in SWEEP_DRAM.items() if variant.startswith(k)), None)
+        mv = re.match(r"(.*?) [0-9.]+ ms$", variant)
+        cap = SWEEP_DRAM.get(mv.group(1) if mv else variant)
+        per_cell = cap[0] if cap else None
         roof = {"kernel": "single-pass FP32 red-black sweep of the finest level (k_sweep_pair / k_sweep_col / "
                           "k_sweep_fused, autotuned: " + variant + ")", "bound": "hbm",
                 "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                 "traffic": per_cell * cells if per_cell else None,
-                "traffic_source": SWEEP_DRAM_SOURCE if per_cell else "no capture of this variant",
+                "traffic_source": (f"ncu dram__bytes_read.sum + dram__bytes_write.sum of one 256^3 launch of {cap[1]} "
+                                   f"(microbench sweep --n 256 --mode {cap[2]}): {cap[0]} B/cell, times this "
+                                   "launch's cells") if cap else "no capture of this variant",
                 "peak_source": src, "frac_of_nominal_8000": ach / 8000.0,
                 "bytes_per_launch": bytes_launch, "bytes_per_cell": 12,
                 "frac_20B": cells * 20 / (avg_ms * 1e-3) / 1e9 / hbm,
