@@ -44,29 +44,51 @@ struct ZeroGeom {
     static constexpr int NT = 32 * NW;
 };
 
-// The red and black updates of two cells, one per lane of the paired arithmetic.  Red lane:
-// all stencil values zero.  Black lane: faces bax, bay, baz, the rest zero.
-__device__ __forceinline__ float2 zero_start_update(float bax, float bay, float baz, const BgCoef& cb, float2 rhs,
-                                                    float2 gapx, float ih2, float nu, float kap, float sp, float Df,
-                                                    float lsat, float h2over6, float inv2P)
+// The general kernels' local evaluation (local_eval2_cf, per lane) and pick_update with the
+// zeros of the first sweep put in, operation for operation, so that each result is the
+// general sweep's; the terms the zeros remove are left out.  The round-to-nearest intrinsics
+// keep the compiler from contracting a product into a neighbouring sum (the general kernels'
+// paired instructions are never contracted either).
+struct ZeroConst {
+    float ih2, nuih2, nu6, kap, kap1, m4P, sp, Df, lsat, h2over6, inv2P;
+};
+
+__device__ __forceinline__ float zero_pick(const ZeroConst& k, float G, float Ltot, float g)
 {
-    Stencil2 st;
-    st.c0 = make_float2(0.f, 0.f);
-    st.ax = make_float2(0.f, bax);
-    st.ay = make_float2(0.f, bay);
-    st.az = make_float2(0.f, baz);
-    st.exy = st.exz = st.eyz = make_float2(0.f, 0.f);
-    const BgCoef ca{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    const Local2 o = local_eval2_cf(st, ca, cb, ih2, nu, f2(kap), rhs, f2(lsat), gapx);
-    float2 e;
-    if (kap == 0.f) {
-        e.x = div_ftz(-o.G.x, o.Ep.x);
-        e.y = div_ftz(-o.G.y, o.Ep.y);
-    } else {
-        e.x = pick_update(o.G.x, o.Ep.x, o.P.x, o.D.x, o.g.x, sp, Df, h2over6, inv2P);
-        e.y = pick_update(o.G.y, o.Ep.y, o.P.y, o.D.y, o.g.y, sp, Df, h2over6, inv2P);
-    }
-    return make_float2(0.f + e.x, 0.f + e.y);  // the new value c0 + e, as the general kernels form it
+    const float Ep = __fmul_rn(__fmaf_rn(8.f, __fmul_rn(k.kap, Ltot), k.nu6), k.ih2);
+    if (k.kap == 0.f) return div_ftz(-G, Ep);
+    const float D = __fmaf_rn(k.m4P, G, __fmul_rn(Ep, Ep));
+    return pick_update(G, Ep, 0.f, D, g, k.sp, k.Df, k.h2over6, k.inv2P);
+}
+
+// Red cell: every stencil value zero, so L = 0 and q2 = 0: E = -(rhs), the gap unchanged.
+__device__ __forceinline__ float zero_red(const ZeroConst& k, float rhs, float gapx)
+{
+    const float lsat = k.kap != 0.f ? k.lsat : 0.f;
+    const float Ltot = __fsub_rn(lsat, gapx);
+    const float g = k.kap != 0.f ? gapx : 0.f;
+    return __fadd_rn(0.f, zero_pick(k, __fsub_rn(0.f, rhs), Ltot, g));
+}
+
+// Black cell: the six faces (sums ax, ay, az of the new red values), centre and edges zero, so
+// X = ax, Y = ay, Z = az and no cross differences; the background enters through cX, cY, cZ.
+__device__ __forceinline__ float zero_black(const ZeroConst& k, float ax, float ay, float az, const BgCoef& cf,
+                                            float rhs, float gapx)
+{
+    const float L1 = __fadd_rn(__fadd_rn(ax, ay), az);
+    float pr = __fmul_rn(ax, ay);
+    pr = __fmaf_rn(ay, az, pr);
+    pr = __fmaf_rn(az, ax, pr);
+    float q2 = __fmul_rn(2.f, pr);
+    q2 = __fmaf_rn(cf.cX, ax, q2);
+    q2 = __fmaf_rn(cf.cY, ay, q2);
+    q2 = __fmaf_rn(cf.cZ, az, q2);
+    const float lsat = k.kap != 0.f ? k.lsat : 0.f;
+    float g = __fmaf_rn(-k.ih2, L1, gapx);
+    const float Ltot = __fsub_rn(lsat, g);
+    g = k.kap != 0.f ? g : 0.f;
+    const float N = __fmaf_rn(-1.f, __fmul_rn(k.kap1, q2), __fmul_rn(k.nuih2, L1));
+    return __fadd_rn(0.f, zero_pick(k, __fsub_rn(N, rhs), Ltot, g));
 }
 
 // One sweep from e = 0 into V (n^3).  F: right-hand side (fscale F + lam [+ *lamp]); gap:
@@ -88,8 +110,18 @@ __global__ void __launch_bounds__(ZeroGeom<TX, TY>::NT, ZeroGeom<TX, TY>::NT <= 
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * NZ;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const size_t plane = (size_t)n * n, cells = plane * (size_t)n;
-    const float h2over6 = 1.f / (6.f * ih2), inv2P = kap != 0.f ? 1.f / (-48.f * kap * ih2 * ih2) : 0.f;
-    const BgCoef nocoef{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    ZeroConst K;
+    K.ih2 = ih2;
+    K.nuih2 = nu * ih2;
+    K.nu6 = -6.f * nu;
+    K.kap = kap;
+    K.kap1 = kap * (ih2 * ih2);
+    K.m4P = -4.f * (-24.f * K.kap1);
+    K.sp = sp;
+    K.Df = Df;
+    K.lsat = lsat;
+    K.h2over6 = 1.f / (6.f * ih2);
+    K.inv2P = kap != 0.f ? 1.f / (-48.f * kap * ih2 * ih2) : 0.f;
     auto slot = [&](int p) { return (p - z0 + 1) % 3; };  // p >= z0 - 1
     const int zred = z0 + NZ;                            // red planes z0 - 1 .. zred
 
@@ -144,17 +176,17 @@ __global__ void __launch_bounds__(ZeroGeom<TX, TY>::NT, ZeroGeom<TX, TY>::NT <= 
                 // its x-neighbour outside the pair: the red cell of pair q + 1 (black column 1) or of
                 // pair q - 1 (black column 0)
                 const float rout = C ? r[y + 1][q] : r[y + 1][q + 2];
-                bax = r2 + rout;
-                bay = r[y + 2][q + 1] + r[y][q + 1];
+                bax = __fadd_rn(r2, rout);
+                bay = __fadd_rn(r[y + 2][q + 1], r[y][q + 1]);
             }
-            const float2 rhs = f2fma(f2(fscale), make_float2(C ? fc.y : fc.x, b2F), f2(lam));
-            const BgCoef cb = blk ? unpack_bg_coef(b2C0, b2C1, 0u) : nocoef;
-            // .x: the red cell of plane s; .y: the black cell of plane s - 2
-            const float2 v = zero_start_update(bax, bay, r1 + r3, cb, rhs, make_float2(C ? gc.y : gc.x, b2G), ih2, nu,
-                                               kap, sp, Df, lsat, h2over6, inv2P);
-            if (s <= zred) ring[slot(s)][y + 1][q + 1] = v.x;
+            // the red cell of plane s
+            const float vr = zero_red(K, __fmaf_rn(fscale, C ? fc.y : fc.x, lam), C ? gc.y : gc.x);
+            if (s <= zred) ring[slot(s)][y + 1][q + 1] = vr;
             if (blk) {
-                const float2 out = C ? make_float2(v.y, r2) : make_float2(r2, v.y);
+                // the black cell of plane s - 2
+                const float vb = zero_black(K, bax, bay, __fadd_rn(r1, r3), unpack_bg_coef(b2C0, b2C1, 0u),
+                                            __fmaf_rn(fscale, b2F, lam), b2G);
+                const float2 out = C ? make_float2(vb, r2) : make_float2(r2, vb);
                 *reinterpret_cast<float2*>(V + (size_t)(s - 2) * plane + rowoff) = out;
             }
             // the black cell of plane s is column 1 - C
@@ -168,7 +200,7 @@ __global__ void __launch_bounds__(ZeroGeom<TX, TY>::NT, ZeroGeom<TX, TY>::NT <= 
             b1C1 = C ? c1c.x : c1c.y;
             r3 = r2;
             r2 = r1;
-            r1 = v.x;
+            r1 = vr;
             __syncthreads();
         }
     } else {
@@ -185,10 +217,7 @@ __global__ void __launch_bounds__(ZeroGeom<TX, TY>::NT, ZeroGeom<TX, TY>::NT <= 
             const bool red = active && s <= zred && ((1 - side + y0 + y + s) & 1) == 0;
             if (red) {
                 const size_t o = (size_t)(s & m) * plane + rowoff;
-                const float2 rhs = f2fma(f2(fscale), make_float2(F[o], 0.f), f2(lam));
-                const float2 v = zero_start_update(0.f, 0.f, 0.f, nocoef, rhs, make_float2(gap[o], 0.f), ih2, nu, kap,
-                                                   sp, Df, lsat, h2over6, inv2P);
-                ring[slot(s)][y + 1][col] = v.x;
+                ring[slot(s)][y + 1][col] = zero_red(K, __fmaf_rn(fscale, F[o], lam), gap[o]);
             }
             __syncthreads();
         }
