@@ -87,7 +87,7 @@ __device__ __forceinline__ void half_sweep_cell(const T* own, const T* oth,
         out[c] = opsplit_update<T>(s, ih2, nu, kc, fscale * F[c] + lam, etanu);
         return;
     }
-    const T lsat = kc != T(0) ? lsat_c / w : T(0);
+    const T lsat = kc != T(0) ? (kmask ? lsat_c / w : lsat_c) : T(0);  // w = 1 without a mask
     Local<T> o = local_eval<T, BG>(s, b, ih2, nu, kc, fscale * F[c] + lam, lsat, gap != nullptr, gap ? gap[c] : T(0));
     out[c] = s.c0 + local_update(o, sp, Df, ih2);
 }
@@ -149,7 +149,7 @@ __device__ __forceinline__ void residual_cell_s(const Stencil<T>& s, const Stenc
 {
     const T w = screen_w<T>(kmask, c);
     const T kc = kap * w;
-    const T lsat = kc != T(0) ? lsat_c / w : T(0);
+    const T lsat = kc != T(0) ? (kmask ? lsat_c / w : lsat_c) : T(0);  // w = 1 without a mask
     Local<T> o = local_eval<T, BG>(s, b, ih2, nu, kc, fscale * F[c] + lam, lsat, gap != nullptr, gap ? gap[c] : T(0));
     // the floored piece exists on the finest level; coarse levels take their pieces from
     // the restricted mask (linear where masked, quadratic elsewhere), so their right-hand
@@ -616,7 +616,7 @@ __device__ void coarsest_block(T* u, const T* F, T fscale, const uint8_t* kmask,
                 if (BG) b = load_stencil<T>(sb, sb, i, j, k, n);
                 const T w = sk[c] >= 8 ? T(0) : (T)(8 - sk[c]) * T(0.125);
                 const T kc = kap * w;
-                Local<T> o = local_eval<T, BG>(s, b, ih2, nu, kc, sf[c] + lam, kc != T(0) ? lsat_c / w : T(0));
+                Local<T> o = local_eval<T, BG>(s, b, ih2, nu, kc, sf[c] + lam, kc != T(0) ? (kmask ? lsat_c / w : lsat_c) : T(0));
                 su[c] = s.c0 + local_update(o, sp, Df, ih2);
             }
             __syncthreads();
@@ -630,7 +630,7 @@ __device__ void coarsest_block(T* u, const T* F, T fscale, const uint8_t* kmask,
             if (BG) b = load_stencil<T>(sb, sb, i, j, k, n);
             const T w = sk[c] >= 8 ? T(0) : (T)(8 - sk[c]) * T(0.125);
             const T kc = kap * w;
-            Local<T> o = local_eval<T, BG>(s, b, ih2, nu, kc, sf[c] + lam, kc != T(0) ? lsat_c / w : T(0));
+            Local<T> o = local_eval<T, BG>(s, b, ih2, nu, kc, sf[c] + lam, kc != T(0) ? (kmask ? lsat_c / w : lsat_c) : T(0));
             const bool fl = (o.P != T(0)) && (o.D < (floor_piece ? Df : T(0)));
             a0 += fl ? nu * o.g : -o.G;
             a1 += fl ? T(0) : T(1);

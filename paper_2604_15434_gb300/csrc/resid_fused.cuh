@@ -131,7 +131,9 @@ __global__ void __launch_bounds__(256) k_residual_zm(const float* __restrict__ u
         };
         const Stencil2 a2 = st2(up, uc, un);
         const float2 kc2 = make_float2(kap * wk[0], kap * wk[1]);
-        const float2 lsat2 = make_float2(kc2.x != 0.f ? lsat_c / wk[0] : 0.f, kc2.y != 0.f ? lsat_c / wk[1] : 0.f);
+        // L_sat / w (w = 1 without a mask: no division)
+        const float2 lsat2 = kmask ? make_float2(kc2.x != 0.f ? lsat_c / wk[0] : 0.f, kc2.y != 0.f ? lsat_c / wk[1] : 0.f)
+                                   : make_float2(kc2.x != 0.f ? lsat_c : 0.f, kc2.y != 0.f ? lsat_c : 0.f);
         const float2 rhs2 = make_float2(fscale * fv[0] + lam, fscale * fv[1] + lam);
         const float2 gap2 = make_float2(gv[0], gv[1]);
         Local2 o2;
