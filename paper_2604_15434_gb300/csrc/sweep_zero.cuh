@@ -19,13 +19,13 @@
 // Layout: a block owns a TX x TY tile of x-y rows and marches NZ planes up z.  A thread owns
 // the column pair (x, x + 1), x even, of one row; on every plane one of the two is red and the
 // other black.  Step s computes the red cell of plane s (rows -1 .. TY of the tile, so the
-// black cells on the tile's y edges have their faces) and the black cell of plane s - 2, the
-// two as the lanes of paired FP32 instructions.  The black cell's z-faces are the red values
+// black cells on the tile's y edges have their faces) and the black cell of plane s - 2, each
+// by a scalar formula with the zeros taken out.  The black cell's z-faces are the red values
 // of planes s - 1 and s - 3 in its column, which this thread computed itself; its in-plane
 // faces are the red values of plane s - 2 of the pair and of the neighbouring pairs and rows,
 // from a three-slot shared ring (one value per pair: the red one).  One more warp computes the
-// red cells just outside the tile in x (x = -1 and x = TX).  Fields are loaded one plane
-// ahead into registers (8-byte loads of the pair, coalesced per row), PF planes ahead.
+// red cells just outside the tile in x (x = -1 and x = TX).  Fields are loaded PF planes
+// ahead into registers (8-byte loads of the pair, coalesced per row).
 #pragma once
 
 #include "sweep_pair.cuh"
