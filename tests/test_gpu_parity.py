@@ -449,6 +449,24 @@ def test_zero_start_sweep_equals_general_sweep_from_zero(gpu_lib, n, pair, varia
     assert np.array_equal(got, want), np.abs(got - want).max() / np.abs(want).max()
 
 
+@pytest.mark.parametrize("n", [64, 256])
+def test_zero_start_sweep_without_screening(gpu_lib, n):
+    """kappa = 0 (no screening term: the linear Newton step in every cell) through the
+    zero-start kernel equals the general coefficient sweep on u = 0."""
+    c = O.coefficients(-0.5, 0.0, 1.0)
+    f = O.source(synth.lognormal_delta(n, -2.0, 1.5, 900 + n), c)
+    rng = np.random.default_rng(3 * n)
+    bg = cu(2.0 * rng.standard_normal((n, n, n)) / n ** 2, torch.float32)
+    gap = cu(rng.standard_normal((n, n, n)), torch.float32)
+    args = (cu(f, torch.float32), -0.02, c["nu"], 0.0, 0.35)
+    want = gpu_lib.pm_mg_sweep_f32(torch.zeros((n, n, n), dtype=torch.float32, device=DEV), *args,
+                                   mode=PAIR_COEF_MODE, bg=bg, gap=gap).cpu().numpy()
+    got = gpu_lib.pm_mg_sweep_f32(cu(rng.standard_normal((n, n, n)), torch.float32), *args, mode=ZERO_START_MODE,
+                                  bg=bg, gap=gap).cpu().numpy()
+    assert np.isfinite(got).all() and np.abs(want).max() > 0
+    assert np.array_equal(got, want), np.abs(got - want).max() / np.abs(want).max()
+
+
 @pytest.mark.parametrize("pair", [(-2.0, 0.0), (-0.5, 0.0)])
 def test_zero_start_solve_equals_cleared_start_256(gpu_lib, pair):
     """Inside the mixed solve at 256^3 (the size where the finest inner level receives the
