@@ -54,6 +54,20 @@ def test_deposit_edge_positions(gpu_lib):
     assert np.array_equal(acc, O.deposit_cic(pos, n))
 
 
+def test_empty_particle_set_is_rejected(gpu_lib):
+    """No particles: the density contrast is undefined, so the deposit and the force
+    interpolation return PM_ERR_INVALID_ARG without touching memory."""
+    n = 16
+    empty = torch.zeros((3, 0), dtype=torch.float64, device=DEV)
+    with pytest.raises(gpu_lib.PMError) as e:
+        gpu_lib.pm_deposit_cic(empty, n)
+    assert e.value.status == gpu_lib.PM_ERR_INVALID_ARG
+    psi = torch.zeros((n, n, n), dtype=torch.float64, device=DEV)
+    with pytest.raises(gpu_lib.PMError) as e:
+        gpu_lib.force_interp(psi, psi, -1.0, 0.2, 1.0, empty)
+    assert e.value.status == gpu_lib.PM_ERR_INVALID_ARG
+
+
 def test_deposit_order_independent_on_gpu(gpu_lib, c1_particles):
     perm = np.random.default_rng(5).permutation(c1_particles.shape[1])
     a = gpu_lib.pm_deposit_cic_fixed(cu(c1_particles), 32).cpu().numpy()
