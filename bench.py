@@ -43,6 +43,18 @@ SWEEP_DRAM = {
     "tile 64x16 nz 32 pair bal": (29.2, "k_sweep_pair<16,1,1,1,1>", 115),
     "tile 64x16 nz 32 col": (29.9, "k_sweep_col<16>", 119),
 }
+
+
+
+def sweep_capture(tune_line: str):
+    """The DRAM capture (bytes per cell, kernel, microbenchmark mode) of the sweep variant a
+    tune-log line names ("sweep32 n=512 bg gap coef: tile 64x16 nz 32 pair 0.94 ms (variants
+    ..."), or None when that variant has no capture."""
+    variant = tune_line.split(": ", 1)[1].split(" (variants")[0] if ": " in tune_line else tune_line
+    mv = re.match(r"(.*?) [0-9.]+ ms$", variant)
+    return SWEEP_DRAM.get(mv.group(1) if mv else variant)
+
+
 TOL = 1e-8
 SEED = 1003
 # the sampler's bound on |mu_chi| = |xi/nu|: draws beyond it (with more than 90% of the cells
@@ -675,8 +687,7 @@ def main():
         ach = bytes_launch / (avg_ms * 1e-3) / 1e9
         tuned = [l for l in ctx.tune_log().splitlines() if f"n={n} bg gap" in l]
         variant = tuned[-1].split(": ", 1)[1].split(" (variants")[0] if tuned else "?"
-        mv = re.match(r"(.*?) [0-9.]+ ms$", variant)
-        cap = SWEEP_DRAM.get(mv.group(1) if mv else variant)
+        cap = sweep_capture(tuned[-1]) if tuned else None
         per_cell = cap[0] if cap else None
         roof = {"kernel": "single-pass FP32 red-black sweep of the finest level (k_sweep_pair / k_sweep_col / "
                           "k_sweep_fused, autotuned: " + variant + ")", "bound": "hbm",

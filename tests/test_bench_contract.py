@@ -74,3 +74,16 @@ def test_reference_arm_other_ranks_exit_without_work():
                           "--warmup", "0", "--sample-n", "32"], capture_output=True, text=True, env=env, cwd=ROOT,
                          timeout=300)
     assert out.returncode == 0 and out.stdout.strip() == ""
+
+
+def test_roofline_traffic_follows_the_autotuners_choice():
+    """The roofline line's DRAM traffic comes from the capture of the sweep variant the
+    autotuner kept, matched on its exact description (the balanced form is not taken for the
+    256-thread one, nor the other way round); a variant without a capture gives none."""
+    sys.path.insert(0, ROOT)
+    import bench
+    line = "sweep32 n=512 bg gap coef: tile 64x16 nz 32 pair {} ms (variants tried, ms: 10:0.9370 14:0.9904)"
+    assert bench.sweep_capture(line.format("0.937099"))[2] == 111
+    assert bench.sweep_capture(line.replace("pair", "pair bal").format("0.99"))[2] == 115
+    assert bench.sweep_capture(line.replace("pair", "col").format("0.97"))[2] == 119
+    assert bench.sweep_capture(line.replace("nz 32", "nz 64").format("1.1")) is None
